@@ -1,0 +1,296 @@
+#!/usr/bin/env python3
+"""Benchmark of the emission-absorption march: ray-substep updates per second.
+
+One step = one rt_advance on the turbulent workload (128^3 lognormal kappa, 16 sources,
+N_Omega 3072, ds 0.5, c dt 128 so N_s 256, 4 frequency bins): packing, zeroing, the march
+kernel and the unpack, inputs resident in HBM. L2 is flushed (256 MiB write) before every
+timed step, outside the step's CUDA-event pair. One update = one substep of one
+(ray, source, bin), U = 16 * 3072 * 256 * 4 = 50,331,648 per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas, weak
+scaling); the time is the max over ranks and the value counts the updates of all ranks.
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-substep updates/s (forward march)"
+UNIT = "updates/s"
+WORKLOAD = ("turbulent lognormal kappa 128^3 (sigma_g 1, mean 0.05), 16 sources with Gaussian j blobs, "
+            "N_Omega 3072, ds 0.5, c*dt 128 (N_s 256), 4 frequency bins, FP32")
+ALGO_BYTES_PER_UPDATE = 68     # 9 gathered floats (8 j corners + 1 kappa) + 8 deposited floats
+FLUSH_BYTES = 256 << 20
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured", p
+    except Exception:
+        return 6800.0, "fallback", {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("march_fwd.cu", "march_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2511_09389_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(src_hash):
+    """DRAM bytes per launch of the march kernel from the committed ncu summary, or None when
+    the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "march_fwd_turbulent128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != src_hash:
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while the benchmark runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(p, src_slice, ns):
+    import oracle
+    t0 = time.perf_counter()
+    F = oracle.advance(p.j, p.kappa, p.sources[src_slice], p.num_rays, p.step_size, ns, geom_mode=0)
+    return F, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The FP64 oracle, as it stands, on one host core: each step marches a bounded sample
+    (one source, all rays, bins and substeps) of the benchmark workload."""
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2511_09389_gb300 import inputs
+    p = inputs.turbulent()
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    per_src = p.num_rays * ns * p.n_freq
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = i % len(p.sources)
+        _, dt = run_oracle_sample(p, slice(s, s + 1), ns)
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = per_src / t
+    sample = f"1 of 16 sources per step ({per_src} updates: 3072 rays x 256 substeps x 4 bins), FP64, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def native_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = rank_info()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2511_09389_gb300 import build, inputs
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2511_09389_gb300.api import Grid
+
+    from paper_2511_09389_gb300.api import num_substeps
+    p = inputs.turbulent()
+    U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
+    g = Grid(p.shape, 8, profile=True, autotune=True)   # tuned during the warm-up calls
+    j = torch.from_numpy(p.j).to(dev)
+    k = torch.from_numpy(p.kappa).to(dev)
+    s = torch.from_numpy(p.sources).to(dev)
+    out = torch.empty_like(j)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
+
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(visible[local].strip() if local < len(visible) else local)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ms, kern_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)                 # evict L2 before the step (not timed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        ev[i][1].synchronize()
+        step_ms.append(ev[i][0].elapsed_time(ev[i][1]))
+        kern_ms.append(g.kernel_ms())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+
+    # end to end through the host entry point: pinned inputs in, field back to the host
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    hj, hk, hs = pin(p.j), pin(p.kappa), pin(p.sources)
+    hout = torch.empty(p.j.shape, dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        g.advance_host(hj, hk, hs, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=hout)
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.advance_host(hj, hk, hs, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=hout)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+
+    ms = statistics.mean(step_ms)
+    kms = statistics.mean(kern_ms)
+    ems = statistics.mean(e2e_ms)
+    if world > 1:
+        t = torch.tensor([ms, kms, ems], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kms, ems = t.tolist()
+
+    peak, peak_kind, _ = load_peaks()
+    achieved = ALGO_BYTES_PER_UPDATE * U / (kms * 1e-3) / 1e9
+    traffic = profiled_traffic(kernel_source_hash())
+    h2d = p.j.nbytes + p.kappa.nbytes + p.sources.nbytes
+    d2h = p.j.nbytes
+
+    line = {
+        "metric": METRIC, "value": world * U / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "updates_per_step": U, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "kernel_ms": kms, "wall_s": wall, "launch_plan": g.last_plan()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "basis": f"{ALGO_BYTES_PER_UPDATE} algorithmic bytes per update x {U} updates per launch / "
+                              "march-kernel CUDA-event time"},
+        "e2e": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": ems},
+        "gpu_launches": 4 * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+        R, dt = run_oracle_sample(p, slice(0, len(p.sources)), ns)
+        line["cpu_baseline"] = {"value": U / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the whole step ({U} updates), FP64, 1 thread, {dt:.1f} s"}
+        F = out.double().cpu().numpy()
+        rel = [float(np.linalg.norm(F[b] - R[b]) / np.linalg.norm(R[b])) for b in range(p.n_freq)]
+        line["parity_vs_oracle"] = {"rel_l2_per_bin": rel}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (faster)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    return native_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * raytrax.h -- C ABI of the GB300 (sm_103a) emission-absorption ray march.
+ *
+ * The library implements the single-source kernel and its multi-source / multi-bin wrapper
+ * of the paper (Sec. 2, "Method and code structure" and "Frequency-bin agnosticism"):
+ * from every source, N_Omega rays on a Fibonacci (golden-angle) lattice march N_s substeps
+ * of Eq. 2,
+ *       x_{k+1} = x_k + n ds,  tau_{k+1} = tau_k + kappa(x_k) ds,
+ *       I_{k+1} = I_k exp(-kappa(x_k) ds) + j(x_k) exp(-tau_k) ds,
+ * with j read trilinearly at x_k, kappa read at the nearest cell of x_k, and I_{k+1}
+ * deposited back with the same trilinear weights, indices clamped to the box. Deposits are
+ * scaled by 4 pi / N_Omega and summed over rays, sources and substeps, per frequency bin.
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are float32, C-contiguous, shape [n_freq][n0][n1][n2]; bins are independent.
+ *   - Grid coordinates are node-centred: voxel (i0, i1, i2) sits at point (i0, i1, i2).
+ *     Component a of a position or direction indexes array axis a.
+ *   - Per axis, f = floor(x), corners clamp(f, 0, n-1) and clamp(f+1, 0, n-1), fraction
+ *     t = x - f (unclamped); a ray that leaves the box keeps marching and deposits on the
+ *     nearest boundary voxels.
+ *   - kappa cell: kappa_mode 0 = the clamped floor corner of x_k (default); kappa_mode 1 =
+ *     clamped floor(x_k + 1/2). The paper says only "nearest-neighbour at the cell index
+ *     used for the previous position".
+ *   - Lattice: z_i = 1 - (2i+1)/N, phi_i = i pi (3 - sqrt 5) mod 2 pi, n_i = (sqrt(1-z^2)
+ *     cos phi, sqrt(1-z^2) sin phi, z), computed in FP64 and rounded once to FP32.
+ *   - Geometry in IEEE FP32 without contraction: d = fl(n ds) once per ray,
+ *     x_{k+1} = fl(x_k + d), t = fl(x - floor x); so cell indices are reproducible.
+ *   - N_s = ceil(c dt / ds) evaluated in FP64 from the float arguments (relative guard
+ *     1e-9 against roundoff), then min(N_s, ns_cap) when ns_cap > 0.
+ *   - "device" pointers are CUDA global-memory pointers of the current device; every
+ *     device call is asynchronous on the given stream (NULL = legacy default stream).
+ *     The caller owns every data buffer; a handle owns only its scratch (direction
+ *     tables, packed inputs, accumulators, checkpoints), freed by rt_destroy.
+ *   - Errors found on the host return at once with nothing enqueued; the thread-local
+ *     message of rt_last_error() says which argument. CUDA launch or allocation failures
+ *     return RT_ERR_CUDA / RT_ERR_OOM. A handle may be used by one host thread at a time.
+ */
+#ifndef RAYTRAX_H
+#define RAYTRAX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_grid rt_grid;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,
+    RT_ERR_CUDA = 2,
+    RT_ERR_OOM = 3,
+    RT_ERR_TIMEOUT = 4,
+    RT_ERR_INTERNAL = 5,
+    RT_ERR_UNSUPPORTED = 6
+} rt_status;
+
+typedef struct {
+    int deterministic;  /* 0: FP32 atomic accumulation (default). 1: 64-bit fixed-point
+                           accumulation, bitwise identical for any launch order or split */
+    int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
+    int ns_cap;         /* 0: none; > 0: cap on the substep count (Sec. 2 "user cap") */
+    int autotune;       /* 1: time the launch shapes once per shape class and keep the best */
+    int ckpt_stride;    /* adjoint checkpoint stride K in substeps; 0: automatic */
+    int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
+                           call's stream, readable with rt_kernel_ms */
+} rt_options;
+
+/* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
+   no autotuning, automatic checkpoint stride). */
+void rt_default_options(rt_options* opt);
+
+/* Create a handle for grids of n0 x n1 x n2 voxels and up to max_freq bins.
+   n0, n1, n2 >= 1, max_freq >= 1, n_freq * n0 * n1 * n2 < 2^31; opt may be NULL (defaults).
+   Allocates nothing on the device until the first call that needs scratch.
+   *out receives the handle (NULL on error). */
+rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, const rt_options* opt);
+
+/* Free the handle and its scratch after synchronising the device. NULL is accepted. */
+rt_status rt_destroy(rt_grid* grid);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* N_s for (step_size, radiation_velocity, time_step) and a cap (<= 0: none), computed as
+   described above; -1 if step_size <= 0, radiation_velocity <= 0, time_step < 0, a value
+   is not finite or N_s would not fit in an int. Paper: Sec. 2 after Eq. 2; App. A. */
+int rt_num_substeps(float step_size, float radiation_velocity, float time_step, int ns_cap);
+
+/* Write the FP32 Fibonacci lattice (Sec. 2) used by the march, in lattice order, to the
+   HOST buffer out[num_rays][3]. num_rays >= 1. */
+rt_status rt_direction_table(int num_rays, float* out);
+
+/* One time step dt of the field (Sec. 2: the single-source kernel's arguments
+   (j_map, kappa_map, source_pos, num_rays, step_size, radiation_velocity, time_step),
+   looped over sources and batched over n_freq bins):
+     out_field[b] (+)= (4 pi / num_rays) sum_sources sum_rays sum_{k < N_s} W(x_k) I_{k+1}.
+   j_map, kappa_map, out_field: device [n_freq][n0][n1][n2] float32 (kappa >= 0 expected).
+   source_pos: device [num_sources][3] float32, grid coordinates, each |x| < 2^24.
+   num_sources >= 0 (0 gives a zero field), num_rays >= 1, step_size > 0,
+   radiation_velocity > 0, time_step >= 0, 1 <= n_freq <= max_freq.
+   accumulate = 0 overwrites out_field, 1 adds to it. out_field must not alias j_map or
+   kappa_map. Stream-ordered; the inputs must stay valid until the work completes. */
+rt_status rt_advance(rt_grid* grid, const float* j_map, const float* kappa_map,
+                     const float* source_pos, int num_sources, int num_rays,
+                     float step_size, float radiation_velocity, float time_step, int n_freq,
+                     float* out_field, int accumulate, void* cuda_stream);
+
+/* rt_advance restricted to the lattice directions ray_begin .. ray_end-1 (each still
+   weighted 4 pi / num_rays): the direction shard of Sec. 2 ("shard directions across
+   devices ... sum per shard before reducing across shards"). Shards that tile
+   [0, num_rays) sum to the rt_advance field. 0 <= ray_begin <= ray_end <= num_rays. */
+rt_status rt_advance_rays(rt_grid* grid, const float* j_map, const float* kappa_map,
+                          const float* source_pos, int num_sources, int num_rays,
+                          int ray_begin, int ray_end, float step_size, float radiation_velocity,
+                          float time_step, int n_freq, float* out_field, int accumulate,
+                          void* cuda_stream);
+
+/* rt_advance with HOST buffers (same shapes): copies the inputs to handle-owned device
+   scratch, runs the march on the given stream, copies the field back and synchronises
+   the stream before returning. Host buffers may be pageable; pinned ones copy faster. */
+rt_status rt_advance_host(rt_grid* grid, const float* j_map, const float* kappa_map,
+                          const float* source_pos, int num_sources, int num_rays,
+                          float step_size, float radiation_velocity, float time_step, int n_freq,
+                          float* out_field, void* cuda_stream);
+
+/* Reverse-mode adjoint of rt_advance (the Jacobians w.r.t. (j, kappa) of Sec. 4,
+   "Coupling to differentiable hydro"). Given grad_out = dL/d(out_field) (device,
+   [n_freq][n0][n1][n2]) and the forward's inputs, writes dL/dj to grad_j and dL/dkappa
+   to grad_kappa (device, same shape, OVERWRITTEN; either may be NULL to skip it).
+   Per ray, with a_k = exp(-kappa_k ds), E_k = exp(-tau_k), s = 4 pi / num_rays:
+     lam_{k+1} = s sum_c w_{k,c} G[c_{k,c}] + a_{k+1} lam_{k+2},
+     mu_k = mu_{k+1} + lam_{k+1} j_k E_k ds,
+     dj[c_{k,c}] += lam_{k+1} E_k ds w_{k,c},
+     dkappa[cell_k] += -ds (lam_{k+1} I_k a_k + mu_{k+1}).
+   The forward state is recomputed from per-ray checkpoints every ckpt_stride substeps
+   (never by dividing out exp(-kappa ds)). Not differentiable in source_pos, ds, c, dt. */
+rt_status rt_backward(rt_grid* grid, const float* grad_out, const float* j_map,
+                      const float* kappa_map, const float* source_pos, int num_sources,
+                      int num_rays, float step_size, float radiation_velocity, float time_step,
+                      int n_freq, float* grad_j, float* grad_kappa, void* cuda_stream);
+
+/* Duration in ms of the march kernel(s) of the last rt_advance / rt_backward call on this
+   handle (forward: the march kernel only, without packing or zeroing; backward: the adjoint
+   kernel). Needs rt_options.profile = 1; waits for that kernel to finish. */
+rt_status rt_kernel_ms(rt_grid* grid, float* ms);
+
+/* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
+   thread), threads per block, gather prefetch (0/1), and the march time the autotuner
+   measured for it in ms (-1 when rt_options.autotune is 0). Any pointer may be NULL.
+   With autotune = 1, the first call of each shape class (n_freq, num_sources, rays, N_s)
+   times every candidate plan on its own inputs before running; it synchronises the stream. */
+rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, float* tuned_ms);
+
+/* Text of the last autotuning pass on this handle: one line per candidate plan with its best
+   march time ("W=4 block=64 prefetch=1 0.5123 ms"), copied NUL-terminated into the HOST
+   buffer buf of len bytes (truncated if needed; "" if the handle never tuned). */
+rt_status rt_tuning_report(rt_grid* grid, char* buf, int len);
+
+/* Test hook: per-substep cell indices of lattice ray `ray` from the HOST position src[3]
+   on this handle's grid, computed on the device by the march's own geometry code.
+   base_cell[k] = flat index of the clamped floor corner of x_k; kappa_cell[k] = flat index
+   of the kappa cell (rt_options.kappa_mode). Host outputs of num_steps entries each.
+   Synchronous. */
+rt_status rt_trace_cells(rt_grid* grid, const float* src, int num_rays, int ray, float step_size,
+                         int num_steps, long long* base_cell, long long* kappa_cell);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAYTRAX_H */

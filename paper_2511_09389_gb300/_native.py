@@ -1,0 +1,91 @@
+"""ctypes loader for the in-tree CUDA library ``librt_gb300.so`` (C ABI of include/raytrax.h).
+
+There is no fallback: if the library is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librt_gb300.so")
+
+RT_OK = 0
+STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM",
+                4: "RT_ERR_TIMEOUT", 5: "RT_ERR_INTERNAL", 6: "RT_ERR_UNSUPPORTED"}
+
+# every symbol include/raytrax.h declares
+EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
+           "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
+           "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
+           "rt_tuning_report")
+
+
+class RTError(RuntimeError):
+    """A non-zero rt_status, with the library's thread-local message."""
+
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+class rt_options(ctypes.Structure):
+    _fields_ = [("deterministic", ctypes.c_int), ("kappa_mode", ctypes.c_int), ("ns_cap", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once) and declare the argument types of every export."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                              "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, fp, i, f = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        lib.rt_default_options.argtypes = [ctypes.POINTER(rt_options)]
+        lib.rt_default_options.restype = None
+        lib.rt_create_grid.argtypes = [ctypes.POINTER(vp), i, i, i, i, ctypes.POINTER(rt_options)]
+        lib.rt_create_grid.restype = i
+        lib.rt_destroy.argtypes = [vp]
+        lib.rt_destroy.restype = i
+        lib.rt_last_error.argtypes = []
+        lib.rt_last_error.restype = ctypes.c_char_p
+        lib.rt_num_substeps.argtypes = [f, f, f, i]
+        lib.rt_num_substeps.restype = i
+        lib.rt_direction_table.argtypes = [i, fp]
+        lib.rt_direction_table.restype = i
+        lib.rt_advance.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, i, vp]
+        lib.rt_advance.restype = i
+        lib.rt_advance_rays.argtypes = [vp, fp, fp, fp, i, i, i, i, f, f, f, i, fp, i, vp]
+        lib.rt_advance_rays.restype = i
+        lib.rt_advance_host.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, vp]
+        lib.rt_advance_host.restype = i
+        lib.rt_backward.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, vp]
+        lib.rt_backward.restype = i
+        lib.rt_trace_cells.argtypes = [vp, fp, i, i, f, i, llp, llp]
+        lib.rt_trace_cells.restype = i
+        lib.rt_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        lib.rt_kernel_ms.restype = i
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.rt_last_plan.argtypes = [vp, ip, ip, ip, ctypes.POINTER(ctypes.c_float)]
+        lib.rt_last_plan.restype = i
+        lib.rt_tuning_report.argtypes = [vp, ctypes.c_char_p, i]
+        lib.rt_tuning_report.restype = i
+        _lib = lib
+        return lib
+
+
+def check(status: int) -> None:
+    if status != RT_OK:
+        msg = _lib.rt_last_error().decode() if _lib is not None else ""
+        raise RTError(status, msg)

@@ -1,0 +1,238 @@
+"""Python binding of the C ABI (include/raytrax.h): argument marshalling only.
+
+PyTorch supplies device memory and streams; every step of the march runs in the CUDA
+library. Tensors are float32, C-contiguous, shape [n_freq, n0, n1, n2] (a 3-D grid is one
+bin); source positions are [n_src, 3] grid coordinates. Calls are asynchronous on the
+current torch stream unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import RTError, check
+
+
+def _stream_ptr(stream, device) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return int(s.cuda_stream)
+
+
+def _grid_tensor(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if t.dim() == 3:
+        t = t.unsqueeze(0)
+    if t.dim() != 4:
+        raise ValueError(f"{name} must be [n_freq, n0, n1, n2] or [n0, n1, n2]")
+    return t.contiguous()
+
+
+def num_substeps(step_size: float, radiation_velocity: float, time_step: float, cap: int = 0) -> int:
+    """N_s = ceil(c dt / ds) (or the cap), as the library computes it."""
+    n = _native.load().rt_num_substeps(float(step_size), float(radiation_velocity), float(time_step), int(cap))
+    if n < 0:
+        raise ValueError("invalid step_size / radiation_velocity / time_step")
+    return n
+
+
+def direction_table(num_rays: int) -> np.ndarray:
+    """The library's FP32 Fibonacci lattice in lattice order, [num_rays, 3]."""
+    out = np.empty((num_rays, 3), np.float32)
+    check(_native.load().rt_direction_table(int(num_rays), out.ctypes.data))
+    return out
+
+
+class Grid:
+    """A library handle for one grid shape (owns its scratch on one device)."""
+
+    def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
+                 ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
+                 device=None):
+        self._lib = _native.load()
+        self.shape = tuple(int(s) for s in shape)
+        if len(self.shape) != 3:
+            raise ValueError("shape must be (n0, n1, n2)")
+        self.max_freq = int(max_freq)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
+                                 int(ckpt_stride), int(bool(profile)))
+        self.options = opt
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._lib.rt_create_grid(ctypes.byref(h), *self.shape, self.max_freq, ctypes.byref(opt)))
+        self._h = h
+
+    # -- lifetime -------------------------------------------------------------------------
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            with torch.cuda.device(self.device):
+                self._lib.rt_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers --------------------------------------------------------------------------
+    def _inputs(self, j, kappa, sources):
+        j = _grid_tensor(j, "j")
+        kappa = _grid_tensor(kappa, "kappa")
+        if j.shape != kappa.shape:
+            raise ValueError("j and kappa must have the same shape")
+        if tuple(j.shape[1:]) != self.shape:
+            raise ValueError(f"grid shape {tuple(j.shape[1:])} differs from the handle's {self.shape}")
+        if j.device != self.device or kappa.device != self.device:
+            raise ValueError(f"tensors must live on {self.device}")
+        src = torch.as_tensor(sources, dtype=torch.float32, device=self.device).reshape(-1, 3).contiguous()
+        return j, kappa, src
+
+    # -- forward --------------------------------------------------------------------------
+    def advance(self, j, kappa, sources, num_rays: int, step_size: float, radiation_velocity: float = 1.0,
+                time_step: float = 1.0, *, out=None, accumulate: bool = False, ray_range=None,
+                stream=None) -> torch.Tensor:
+        """One dt of the field: out[b] (+)= (4 pi / N_Omega) sum_src sum_rays sum_k W(x_k) I_{k+1}."""
+        j, kappa, src = self._inputs(j, kappa, sources)
+        nf = j.shape[0]
+        if out is None:
+            out = torch.empty_like(j)
+            accumulate = False
+        elif out.shape != j.shape or out.dtype != torch.float32 or not out.is_contiguous() \
+                or out.device != self.device:
+            raise ValueError("out must be a contiguous float32 tensor shaped like j on the handle's device")
+        sp = _stream_ptr(stream, self.device)
+        with torch.cuda.device(self.device):
+            if ray_range is None:
+                st = self._lib.rt_advance(self._h, j.data_ptr(), kappa.data_ptr(), src.data_ptr(), src.shape[0],
+                                          int(num_rays), float(step_size), float(radiation_velocity),
+                                          float(time_step), nf, out.data_ptr(), int(bool(accumulate)), sp)
+            else:
+                rb, re = ray_range
+                st = self._lib.rt_advance_rays(self._h, j.data_ptr(), kappa.data_ptr(), src.data_ptr(),
+                                               src.shape[0], int(num_rays), int(rb), int(re), float(step_size),
+                                               float(radiation_velocity), float(time_step), nf, out.data_ptr(),
+                                               int(bool(accumulate)), sp)
+        check(st)
+        return out
+
+    def advance_host(self, j: np.ndarray, kappa: np.ndarray, sources: np.ndarray, num_rays: int,
+                     step_size: float, radiation_velocity: float = 1.0, time_step: float = 1.0, *,
+                     out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """rt_advance_host: host (numpy / pinned torch CPU) buffers in, host field out, synchronous."""
+        def host(a, name):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous float32 CPU tensor")
+                return a, a.data_ptr(), tuple(a.shape)
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            return a, a.ctypes.data, a.shape
+        jh, jp, jshape = host(j, "j")
+        kh, kp, kshape = host(kappa, "kappa")
+        sh, spp, sshape = host(sources, "sources")
+        if len(jshape) == 3:
+            jshape = (1,) + tuple(jshape)
+        if tuple(jshape) != tuple(kshape if len(kshape) == 4 else (1,) + tuple(kshape)) or tuple(jshape[1:]) != self.shape:
+            raise ValueError("j / kappa shapes do not match the handle")
+        nsrc = int(np.prod(sshape)) // 3
+        if out is None:
+            out = np.empty(jshape, np.float32)
+        oh, op, oshape = host(out, "out")
+        if tuple(oshape) != tuple(jshape):
+            raise ValueError("out has the wrong shape")
+        with torch.cuda.device(self.device):
+            st = self._lib.rt_advance_host(self._h, jp, kp, spp, nsrc, int(num_rays), float(step_size),
+                                           float(radiation_velocity), float(time_step), jshape[0], op,
+                                           _stream_ptr(stream, self.device))
+        check(st)
+        return oh
+
+    # -- adjoint --------------------------------------------------------------------------
+    def backward(self, grad_out, j, kappa, sources, num_rays: int, step_size: float,
+                 radiation_velocity: float = 1.0, time_step: float = 1.0, *, need_j: bool = True,
+                 need_kappa: bool = True, stream=None):
+        """(dL/dj, dL/dkappa) for G = dL/d(out) of :meth:`advance` (either may be None if not needed)."""
+        j, kappa, src = self._inputs(j, kappa, sources)
+        g = _grid_tensor(grad_out, "grad_out")
+        if g.shape != j.shape or g.device != self.device:
+            raise ValueError("grad_out must be shaped like j on the handle's device")
+        gj = torch.empty_like(j) if need_j else None
+        gk = torch.empty_like(j) if need_kappa else None
+        with torch.cuda.device(self.device):
+            st = self._lib.rt_backward(self._h, g.data_ptr(), j.data_ptr(), kappa.data_ptr(), src.data_ptr(),
+                                       src.shape[0], int(num_rays), float(step_size), float(radiation_velocity),
+                                       float(time_step), j.shape[0], gj.data_ptr() if gj is not None else None,
+                                       gk.data_ptr() if gk is not None else None,
+                                       _stream_ptr(stream, self.device))
+        check(st)
+        return gj, gk
+
+    def kernel_ms(self) -> float:
+        """Duration of the last call's march kernel (needs profile=True)."""
+        ms = ctypes.c_float()
+        check(self._lib.rt_kernel_ms(self._h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def last_plan(self) -> dict:
+        """Launch plan of the last forward call (width, block, prefetch, tuned_ms)."""
+        w, b, p, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(self._lib.rt_last_plan(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(p), ctypes.byref(t)))
+        return {"width": w.value, "block": b.value, "prefetch": p.value, "tuned_ms": t.value}
+
+    def tuning_report(self) -> str:
+        """Candidates and times of the last autotuning pass ("" if none)."""
+        buf = ctypes.create_string_buffer(8192)
+        check(self._lib.rt_tuning_report(self._h, buf, len(buf)))
+        return buf.value.decode()
+
+    # -- test hook ------------------------------------------------------------------------
+    def trace_cells(self, source, num_rays: int, ray: int, step_size: float, num_steps: int):
+        """Per-substep (base corner, kappa cell) flat indices of one lattice ray, from the device."""
+        src = np.ascontiguousarray(np.asarray(source, np.float32).reshape(3))
+        base = np.zeros(num_steps, np.int64)
+        nn = np.zeros(num_steps, np.int64)
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        with torch.cuda.device(self.device):
+            st = self._lib.rt_trace_cells(self._h, src.ctypes.data, int(num_rays), int(ray), float(step_size),
+                                          int(num_steps), base.ctypes.data_as(llp), nn.ctypes.data_as(llp))
+        check(st)
+        return base, nn
+
+
+_grid_cache: dict = {}
+
+
+def _cached_grid(shape, n_freq, device, **opts) -> Grid:
+    key = (tuple(shape), int(device.index), tuple(sorted(opts.items())))
+    g = _grid_cache.get(key)
+    if g is None or g.max_freq < n_freq:
+        g = Grid(shape, max(8, n_freq), device=device, **opts)
+        _grid_cache[key] = g
+    return g
+
+
+def advance(j, kappa, sources, num_rays: int, step_size: float, radiation_velocity: float = 1.0,
+            time_step: float = 1.0, **opts) -> torch.Tensor:
+    """Functional form of :meth:`Grid.advance` with a cached handle per (shape, device, options)."""
+    jj = _grid_tensor(j, "j")
+    g = _cached_grid(jj.shape[1:], jj.shape[0], jj.device, **opts)
+    out = g.advance(jj, kappa, sources, num_rays, step_size, radiation_velocity, time_step)
+    return out if j.dim() == 4 else out[0]
+
+
+__all__ = ["Grid", "advance", "num_substeps", "direction_table", "RTError"]

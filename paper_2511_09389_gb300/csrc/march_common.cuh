@@ -1,0 +1,128 @@
+// march_common.cuh -- device building blocks of the emission-absorption march (sm_103a).
+//
+// Geometry (paper Sec. 2): node-centred grid, per axis f = floor(x), corners
+// clamp(f, 0, n-1) / clamp(f+1, 0, n-1), fraction t = x - f; kappa at the nearest cell of the
+// previous position x_k. All geometry uses explicit round-to-nearest FP32 intrinsics so the
+// compiler cannot contract or reorder it: the cell sequence of a ray is a pure function of
+// (source, direction, ds) and identical in every kernel of this library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rt {
+
+constexpr float kFourPi = 12.566370614359172f;
+
+// Clamped corner pair and fraction along one axis.
+struct Axis {
+    int lo, hi;   // clamped floor corner and clamped floor+1 corner
+    float t;      // x - floor(x), not clamped
+};
+
+__device__ __forceinline__ Axis axis_sample(float x, int n) {
+    Axis a;
+    const float f = floorf(x);
+    a.t = __fsub_rn(x, f);
+    // clamp in float first so the conversion never leaves the int range
+    const int fi = __float2int_rz(fminf(fmaxf(f, -1.0f), (float)(n - 1)));
+    a.lo = max(fi, 0);
+    a.hi = min(fi + 1, n - 1);
+    return a;
+}
+
+__device__ __forceinline__ int nearest_round(float x, int n) {
+    const float f = floorf(__fadd_rn(x, 0.5f));
+    return __float2int_rz(fminf(fmaxf(f, 0.0f), (float)(n - 1)));
+}
+
+// The eight trilinear corners of x_k and its kappa cell. Corner c has bits (b0 b1 b2) =
+// (c >> 2, c >> 1, c) & 1 selecting hi along axes 0, 1, 2.
+struct Sample {
+    int cell[8];
+    float w[8];
+    int nn;
+};
+
+__device__ __forceinline__ void make_sample(float x0, float x1, float x2, int n0, int n1, int n2,
+                                            int kappa_mode, Sample& s) {
+    const Axis a0 = axis_sample(x0, n0), a1 = axis_sample(x1, n1), a2 = axis_sample(x2, n2);
+    const int r00 = (a0.lo * n1 + a1.lo) * n2, r01 = (a0.lo * n1 + a1.hi) * n2;
+    const int r10 = (a0.hi * n1 + a1.lo) * n2, r11 = (a0.hi * n1 + a1.hi) * n2;
+    s.cell[0] = r00 + a2.lo; s.cell[1] = r00 + a2.hi;
+    s.cell[2] = r01 + a2.lo; s.cell[3] = r01 + a2.hi;
+    s.cell[4] = r10 + a2.lo; s.cell[5] = r10 + a2.hi;
+    s.cell[6] = r11 + a2.lo; s.cell[7] = r11 + a2.hi;
+    const float u0 = 1.0f - a0.t, u1 = 1.0f - a1.t, u2 = 1.0f - a2.t;
+    const float w00 = u0 * u1, w01 = u0 * a1.t, w10 = a0.t * u1, w11 = a0.t * a1.t;
+    s.w[0] = w00 * u2; s.w[1] = w00 * a2.t;
+    s.w[2] = w01 * u2; s.w[3] = w01 * a2.t;
+    s.w[4] = w10 * u2; s.w[5] = w10 * a2.t;
+    s.w[6] = w11 * u2; s.w[7] = w11 * a2.t;
+    if (kappa_mode == 0) {
+        s.nn = s.cell[0];
+    } else {
+        s.nn = (nearest_round(x0, n0) * n1 + nearest_round(x1, n1)) * n2 + nearest_round(x2, n2);
+    }
+}
+
+// ---- W-wide bin vectors -----------------------------------------------------------------
+template <int W> struct Vec;
+template <> struct Vec<1> { float v[1]; };
+template <> struct Vec<2> { float v[2]; };
+template <> struct Vec<4> { float v[4]; };
+
+template <int W>
+__device__ __forceinline__ Vec<W> ldg_vec(const float* __restrict__ p, int cell);
+
+template <>
+__device__ __forceinline__ Vec<1> ldg_vec<1>(const float* __restrict__ p, int cell) {
+    Vec<1> r; r.v[0] = __ldg(p + cell); return r;
+}
+template <>
+__device__ __forceinline__ Vec<2> ldg_vec<2>(const float* __restrict__ p, int cell) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p) + cell);
+    Vec<2> r; r.v[0] = q.x; r.v[1] = q.y; return r;
+}
+template <>
+__device__ __forceinline__ Vec<4> ldg_vec<4>(const float* __restrict__ p, int cell) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + cell);
+    Vec<4> r; r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w; return r;
+}
+
+// Fire-and-forget global reductions (no return value): one L2 atomic per W-vector. They carry
+// no "memory" clobber: the accumulators they target are never read by the kernels that issue
+// them, so loads of the read-only inputs may be scheduled across them; kernel completion
+// orders them before any later reader.
+__device__ __forceinline__ void red_add(float* p, float a) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a));
+}
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b));
+}
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(d));
+}
+
+template <int W>
+__device__ __forceinline__ void red_vec(float* __restrict__ base, int cell, const float* v);
+template <>
+__device__ __forceinline__ void red_vec<1>(float* __restrict__ base, int cell, const float* v) {
+    red_add(base + cell, v[0]);
+}
+template <>
+__device__ __forceinline__ void red_vec<2>(float* __restrict__ base, int cell, const float* v) {
+    red_add2(base + 2 * (size_t)cell, v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void red_vec<4>(float* __restrict__ base, int cell, const float* v) {
+    red_add4(base + 4 * (size_t)cell, v[0], v[1], v[2], v[3]);
+}
+
+// 64-bit integer reduction for the deterministic (fixed-point) accumulation mode.
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long a) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(a));
+}
+
+}  // namespace rt

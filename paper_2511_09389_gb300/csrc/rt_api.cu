@@ -1,0 +1,576 @@
+// rt_api.cu -- host side of the C ABI declared in include/raytrax.h.
+//
+// Validation, the substep rule, the Fibonacci lattice (built in FP64 on the host, rounded to
+// FP32 and sorted into angular patches), handle-owned scratch, and the dispatch of the march
+// kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "raytrax.h"
+#include "rt_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rt_status fail(rt_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+rt_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(RT_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(RT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RT_CUDA(call, what)                             \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---- Fibonacci lattice (Sec. 2) ------------------------------------------------------------
+// n_i = (rho cos phi, rho sin phi, z), z = 1 - (2i+1)/N, rho = sqrt(1 - z^2),
+// phi = i * pi (3 - sqrt 5) mod 2 pi, in FP64, each component rounded once to FP32.
+void lattice_entry(int i, int n, float out[3]) {
+    const double pi = 3.14159265358979323846;
+    const double golden = pi * (3.0 - std::sqrt(5.0));
+    const double z = 1.0 - (2.0 * i + 1.0) / (double)n;
+    const double rho = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+    const double phi = std::fmod((double)i * golden, 2.0 * pi);
+    out[0] = (float)(rho * std::cos(phi));
+    out[1] = (float)(rho * std::sin(phi));
+    out[2] = (float)z;
+}
+
+// Sort key grouping angular neighbours: cube face of the direction, then a Morton code of the
+// two minor components over that face. Consecutive keys form compact patches on the sphere,
+// so a warp's rays start out sharing cells near the source.
+uint32_t spread10(uint32_t v) {
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000ff;
+    v = (v | (v << 8)) & 0x0300f00f;
+    v = (v | (v << 4)) & 0x030c30c3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+}
+
+uint32_t angular_key(const float d[3]) {
+    const float ax = std::fabs(d[0]), ay = std::fabs(d[1]), az = std::fabs(d[2]);
+    int major;
+    if (ax >= ay && ax >= az) major = 0;
+    else if (ay >= az) major = 1;
+    else major = 2;
+    const float m = std::fmax(std::fabs(d[major]), 1e-30f);
+    const int u_ax = (major + 1) % 3, v_ax = (major + 2) % 3;
+    const float u = d[u_ax] / m, v = d[v_ax] / m;
+    auto q = [](float s) {
+        int k = (int)std::floor((s + 1.0f) * 512.0f);
+        return (uint32_t)std::min(std::max(k, 0), 1023);
+    };
+    const uint32_t face = (uint32_t)(2 * major + (d[major] < 0.0f ? 1 : 0));
+    return (face << 20) | (spread10(q(u)) << 1) | spread10(q(v));
+}
+
+struct DirTable {
+    int n = 0, begin = 0, end = 0;
+    float4* d = nullptr;
+};
+
+// Launch plan of the forward march: bin-group width, threads per block, gather prefetch.
+struct Plan {
+    int W = 1, block = 64, prefetch = 1;
+};
+
+}  // namespace
+
+struct rt_grid {
+    int n0 = 0, n1 = 0, n2 = 0, max_freq = 0;
+    rt_options opt{};
+    int device = 0;
+    std::vector<DirTable> dirs;
+    // scratch slots
+    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, NSLOT };
+    void* buf[NSLOT] = {};
+    size_t cap[NSLOT] = {};
+    // profiling events around the last march kernel
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool ev_valid = false;
+    // autotuning cache: shape class -> fastest launch plan
+    struct TuneKey {
+        int n_freq, nsrc, rays, ns;
+        bool operator==(const TuneKey& o) const {
+            return n_freq == o.n_freq && nsrc == o.nsrc && rays == o.rays && ns == o.ns;
+        }
+    };
+    std::vector<std::pair<TuneKey, std::pair<Plan, float>>> tuned;
+    Plan last_plan;
+    float last_plan_ms = -1.0f;
+    std::string tune_report;   // candidates timed by the last autotuning pass
+
+    rt_status mark(int which, cudaStream_t st) {
+        if (!opt.profile) return RT_OK;
+        if (!ev[which]) RT_CUDA(cudaEventCreate(&ev[which]), "cudaEventCreate");
+        RT_CUDA(cudaEventRecord(ev[which], st), "cudaEventRecord");
+        ev_valid = which == 1;
+        return RT_OK;
+    }
+
+    long long ncell() const { return (long long)n0 * n1 * n2; }
+
+    rt_status ensure(Slot s, size_t bytes, void** out) {
+        if (bytes == 0) bytes = 16;
+        if (cap[s] < bytes) {
+            if (buf[s]) {
+                cudaError_t e = cudaFree(buf[s]);
+                buf[s] = nullptr;
+                cap[s] = 0;
+                if (e != cudaSuccess) return cuda_fail(e, "cudaFree(scratch)");
+            }
+            cudaError_t e = cudaMalloc(&buf[s], bytes);
+            if (e != cudaSuccess) {
+                buf[s] = nullptr;
+                return cuda_fail(e, "cudaMalloc(scratch)");
+            }
+            cap[s] = bytes;
+        }
+        *out = buf[s];
+        return RT_OK;
+    }
+
+    // Direction table of lattice rays [begin, end) of an N-ray lattice, sorted by angular_key.
+    rt_status table(int n, int begin, int end, const float4** out) {
+        for (auto& t : dirs)
+            if (t.n == n && t.begin == begin && t.end == end) { *out = t.d; return RT_OK; }
+        const int cnt = end - begin;
+        std::vector<float> xyz(3 * (size_t)cnt);
+        std::vector<uint32_t> key(cnt);
+        std::vector<int> order(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            lattice_entry(begin + i, n, &xyz[3 * (size_t)i]);
+            key[i] = angular_key(&xyz[3 * (size_t)i]);
+        }
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+        std::vector<float4> host(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            const float* p = &xyz[3 * (size_t)order[i]];
+            host[i] = make_float4(p[0], p[1], p[2], 0.0f);
+        }
+        DirTable t;
+        t.n = n; t.begin = begin; t.end = end;
+        RT_CUDA(cudaMalloc(&t.d, sizeof(float4) * (size_t)std::max(cnt, 1)), "cudaMalloc(directions)");
+        cudaError_t e = cudaMemcpy(t.d, host.data(), sizeof(float4) * (size_t)cnt, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(t.d); return cuda_fail(e, "cudaMemcpy(directions)"); }
+        if (dirs.size() >= 16) {
+            cudaFree(dirs.front().d);
+            dirs.erase(dirs.begin());
+        }
+        dirs.push_back(t);
+        *out = t.d;
+        return RT_OK;
+    }
+
+    void release() {
+        cudaDeviceSynchronize();
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto& t : dirs) cudaFree(t.d);
+        dirs.clear();
+        for (int s = 0; s < NSLOT; ++s) {
+            if (buf[s]) cudaFree(buf[s]);
+            buf[s] = nullptr;
+            cap[s] = 0;
+        }
+    }
+};
+
+namespace {
+
+int num_substeps(float ds, float c, float dt, int cap) {
+    if (!std::isfinite(ds) || !std::isfinite(c) || !std::isfinite(dt)) return -1;
+    if (!(ds > 0.0f) || !(c > 0.0f) || !(dt >= 0.0f)) return -1;
+    const double q = (double)c * (double)dt / (double)ds;
+    const double n = std::ceil(q - 1e-9 * q);
+    if (!(n <= 2147483647.0)) return -1;
+    int ns = n < 0.0 ? 0 : (int)n;
+    if (cap > 0 && ns > cap) ns = cap;
+    return ns;
+}
+
+rt_status check_device(rt_grid* g) {
+    int dev = -1;
+    RT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != g->device)
+        return fail(RT_ERR_INVALID_ARG, "current device %d differs from the handle's device %d", dev, g->device);
+    return RT_OK;
+}
+
+struct Call {
+    const float* j; const float* kappa; const float* src;
+    int nsrc, num_rays, ray_begin, ray_end;
+    float ds, c, dt;
+    int n_freq;
+    float* out;
+    int accumulate;
+    cudaStream_t st;
+};
+
+rt_status validate(rt_grid* g, const Call& a, int* ns_out) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (a.n_freq < 1 || a.n_freq > g->max_freq)
+        return fail(RT_ERR_INVALID_ARG, "n_freq = %d outside [1, max_freq = %d]", a.n_freq, g->max_freq);
+    if (a.num_rays < 1) return fail(RT_ERR_INVALID_ARG, "num_rays = %d must be >= 1", a.num_rays);
+    if (a.nsrc < 0) return fail(RT_ERR_INVALID_ARG, "num_sources = %d must be >= 0", a.nsrc);
+    if (a.ray_begin < 0 || a.ray_end > a.num_rays || a.ray_begin > a.ray_end)
+        return fail(RT_ERR_INVALID_ARG, "ray range [%d, %d) not inside [0, %d)", a.ray_begin, a.ray_end,
+                    a.num_rays);
+    if (!(a.ds > 0.0f) || !std::isfinite(a.ds))
+        return fail(RT_ERR_INVALID_ARG, "step_size must be finite and > 0");
+    if (!(a.c > 0.0f) || !std::isfinite(a.c))
+        return fail(RT_ERR_INVALID_ARG, "radiation_velocity must be finite and > 0");
+    if (!(a.dt >= 0.0f) || !std::isfinite(a.dt))
+        return fail(RT_ERR_INVALID_ARG, "time_step must be finite and >= 0");
+    const int ns = num_substeps(a.ds, a.c, a.dt, g->opt.ns_cap);
+    if (ns < 0) return fail(RT_ERR_INVALID_ARG, "substep count c*dt/ds does not fit in an int");
+    if ((double)ns * a.ds > 1.6e7)
+        return fail(RT_ERR_INVALID_ARG, "ray length N_s*ds = %g exceeds 1.6e7 cells", (double)ns * a.ds);
+    if (!a.j || !a.kappa || !a.out) return fail(RT_ERR_INVALID_ARG, "j_map, kappa_map and out_field must be non-NULL");
+    if (a.nsrc > 0 && !a.src) return fail(RT_ERR_INVALID_ARG, "source_pos is NULL");
+    if (a.out == a.j || a.out == a.kappa) return fail(RT_ERR_INVALID_ARG, "out_field aliases an input");
+    *ns_out = ns;
+    return RT_OK;
+}
+
+// Default bin-group width W: one bin needs no repacking; wider groups share the geometry.
+int pick_width(int n_freq) {
+    if (n_freq == 1) return 1;
+    if (n_freq == 2) return 2;
+    return 4;
+}
+
+// Lay out the inputs for bin-group width W (packing for W > 1) and fill the march arguments.
+// The accumulator is `out` itself for W = 1 with an output, else the handle's scratch.
+rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const float4* dirs, float scale,
+                  float* out, rt::MarchArgs* m) {
+    rt_status st;
+    const long long ncell = g->ncell();
+    *m = rt::MarchArgs{};
+    m->dirs = dirs;
+    m->src = a.src;
+    m->n0 = g->n0; m->n1 = g->n1; m->n2 = g->n2;
+    m->ns = ns;
+    m->ds = a.ds;
+    m->ray_count = a.ray_end - a.ray_begin;
+    m->nsrc = a.nsrc;
+    m->n_freq = a.n_freq;
+    m->kappa_mode = g->opt.kappa_mode;
+    m->block = plan.block;
+    m->prefetch = plan.prefetch;
+    if (plan.W == 1) {
+        float* acc = out;
+        if (!acc) {
+            void* p;
+            if ((st = g->ensure(rt_grid::ACC, sizeof(float) * (size_t)a.n_freq * ncell, &p)) != RT_OK) return st;
+            acc = (float*)p;
+        }
+        m->jp = a.j; m->kp = a.kappa; m->acc = acc;
+        m->groups = a.n_freq;
+        m->dep_scale = scale;
+        return RT_OK;
+    }
+    const int W = plan.W, groups = (a.n_freq + W - 1) / W;
+    const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
+    void *jp, *kp, *acc;
+    if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::ACC, packed, &acc)) != RT_OK) return st;
+    RT_CUDA(rt::launch_pack(a.j, (float*)jp, a.n_freq, W, groups, ncell, a.st), "pack(j) launch");
+    RT_CUDA(rt::launch_pack(a.kappa, (float*)kp, a.n_freq, W, groups, ncell, a.st), "pack(kappa) launch");
+    m->jp = (const float*)jp; m->kp = (const float*)kp; m->acc = (float*)acc;
+    m->groups = groups;
+    m->dep_scale = 1.0f;
+    return RT_OK;
+}
+
+size_t acc_bytes(const rt_grid* g, const Call& a, const Plan& plan) {
+    const int groups = (a.n_freq + plan.W - 1) / plan.W;
+    return sizeof(float) * (size_t)groups * g->ncell() * plan.W;
+}
+
+// Autotuner: on the first call of a shape class, time every candidate plan's march kernel on
+// the call's own inputs (into scratch; best of two runs each) and keep the fastest.
+rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scale, Plan* best) {
+    const rt_grid::TuneKey key{a.n_freq, a.nsrc, a.ray_end - a.ray_begin, ns};
+    for (const auto& e : g->tuned)
+        if (e.first == key) {
+            *best = e.second.first;
+            g->last_plan_ms = e.second.second;
+            return RT_OK;
+        }
+    std::vector<int> widths{pick_width(a.n_freq)};
+    if (a.n_freq >= 3) widths.push_back(2);
+    if (a.n_freq >= 2) widths.push_back(1);
+    const int blocks[] = {32, 64, 128, 256};
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    float best_ms = 3.0e38f;
+    Plan bp;
+    bp.W = widths[0];
+    g->tune_report.clear();
+    rt_status st = RT_OK;
+    cudaError_t ce = cudaEventCreate(&e[0]);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e[1]);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventCreate");
+    for (int W : widths) {
+        for (int b : blocks) {
+            for (int pf = 0; pf < 2; ++pf) {
+                if (st != RT_OK) break;
+                Plan p;
+                p.W = W; p.block = b; p.prefetch = pf;
+                rt::MarchArgs m;
+                if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
+                float cand_ms = 3.0e38f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    ce = cudaMemsetAsync(m.acc, 0, acc_bytes(g, a, p), a.st);
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e[0], a.st);
+                    if (ce == cudaSuccess) ce = rt::launch_march_fwd(W, m, a.st);
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e[1], a.st);
+                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
+                    float ms = 0.0f;
+                    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[0], e[1]);
+                    if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune run"); break; }
+                    if (ms < cand_ms) cand_ms = ms;
+                    if (ms < best_ms) { best_ms = ms; bp = p; }
+                }
+                if (st == RT_OK) {
+                    char line[96];
+                    snprintf(line, sizeof line, "W=%d block=%d prefetch=%d %.4f ms\n", W, b, pf, cand_ms);
+                    g->tune_report += line;
+                }
+            }
+        }
+    }
+    for (auto ev : e)
+        if (ev) cudaEventDestroy(ev);
+    if (st != RT_OK) return st;
+    if (g->tuned.size() >= 64) g->tuned.erase(g->tuned.begin());
+    g->tuned.push_back({key, {bp, best_ms}});
+    *best = bp;
+    g->last_plan_ms = best_ms;
+    return RT_OK;
+}
+
+rt_status advance_impl(rt_grid* g, const Call& a) {
+    int ns = 0;
+    rt_status st = validate(g, a, &ns);
+    if (st != RT_OK) return st;
+    if ((st = check_device(g)) != RT_OK) return st;
+    const long long ncell = g->ncell();
+    const size_t field_bytes = sizeof(float) * (size_t)a.n_freq * ncell;
+    const int count = a.ray_end - a.ray_begin;
+    if (ns == 0 || a.nsrc == 0 || count == 0) {
+        if (!a.accumulate) RT_CUDA(cudaMemsetAsync(a.out, 0, field_bytes, a.st), "cudaMemsetAsync(out)");
+        return RT_OK;
+    }
+    if (g->opt.deterministic) return fail(RT_ERR_UNSUPPORTED, "deterministic mode is not available yet");
+
+    const float4* dirs = nullptr;
+    if ((st = g->table(a.num_rays, a.ray_begin, a.ray_end, &dirs)) != RT_OK) return st;
+    const float scale = (float)(4.0 * 3.14159265358979323846 / (double)a.num_rays);
+
+    // default plan (measured on GB300): 32-thread blocks; gather prefetch only pays for one bin
+    Plan plan;
+    plan.W = pick_width(a.n_freq);
+    plan.block = 32;
+    plan.prefetch = plan.W == 1 ? 1 : 0;
+    g->last_plan_ms = -1.0f;
+    if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
+    g->last_plan = plan;
+
+    rt::MarchArgs m;
+    if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
+    if (plan.W > 1 || !a.accumulate)
+        RT_CUDA(cudaMemsetAsync(m.acc, 0, plan.W == 1 ? field_bytes : acc_bytes(g, a, plan), a.st),
+                "cudaMemsetAsync(accumulator)");
+    if ((st = g->mark(0, a.st)) != RT_OK) return st;
+    RT_CUDA(rt::launch_march_fwd(plan.W, m, a.st), "march kernel launch");
+    if ((st = g->mark(1, a.st)) != RT_OK) return st;
+    if (plan.W > 1)
+        RT_CUDA(rt::launch_unpack(m.acc, a.out, a.n_freq, plan.W, ncell, scale, a.accumulate, a.st),
+                "unpack launch");
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rt_default_options(rt_options* opt) {
+    if (opt) std::memset(opt, 0, sizeof(*opt));
+}
+
+rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, const rt_options* opt) {
+    if (!out) return fail(RT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n0 < 1 || n1 < 1 || n2 < 1) return fail(RT_ERR_INVALID_ARG, "grid extents must be >= 1");
+    if (max_freq < 1) return fail(RT_ERR_INVALID_ARG, "max_freq must be >= 1");
+    const long long cells = (long long)n0 * n1 * n2;
+    // packed groups of 4 bins may exceed n_freq by 3: keep every flat index below 2^31
+    if (cells * (long long)((max_freq + 3) / 4 * 4) >= (1LL << 31))
+        return fail(RT_ERR_INVALID_ARG, "grid too large: n_freq * n0 * n1 * n2 must stay below 2^31");
+    rt_options o;
+    rt_default_options(&o);
+    if (opt) o = *opt;
+    if (o.kappa_mode != 0 && o.kappa_mode != 1) return fail(RT_ERR_INVALID_ARG, "kappa_mode must be 0 or 1");
+    if (o.ns_cap < 0 || o.ckpt_stride < 0) return fail(RT_ERR_INVALID_ARG, "ns_cap and ckpt_stride must be >= 0");
+    rt_grid* g = new (std::nothrow) rt_grid();
+    if (!g) return fail(RT_ERR_OOM, "host allocation failed");
+    g->n0 = n0; g->n1 = n1; g->n2 = n2; g->max_freq = max_freq;
+    g->opt = o;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return fail(RT_ERR_CUDA, "no CUDA device available");
+    }
+    *out = g;
+    return RT_OK;
+}
+
+rt_status rt_destroy(rt_grid* g) {
+    if (!g) return RT_OK;
+    g->release();
+    delete g;
+    return RT_OK;
+}
+
+const char* rt_last_error(void) { return g_last_error.c_str(); }
+
+int rt_num_substeps(float step_size, float radiation_velocity, float time_step, int ns_cap) {
+    return num_substeps(step_size, radiation_velocity, time_step, ns_cap);
+}
+
+rt_status rt_direction_table(int num_rays, float* out) {
+    if (num_rays < 1 || !out) return fail(RT_ERR_INVALID_ARG, "num_rays must be >= 1 and out non-NULL");
+    for (int i = 0; i < num_rays; ++i) lattice_entry(i, num_rays, out + 3 * (size_t)i);
+    return RT_OK;
+}
+
+rt_status rt_advance(rt_grid* grid, const float* j_map, const float* kappa_map, const float* source_pos,
+                     int num_sources, int num_rays, float step_size, float radiation_velocity,
+                     float time_step, int n_freq, float* out_field, int accumulate, void* cuda_stream) {
+    Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size,
+           radiation_velocity, time_step, n_freq, out_field, accumulate ? 1 : 0, (cudaStream_t)cuda_stream};
+    return advance_impl(grid, a);
+}
+
+rt_status rt_advance_rays(rt_grid* grid, const float* j_map, const float* kappa_map, const float* source_pos,
+                          int num_sources, int num_rays, int ray_begin, int ray_end, float step_size,
+                          float radiation_velocity, float time_step, int n_freq, float* out_field,
+                          int accumulate, void* cuda_stream) {
+    Call a{j_map, kappa_map, source_pos, num_sources, num_rays, ray_begin, ray_end, step_size,
+           radiation_velocity, time_step, n_freq, out_field, accumulate ? 1 : 0, (cudaStream_t)cuda_stream};
+    return advance_impl(grid, a);
+}
+
+rt_status rt_advance_host(rt_grid* g, const float* j_map, const float* kappa_map, const float* source_pos,
+                          int num_sources, int num_rays, float step_size, float radiation_velocity,
+                          float time_step, int n_freq, float* out_field, void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (n_freq < 1 || n_freq > g->max_freq)
+        return fail(RT_ERR_INVALID_ARG, "n_freq = %d outside [1, max_freq = %d]", n_freq, g->max_freq);
+    if (num_sources < 0) return fail(RT_ERR_INVALID_ARG, "num_sources must be >= 0");
+    if (!j_map || !kappa_map || !out_field || (num_sources > 0 && !source_pos))
+        return fail(RT_ERR_INVALID_ARG, "host buffers must be non-NULL");
+    rt_status st = check_device(g);
+    if (st != RT_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t field = sizeof(float) * (size_t)n_freq * g->ncell();
+    const size_t srcb = sizeof(float) * 3 * (size_t)std::max(num_sources, 1);
+    void *dj, *dk, *dout, *dsrc;
+    if ((st = g->ensure(rt_grid::HJ, field, &dj)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::HK, field, &dk)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::HOUT, field, &dout)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::HSRC, srcb, &dsrc)) != RT_OK) return st;
+    RT_CUDA(cudaMemcpyAsync(dj, j_map, field, cudaMemcpyHostToDevice, s), "copy j to device");
+    RT_CUDA(cudaMemcpyAsync(dk, kappa_map, field, cudaMemcpyHostToDevice, s), "copy kappa to device");
+    if (num_sources > 0)
+        RT_CUDA(cudaMemcpyAsync(dsrc, source_pos, sizeof(float) * 3 * (size_t)num_sources,
+                                cudaMemcpyHostToDevice, s), "copy sources to device");
+    Call a{(const float*)dj, (const float*)dk, (const float*)dsrc, num_sources, num_rays, 0, num_rays,
+           step_size, radiation_velocity, time_step, n_freq, (float*)dout, 0, s};
+    if ((st = advance_impl(g, a)) != RT_OK) return st;
+    RT_CUDA(cudaMemcpyAsync(out_field, dout, field, cudaMemcpyDeviceToHost, s), "copy field to host");
+    RT_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return RT_OK;
+}
+
+rt_status rt_trace_cells(rt_grid* g, const float* src, int num_rays, int ray, float step_size, int num_steps,
+                         long long* base_cell, long long* kappa_cell) {
+    if (!g || !src || !base_cell || !kappa_cell) return fail(RT_ERR_INVALID_ARG, "NULL argument");
+    if (num_rays < 1 || ray < 0 || ray >= num_rays || num_steps < 0 || !(step_size > 0.0f))
+        return fail(RT_ERR_INVALID_ARG, "invalid ray / num_rays / num_steps / step_size");
+    rt_status st = check_device(g);
+    if (st != RT_OK) return st;
+    if (num_steps == 0) return RT_OK;
+    float d[3];
+    lattice_entry(ray, num_rays, d);
+    void* buf;
+    if ((st = g->ensure(rt_grid::TRACE, 2 * sizeof(long long) * (size_t)num_steps, &buf)) != RT_OK) return st;
+    long long* dbase = (long long*)buf;
+    long long* dnn = dbase + num_steps;
+    RT_CUDA(rt::launch_trace(src[0], src[1], src[2], d[0], d[1], d[2], step_size, num_steps, g->n0, g->n1,
+                             g->n2, g->opt.kappa_mode, dbase, dnn, 0),
+            "trace kernel launch");
+    RT_CUDA(cudaMemcpy(base_cell, dbase, sizeof(long long) * num_steps, cudaMemcpyDeviceToHost), "copy trace");
+    RT_CUDA(cudaMemcpy(kappa_cell, dnn, sizeof(long long) * num_steps, cudaMemcpyDeviceToHost), "copy trace");
+    return RT_OK;
+}
+
+rt_status rt_kernel_ms(rt_grid* g, float* ms) {
+    if (!g || !ms) return fail(RT_ERR_INVALID_ARG, "NULL argument");
+    if (!g->opt.profile) return fail(RT_ERR_INVALID_ARG, "the handle was created without rt_options.profile");
+    if (!g->ev_valid) return fail(RT_ERR_INVALID_ARG, "no march kernel has been timed on this handle yet");
+    RT_CUDA(cudaEventSynchronize(g->ev[1]), "cudaEventSynchronize");
+    RT_CUDA(cudaEventElapsedTime(ms, g->ev[0], g->ev[1]), "cudaEventElapsedTime");
+    return RT_OK;
+}
+
+rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, float* tuned_ms) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (width) *width = g->last_plan.W;
+    if (block) *block = g->last_plan.block;
+    if (prefetch) *prefetch = g->last_plan.prefetch;
+    if (tuned_ms) *tuned_ms = g->last_plan_ms;
+    return RT_OK;
+}
+
+rt_status rt_tuning_report(rt_grid* g, char* buf, int len) {
+    if (!g || !buf || len < 1) return fail(RT_ERR_INVALID_ARG, "NULL buffer or length < 1");
+    const std::string& r = g->tune_report;
+    const size_t n = std::min(r.size(), (size_t)len - 1);
+    std::memcpy(buf, r.data(), n);
+    buf[n] = 0;
+    return RT_OK;
+}
+
+rt_status rt_backward(rt_grid* g, const float*, const float*, const float*, const float*, int, int, float,
+                      float, float, int, float*, float*, void*) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    return fail(RT_ERR_UNSUPPORTED, "rt_backward is not available yet");
+}
+
+}  // extern "C"

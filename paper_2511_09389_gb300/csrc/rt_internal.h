@@ -1,0 +1,72 @@
+// rt_internal.h -- launchers shared between the C-ABI host code and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rt {
+
+// One forward march launch over a set of (source, bin-group, ray) lanes.
+struct MarchArgs {
+    const float* jp;        // packed j    [groups][ncell][W]   (W = 1: plain [n_freq][ncell])
+    const float* kp;        // packed kappa, same layout
+    float* acc;             // FP32 accumulator, same layout (W = 1: may be the output itself)
+    unsigned long long* acc64;  // fixed-point accumulator [n_freq][ncell] (deterministic mode)
+    const float4* dirs;     // ray directions (xyz, w unused), ray_count entries
+    const float* src;       // device [nsrc][3]
+    int n0, n1, n2;
+    int ns;                 // substeps N_s
+    float ds;               // step length
+    float dep_scale;        // factor applied to every deposit (4 pi / N_Omega, or 1)
+    double fix_scale;       // fixed-point: units per unit deposit (deterministic mode)
+    int ray_count;
+    int nsrc;
+    int groups;             // bin groups of width W
+    int n_freq;             // real bins (deterministic mode writes only these)
+    int kappa_mode;
+    int block;              // threads per block
+    int prefetch;           // 1: issue the next substep's gathers before the current update
+};
+
+cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);
+
+// [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).
+cudaError_t launch_pack(const float* in, float* out, int n_freq, int W, int groups, long long ncell,
+                        cudaStream_t st);
+// out[b][c] (+)= scale * acc[b / W][c][b % W]
+cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long long ncell,
+                          float scale, int accumulate, cudaStream_t st);
+// out[b][c] (+)= acc64[b][c] / fix_scale (deterministic mode)
+cudaError_t launch_unpack_fixed(const unsigned long long* acc, float* out, long long count,
+                                double inv_fix_scale, int accumulate, cudaStream_t st);
+
+// Geometry trace of one ray (test hook).
+cudaError_t launch_trace(float sx, float sy, float sz, float nx, float ny, float nz, float ds,
+                         int ns, int n0, int n1, int n2, int kappa_mode, long long* base,
+                         long long* nn, cudaStream_t st);
+
+// Reverse-mode adjoint.
+struct BackArgs {
+    const float* grad;      // G [n_freq][ncell]
+    const float* j;         // [n_freq][ncell]
+    const float* kappa;     // [n_freq][ncell]
+    float* dj;              // [n_freq][ncell] accumulated
+    float* dk;              // [n_freq][ncell] accumulated
+    float* ckpt;            // checkpoint scratch
+    const float4* dirs;
+    const float* src;
+    int n0, n1, n2;
+    int ns;
+    int stride;             // checkpoint stride K
+    float ds;
+    float scale;            // 4 pi / N_Omega
+    int ray_count;
+    int nsrc;
+    int n_freq;
+    int kappa_mode;
+    int block;
+};
+size_t backward_ckpt_floats(const BackArgs& a);
+cudaError_t launch_march_bwd(const BackArgs& a, cudaStream_t st);
+
+}  // namespace rt

@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every symbol include/raytrax.h declares; host-only
+logic (substep rule, direction lattice) agrees with the oracle. No GPU compute is called."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_09389_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names += _declared(h)
+    assert names, "no declarations found"
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    from paper_2511_09389_gb300 import _native
+    assert set(_native.EXPORTS) <= set(names)
+
+
+def test_num_substeps_matches_oracle(lib):
+    cases = [(0.5, 1.0, 16.0, 0), (0.5, 1.0, 128.0, 0), (0.25, 2.0, 3.3, 0), (0.5, 1.0, 64.0, 100),
+             (0.5, 1.0, 0.0, 0), (1.0, 1.0, 160.0, 0), (0.3, 1.0, 0.9, 0), (0.7, 1.3, 11.1, 7)]
+    for ds, c, dt, cap in cases:
+        # the library takes float arguments: give the oracle the same FP32 values
+        f = [float(np.float32(v)) for v in (ds, c, dt)]
+        assert lib.rt_num_substeps(*f, cap) == oracle.num_substeps(*f, cap), (ds, c, dt, cap)
+    assert lib.rt_num_substeps(0.0, 1.0, 1.0, 0) == -1
+    assert lib.rt_num_substeps(0.5, -1.0, 1.0, 0) == -1
+    assert lib.rt_num_substeps(0.5, 1.0, -1.0, 0) == -1
+    assert lib.rt_num_substeps(1e-30, 1e30, 1e30, 0) == -1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 37, 192, 768, 3072, 12288])
+def test_direction_table_bit_equal_to_oracle(lib, n):
+    from paper_2511_09389_gb300.api import direction_table
+    assert np.array_equal(direction_table(n), oracle.fibonacci_dirs_f32(n))
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.rt_create_grid(ctypes.byref(h), 0, 4, 4, 1, None) == 1
+    assert b"extents" in lib.rt_last_error()
+    assert lib.rt_create_grid(ctypes.byref(h), 4, 4, 4, 0, None) == 1
+    assert lib.rt_create_grid(ctypes.byref(h), 2048, 2048, 1024, 1, None) == 1
+    assert lib.rt_destroy(None) == 0
+    assert lib.rt_direction_table(0, None) == 1

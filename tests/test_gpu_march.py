@@ -1,0 +1,186 @@
+"""GPU parity of the forward march (rt_advance) against the FP64 oracle.
+
+Bar (FP32 path vs FP64 oracle): per bin, relative L2 error <= 1e-5 and max-abs error
+<= 1e-4 * max|F_oracle| (the pointwise relative error is undefined past the light-travel
+horizon, where the field is zero). Cell indices and the direction lattice are bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09389_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_ABS_REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2511_09389_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def errors(F, R):
+    """Per-bin (relative L2, max-abs relative to max|R|)."""
+    F = np.asarray(F, np.float64).reshape(R.shape)
+    out = []
+    for b in range(R.shape[0]):
+        d = F[b] - R[b]
+        nr = np.linalg.norm(R[b])
+        mx = np.abs(R[b]).max()
+        out.append((np.linalg.norm(d) / nr if nr > 0 else np.linalg.norm(d),
+                    np.abs(d).max() / mx if mx > 0 else np.abs(d).max()))
+    return out
+
+
+def assert_parity(F, R, rel=REL_L2, mx=MAX_ABS_REL):
+    for b, (e2, emax) in enumerate(errors(F, R)):
+        assert e2 <= rel and emax <= mx, f"bin {b}: rel-L2 {e2:.3e}, max-abs-rel {emax:.3e}"
+
+
+def run_gpu(torch, p, ns=None, kappa_mode=0, grid=None, **kw):
+    from paper_2511_09389_gb300.api import Grid
+    g = grid or Grid(p.shape, max(8, p.n_freq), kappa_mode=kappa_mode)
+    j = torch.from_numpy(p.j).cuda()
+    k = torch.from_numpy(p.kappa).cuda()
+    s = torch.from_numpy(p.sources).cuda()
+    dt = p.time_step if ns is None else ns * p.step_size
+    out = g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, dt, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def run_oracle(p, ns=None, kappa_mode=0, ray_range=None):
+    if ns is None:
+        ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    return oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, geom_mode=0,
+                          kappa_mode=kappa_mode, ray_range=ray_range)
+
+
+def test_single_source_uniform_32cubed(torch_cuda):
+    """32^3, kappa 0.1, sigma-1 blob at the centre, N_Omega 768, ds 0.5, c dt 16, one bin."""
+    p = inputs.single_source_uniform()
+    assert_parity(run_gpu(torch_cuda, p), run_oracle(p))
+
+
+@pytest.mark.parametrize("n_freq", [1, 2, 3, 4, 5, 8])
+def test_random_irregular_grids_all_bin_widths(torch_cuda, n_freq):
+    """Non-cubic grid, sources outside the box, ragged ray count, every bin-group width."""
+    p = inputs.random_small(10 + n_freq, shape=(13, 9, 17), n_freq=n_freq, n_src=5, num_rays=131,
+                            step_size=0.6, horizon=14.0)
+    assert_parity(run_gpu(torch_cuda, p), run_oracle(p))
+
+
+@pytest.mark.parametrize("kappa_mode", [0, 1])
+def test_kappa_modes(torch_cuda, kappa_mode):
+    p = inputs.random_small(21, shape=(16, 12, 10), n_freq=4, n_src=3, num_rays=200, horizon=12.0)
+    assert_parity(run_gpu(torch_cuda, p, kappa_mode=kappa_mode), run_oracle(p, kappa_mode=kappa_mode))
+
+
+def test_cell_trace_bit_exact(torch_cuda):
+    from paper_2511_09389_gb300.api import Grid
+    shape = (23, 19, 29)
+    rng = np.random.default_rng(2)
+    for kappa_mode in (0, 1):
+        g = Grid(shape, 1, kappa_mode=kappa_mode)
+        z = np.zeros((1,) + shape)
+        for trial in range(12):
+            src = rng.uniform(-3, 25, 3).astype(np.float32)
+            nr = int(rng.choice([1, 7, 768, 3072, 12288]))
+            ray = int(rng.integers(0, nr))
+            ds = float(np.float32(rng.choice([0.5, 0.37, 1.0, 0.125])))
+            ns = 200
+            b_o, n_o, _ = oracle.trace_ray(z, z, src, nr, ray, ds, ns, geom_mode=0, kappa_mode=kappa_mode)
+            b_g, n_g = g.trace_cells(src, nr, ray, ds, ns)
+            assert np.array_equal(b_o, b_g) and np.array_equal(n_o, n_g), (kappa_mode, trial)
+
+
+def test_turbulent_reduced(torch_cuda):
+    """Turbulent medium at reduced size: 48^3 lognormal, 6 sources, 4 bins, N_Omega 768,
+    N_s 96 (rays cross the box and deposit on its faces)."""
+    p = inputs.turbulent(n=48, n_src=6, num_rays=768, horizon=48.0, seed=77)
+    assert_parity(run_gpu(torch_cuda, p), run_oracle(p))
+
+
+@pytest.mark.slow
+def test_turbulent_full_size(torch_cuda):
+    """The benchmark workload at full size, in the launch configuration the benchmark times:
+    128^3, 16 sources, N_Omega 3072, N_s 256, 4 bins (the oracle takes a few seconds per
+    bin on one core)."""
+    p = inputs.turbulent()
+    assert_parity(run_gpu(torch_cuda, p), run_oracle(p))
+
+
+def test_uniform_closed_form_on_gpu(torch_cuda):
+    """Uniform j0, kappa: sum over cells = n_src * 4 pi sum_k (k+1) j0 ds exp(-kappa k ds)."""
+    n, ns, ds, j0, kap = 40, 77, 0.5, 0.8, 0.05
+    p = inputs.Problem("u", np.full((2, n, n, n), j0, np.float32),
+                       np.stack([np.full((n, n, n), kap, np.float32), np.zeros((n, n, n), np.float32)]),
+                       np.array([[3.0, 20.0, 38.5], [-4.0, 10.0, 10.0]], np.float32), 1000, ds, 1.0, ns * ds)
+    F = run_gpu(torch_cuda, p)
+    k = np.arange(ns)
+    for b, kb in enumerate((kap, 0.0)):
+        expect = 2 * 4 * math.pi * np.sum((k + 1) * j0 * ds * np.exp(-kb * k * ds))
+        assert abs(F[b].sum(dtype=np.float64) / expect - 1) < 2e-5
+
+
+def test_shards_accumulate_and_empty_cases(torch_cuda):
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.random_small(31, shape=(12, 12, 12), n_freq=3, n_src=4, num_rays=300, horizon=10.0)
+    g = Grid(p.shape, 8)
+    j, k, s = (torch.from_numpy(a).cuda() for a in (p.j, p.kappa, p.sources))
+    full = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
+    acc = torch.zeros_like(full)
+    for rb, re in [(0, 1), (1, 100), (100, 100), (100, 300)]:
+        g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step, out=acc, accumulate=True, ray_range=(rb, re))
+    assert torch.allclose(acc, full, rtol=1e-5, atol=1e-6 * full.abs().max().item())
+    # accumulate adds to what is there
+    twice = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step, out=full.clone(), accumulate=True)
+    assert torch.allclose(twice, 2 * full, rtol=1e-5, atol=1e-6 * full.abs().max().item())
+    # no sources, zero horizon: zero field (overwriting garbage)
+    junk = torch.full_like(full, 7.0)
+    g.advance(j, k, s[:0], p.num_rays, p.step_size, 1.0, p.time_step, out=junk)
+    assert torch.count_nonzero(junk).item() == 0
+    junk.fill_(7.0)
+    g.advance(j, k, s, p.num_rays, p.step_size, 1.0, 0.0, out=junk)
+    assert torch.count_nonzero(junk).item() == 0
+    torch.cuda.synchronize()
+
+
+def test_host_entry_point_matches_device(torch_cuda):
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.random_small(41, shape=(20, 18, 16), n_freq=4, n_src=3, num_rays=256, horizon=16.0)
+    g = Grid(p.shape, 8)
+    dev = g.advance(*(torch.from_numpy(a).cuda() for a in (p.j, p.kappa, p.sources)), p.num_rays,
+                    p.step_size, 1.0, p.time_step).cpu().numpy()
+    host = g.advance_host(p.j, p.kappa, p.sources, p.num_rays, p.step_size, 1.0, p.time_step)
+    np.testing.assert_allclose(host, dev, rtol=2e-5, atol=1e-6 * np.abs(dev).max())
+    assert_parity(host, run_oracle(p))
+
+
+def test_invalid_arguments_raise(torch_cuda):
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid, RTError
+    g = Grid((8, 8, 8), 2)
+    j = torch.ones(2, 8, 8, 8, device="cuda")
+    s = torch.zeros(1, 3, device="cuda")
+    bad = [dict(num_rays=0), dict(step_size=0.0), dict(step_size=-1.0), dict(radiation_velocity=0.0),
+           dict(time_step=-1.0), dict(ray_range=(5, 2)), dict(ray_range=(0, 11))]
+    for b in bad:
+        kw = dict(num_rays=10, step_size=0.5, radiation_velocity=1.0, time_step=2.0)
+        kw.update(b)
+        with pytest.raises(RTError, match="INVALID_ARG"):
+            g.advance(j, j, s, **kw)
+    with pytest.raises(RTError, match="INVALID_ARG"):
+        Grid((8, 8, 8), 1).advance(j, j, s, 10, 0.5, 1.0, 2.0)      # n_freq above max_freq
+    with pytest.raises(RTError, match="INVALID_ARG"):
+        g.advance(j, j, s, 10, 0.5, 1.0, 2.0, out=j)                  # out aliases an input
