@@ -144,6 +144,31 @@ rt_status rt_backward(rt_grid* grid, const float* grad_out, const float* j_map,
    kernel). Needs rt_options.profile = 1; waits for that kernel to finish. */
 rt_status rt_kernel_ms(rt_grid* grid, float* ms);
 
+/* Allocation-free forward march. The paper has no counterpart: this entry point exists for
+   callers that cannot allocate memory while they run -- a program whose GPU memory belongs to
+   another framework's pool or a fixed budget, or a loop that must never block in an allocator.
+   It computes exactly what rt_advance computes (default options: kappa_mode 0, no N_s cap)
+   for the same arguments, without a handle, and calls no cudaMalloc / cudaFree or any other
+   allocating routine. Its scratch (sorted direction table, packed inputs, accumulator) is one
+   static device array of RT_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that
+   loads the library holds until the process exits. Limits: num_rays <= RT_NOALLOC_MAX_RAYS,
+   and for n_freq >= 2, 3 * ceil(n_freq / W) * W * n0 * n1 * n2 * 4 bytes (W = 2 for two bins,
+   else 4) must fit in the rest of the array after the 256 KiB table (e.g. 64^3 with 4 bins);
+   larger problems return RT_ERR_INVALID_ARG with the sizes in rt_last_error(). One bin needs
+   only the table. The first call on each device (with that device current) looks up the
+   array's device address, and a call with a new num_rays waits for the stream, rebuilds the
+   table and copies it in stream order, then waits again: make such calls before any stream
+   capture. All calls share the array
+   and it keeps the last call's contents (the accumulator is cleared on the stream at every
+   call); calls whose GPU work overlaps (other streams or host threads) race on it.
+   Buffers, shapes and stream as in rt_advance; out_field is overwritten. */
+#define RT_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define RT_NOALLOC_MAX_RAYS 16384
+rt_status rt_advance_noalloc(const float* j_map, const float* kappa_map, const float* source_pos,
+                             int num_sources, int n0, int n1, int n2, int num_rays, float step_size,
+                             float radiation_velocity, float time_step, int n_freq, float* out_field,
+                             void* cuda_stream);
+
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
    thread), threads per block, gather prefetch (0/1), and the march time the autotuner
    measured for it in ms (-1 when rt_options.autotune is 0). Any pointer may be NULL.

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ER
 EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
-           "rt_tuning_report")
+           "rt_tuning_report", "rt_advance_noalloc")
 
 
 class RTError(RuntimeError):
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
         lib.rt_last_plan.restype = i
         lib.rt_tuning_report.argtypes = [vp, ctypes.c_char_p, i]
         lib.rt_tuning_report.restype = i
+        lib.rt_advance_noalloc.argtypes = [fp, fp, fp, i, i, i, i, i, f, f, f, i, fp, vp]
+        lib.rt_advance_noalloc.restype = i
         _lib = lib
         return lib
 

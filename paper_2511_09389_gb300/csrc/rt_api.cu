@@ -87,6 +87,33 @@ uint32_t angular_key(const float d[3]) {
     return (face << 20) | (spread10(q(u)) << 1) | spread10(q(v));
 }
 
+}  // namespace
+
+namespace rt {
+
+void sorted_lattice(int n, int begin, int end, float4* out, uint32_t* key, int* order) {
+    const int cnt = end - begin;
+    for (int i = 0; i < cnt; ++i) {
+        float d[3];
+        lattice_entry(begin + i, n, d);
+        key[i] = angular_key(d);
+        order[i] = i;
+    }
+    // (key, index) order: the same permutation a stable sort by key gives, without a buffer
+    std::sort(order, order + cnt, [&](int a, int b) { return key[a] < key[b] || (key[a] == key[b] && a < b); });
+    for (int i = 0; i < cnt; ++i) {
+        float d[3];
+        lattice_entry(begin + order[i], n, d);
+        out[i] = make_float4(d[0], d[1], d[2], 0.0f);
+    }
+}
+
+rt_status set_error(rt_status st, const char* msg) { return fail(st, "%s", msg); }
+
+}  // namespace rt
+
+namespace {
+
 struct DirTable {
     int n = 0, begin = 0, end = 0;
     float4* d = nullptr;
@@ -158,20 +185,10 @@ struct rt_grid {
         for (auto& t : dirs)
             if (t.n == n && t.begin == begin && t.end == end) { *out = t.d; return RT_OK; }
         const int cnt = end - begin;
-        std::vector<float> xyz(3 * (size_t)cnt);
         std::vector<uint32_t> key(cnt);
         std::vector<int> order(cnt);
-        for (int i = 0; i < cnt; ++i) {
-            lattice_entry(begin + i, n, &xyz[3 * (size_t)i]);
-            key[i] = angular_key(&xyz[3 * (size_t)i]);
-        }
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
         std::vector<float4> host(cnt);
-        for (int i = 0; i < cnt; ++i) {
-            const float* p = &xyz[3 * (size_t)order[i]];
-            host[i] = make_float4(p[0], p[1], p[2], 0.0f);
-        }
+        rt::sorted_lattice(n, begin, end, host.data(), key.data(), order.data());
         DirTable t;
         t.n = n; t.begin = begin; t.end = end;
         RT_CUDA(cudaMalloc(&t.d, sizeof(float4) * (size_t)std::max(cnt, 1)), "cudaMalloc(directions)");

@@ -4,7 +4,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "raytrax.h"
+
 namespace rt {
+
+// Fibonacci lattice rays [begin, end) of an n-ray lattice, FP64 -> FP32, sorted into angular
+// patches; writes end-begin float4 entries to out. key/order: caller buffers of end-begin
+// entries (the function allocates nothing).
+void sorted_lattice(int n, int begin, int end, float4* out, uint32_t* key, int* order);
+
+// Record a message for rt_last_error() on this thread and return st.
+rt_status set_error(rt_status st, const char* msg);
 
 // One forward march launch over a set of (source, bin-group, ray) lanes.
 struct MarchArgs {
