@@ -153,6 +153,44 @@ def reference_arm(args):
     return 0
 
 
+def fwd_adjoint(args, dev, flush, stream):
+    """Forward + adjoint updates/s on the inverse-problem workload (64^3 lognormal kappa, 8
+    sources at Gaussian blob centres, N_Omega 3072, ds 0.5, N_s 128, one bin): each step is one
+    rt_advance and one rt_backward (dL/dj and dL/dkappa), L2 flushed before each step."""
+    import statistics as st
+    import torch
+    from paper_2511_09389_gb300 import inputs
+    from paper_2511_09389_gb300.api import Grid, num_substeps
+    p = inputs.inverse_problem()
+    U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
+    g = Grid(p.shape, 1, profile=True)
+    j, k, s = (torch.from_numpy(a).to(dev) for a in (p.j, p.kappa, p.sources))
+    G = torch.randn(p.j.shape, device=dev)
+    out = torch.empty_like(j)
+    fwd, bwd, kf, kb = [], [], [], []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 0xff)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
+        e[1].record(stream)
+        kfwd = g.kernel_ms()
+        g.backward(G, j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step)
+        e[2].record(stream)
+        e[2].synchronize()
+        if i >= args.warmup:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+            kf.append(kfwd)
+            kb.append(g.kernel_ms())
+    g.close()
+    tf, tb = st.mean(fwd), st.mean(bwd)
+    return {"value": U / ((tf + tb) * 1e-3), "unit": "updates/s", "updates_per_step": U,
+            "workload": "inverse problem: lognormal kappa 64^3, 8 sources, N_Omega 3072, ds 0.5, N_s 128, 1 bin",
+            "ms_fwd": tf, "ms_bwd": tb, "fwd_kernel_ms": st.mean(kf), "adjoint_kernel_ms": st.mean(kb),
+            "adjoint_updates_per_s": U / (tb * 1e-3)}
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -174,7 +212,11 @@ def native_arm(args):
     from paper_2511_09389_gb300.api import num_substeps
     p = inputs.turbulent()
     U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
-    g = Grid(p.shape, 8, profile=True, autotune=True)   # tuned during the warm-up calls
+    if args.plan:
+        w, b, pf = (int(x) for x in args.plan.split(","))
+        g = Grid(p.shape, 8, profile=True, plan=(w, b, pf))
+    else:
+        g = Grid(p.shape, 8, profile=True, autotune=True)   # tuned during the warm-up calls
     j = torch.from_numpy(p.j).to(dev)
     k = torch.from_numpy(p.kappa).to(dev)
     s = torch.from_numpy(p.sources).to(dev)
@@ -259,6 +301,8 @@ def native_arm(args):
                    "samples": clk["samples"]},
     }
 
+    line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
@@ -284,6 +328,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (faster)")
+    ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_thread,block,prefetch' "
+                                               "instead of autotuning (for reproducible profiles)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

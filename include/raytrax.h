@@ -63,6 +63,9 @@ typedef struct {
     int ckpt_stride;    /* adjoint checkpoint stride K in substeps; 0: automatic */
     int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
                            call's stream, readable with rt_kernel_ms */
+    int plan_width;     /* forward launch plan, used when autotune = 0 (0: default for each):  */
+    int plan_block;     /*   bins per thread (1, 2 or 4), threads per block (32..256, multiple */
+    int plan_prefetch;  /*   of 32), gather prefetch (1: off, 2: on)                           */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,

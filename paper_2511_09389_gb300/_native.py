@@ -33,7 +33,8 @@ class RTError(RuntimeError):
 class rt_options(ctypes.Structure):
     _fields_ = [("deterministic", ctypes.c_int), ("kappa_mode", ctypes.c_int), ("ns_cap", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("plan_width", ctypes.c_int), ("plan_block", ctypes.c_int),
+                ("plan_prefetch", ctypes.c_int)]
 
 
 _lock = threading.Lock()

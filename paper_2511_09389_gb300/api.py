@@ -51,11 +51,14 @@ def direction_table(num_rays: int) -> np.ndarray:
 
 
 class Grid:
-    """A library handle for one grid shape (owns its scratch on one device)."""
+    """A library handle for one grid shape (owns its scratch on one device).
+
+    plan=(bins_per_thread, block, prefetch) pins the forward launch plan (ignored when
+    autotune=True, which times the candidates on the first call of each shape class)."""
 
     def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
                  ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
-                 device=None):
+                 plan=None, device=None):
         self._lib = _native.load()
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) != 3:
@@ -63,8 +66,9 @@ class Grid:
         self.max_freq = int(max_freq)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
+        pw, pb, pp = (0, 0, 0) if plan is None else (int(plan[0]), int(plan[1]), 2 if plan[2] else 1)
         opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
-                                 int(ckpt_stride), int(bool(profile)))
+                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp)
         self.options = opt
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

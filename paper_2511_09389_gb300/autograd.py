@@ -1,0 +1,48 @@
+"""Differentiable march: a torch.autograd.Function over rt_advance / rt_backward.
+
+The forward pass is one rt_advance; the backward pass is the hand-written reverse-march
+adjoint (rt_backward), which recomputes the forward state from per-ray checkpoints. Gradients
+flow to j and kappa (the Jacobians w.r.t. (j, kappa) of Sec. 4); source positions, the step
+length, c and dt are not differentiated.
+"""
+from __future__ import annotations
+
+import torch
+
+from .api import Grid, _cached_grid, _grid_tensor
+
+
+class RTFunction(torch.autograd.Function):
+    """field = RTFunction.apply(j, kappa, sources, num_rays, step_size, radiation_velocity,
+    time_step, grid); j, kappa: [n_freq, n0, n1, n2] CUDA float32 (or 3-D for one bin)."""
+
+    @staticmethod
+    def forward(ctx, j, kappa, sources, num_rays, step_size, radiation_velocity, time_step, grid):
+        squeeze = j.dim() == 3
+        j4 = _grid_tensor(j, "j")
+        k4 = _grid_tensor(kappa, "kappa")
+        if grid is None:
+            grid = _cached_grid(j4.shape[1:], j4.shape[0], j4.device)
+        out = grid.advance(j4, k4, sources, num_rays, step_size, radiation_velocity, time_step)
+        ctx.save_for_backward(j4, k4, torch.as_tensor(sources, dtype=torch.float32, device=j4.device))
+        ctx.args = (num_rays, step_size, radiation_velocity, time_step, grid, squeeze)
+        return out[0] if squeeze else out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        j4, k4, src = ctx.saved_tensors
+        num_rays, step_size, c, dt, grid, squeeze = ctx.args
+        g = grad_out.unsqueeze(0) if squeeze else grad_out
+        need_j, need_k = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gj, gk = grid.backward(g.contiguous().float(), j4, k4, src, num_rays, step_size, c, dt,
+                               need_j=need_j, need_kappa=need_k)
+        if squeeze:
+            gj = gj[0] if gj is not None else None
+            gk = gk[0] if gk is not None else None
+        return gj, gk, None, None, None, None, None, None
+
+
+def render(j, kappa, sources, num_rays: int, step_size: float, radiation_velocity: float = 1.0,
+           time_step: float = 1.0, grid: Grid | None = None) -> torch.Tensor:
+    """Differentiable one-dt field (see RTFunction)."""
+    return RTFunction.apply(j, kappa, sources, num_rays, step_size, radiation_velocity, time_step, grid)

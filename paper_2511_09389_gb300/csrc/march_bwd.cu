@@ -1,0 +1,227 @@
+// march_bwd.cu -- reverse-mode adjoint of the forward march (sm_103a).
+//
+// For a loss L with G = dL/d(field), differentiating Eq. 2 along one ray and bin gives, with
+// a_k = exp(-kappa_k ds), E_k = exp(-tau_k), e_k = j_k E_k ds and s = 4 pi / N_Omega:
+//     g_k       = s * sum_c w_{k,c} G[c_{k,c}]          (adjoint of the deposit of I_{k+1})
+//     lam_{k+1} = g_k + a_{k+1} lam_{k+2},   lam_{N_s+1} = 0
+//     dj[c_{k,c}]  += lam_{k+1} E_k ds w_{k,c}            (adjoint of the trilinear gather)
+//     dkap[cell_k] += -ds (lam_{k+1} I_k a_k + mu_{k+1}),  (nearest-cell kappa)
+//     mu_k = mu_{k+1} + lam_{k+1} e_k,  mu_{N_s} = 0.
+// One thread per (ray, source, bin group). A forward sweep stores (x_k, I_k, tau_k) every K
+// substeps; the reverse sweep replays each K-substep segment from its checkpoint into a
+// per-thread record (x_k, I_k, E_k, a_k, e_k) and then walks it backwards, so the forward state
+// is recomputed exactly and never reconstructed by dividing out exp(-kappa ds). Scatters into
+// dj / dkappa are merged in registers while the corner set (or kappa cell) is unchanged.
+#include "march_common.cuh"
+#include "rt_internal.h"
+
+namespace rt {
+
+template <int W, int K>
+__global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
+    const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
+    const int rb = blockIdx.x % rblocks;
+    const int sg = blockIdx.x / rblocks;
+    const int s = sg % a.nsrc;
+    const int g = sg / a.nsrc;
+    const int r = rb * blockDim.x + threadIdx.x;
+    if (r >= a.ray_count) return;
+    const long long lanes = (long long)a.ray_count * a.nsrc * ((a.n_freq + W - 1) / W);
+    const long long lane = ((long long)g * a.nsrc + s) * a.ray_count + r;
+
+    const long long ncell = (long long)a.n0 * a.n1 * a.n2;
+    const float* __restrict__ jg = a.j + (size_t)g * ncell * W;
+    const float* __restrict__ kg = a.kappa + (size_t)g * ncell * W;
+    const float* __restrict__ Gg = a.grad + (size_t)g * ncell * W;
+    float* __restrict__ djg = a.dj ? a.dj + (size_t)g * ncell * W : nullptr;
+    float* __restrict__ dkg = a.dk ? a.dk + (size_t)g * ncell * W : nullptr;
+
+    const float4 n = a.dirs[r];
+    const float ds = a.ds;
+    const float dx = __fmul_rn(n.x, ds), dy = __fmul_rn(n.y, ds), dz = __fmul_rn(n.z, ds);
+    constexpr int F = 3 + 2 * W;   // checkpoint fields: x, y, z, I[W], tau[W]
+    float* __restrict__ ck = a.ckpt;
+    auto ck_at = [&](int c, int f) -> float& { return ck[((size_t)c * F + f) * lanes + lane]; };
+
+    // ---- forward sweep: Eq. 2, checkpoint every K substeps ----
+    {
+        float x = a.src[3 * s + 0], y = a.src[3 * s + 1], z = a.src[3 * s + 2];
+        float I[W], tau[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+#pragma unroll 1
+        for (int k = 0; k < a.ns; ++k) {
+            if (k % K == 0) {
+                const int c = k / K;
+                ck_at(c, 0) = x; ck_at(c, 1) = y; ck_at(c, 2) = z;
+#pragma unroll
+                for (int b = 0; b < W; ++b) { ck_at(c, 3 + b) = I[b]; ck_at(c, 3 + W + b) = tau[b]; }
+            }
+            Sample sm;
+            make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
+            Vec<W> jc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
+            const Vec<W> kc = ldg_vec<W>(kg, sm.nn);
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                float jk = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jc[c].v[b], jk);
+                const float kds = kc.v[b] * ds;
+                I[b] = fmaf(I[b], expf(-kds), jk * expf(-tau[b]) * ds);
+                tau[b] += kds;
+            }
+            x = __fadd_rn(x, dx);
+            y = __fadd_rn(y, dy);
+            z = __fadd_rn(z, dz);
+        }
+    }
+
+    // ---- reverse sweep ----
+    float lam_next[W], a_next[W], mu[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { lam_next[b] = 0.0f; a_next[b] = 0.0f; mu[b] = 0.0f; }
+    int pc[8];
+    float pdj[8][W];
+    int pnn = -1;
+    float pdk[W];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = -1;
+#pragma unroll
+        for (int b = 0; b < W; ++b) pdj[c][b] = 0.0f;
+    }
+#pragma unroll
+    for (int b = 0; b < W; ++b) pdk[b] = 0.0f;
+
+    // per-thread segment record (local memory): x, I_k, E_k, a_k, e_k
+    float rx[K], ry[K], rz[K], rI[K][W], rE[K][W], ra[K][W], re[K][W];
+    const int nseg = (a.ns + K - 1) / K;
+#pragma unroll 1
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int k0 = seg * K;
+        const int len = min(K, a.ns - k0);
+        float x = ck_at(seg, 0), y = ck_at(seg, 1), z = ck_at(seg, 2);
+        float I[W], tau[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) { I[b] = ck_at(seg, 3 + b); tau[b] = ck_at(seg, 3 + W + b); }
+        // replay the segment exactly as the forward sweep ran it
+#pragma unroll 1
+        for (int q = 0; q < len; ++q) {
+            Sample sm;
+            make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
+            Vec<W> jc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
+            const Vec<W> kc = ldg_vec<W>(kg, sm.nn);
+            rx[q] = x; ry[q] = y; rz[q] = z;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                float jk = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jc[c].v[b], jk);
+                const float kds = kc.v[b] * ds;
+                const float att = expf(-kds), em = expf(-tau[b]);
+                const float emis = jk * em * ds;
+                rI[q][b] = I[b]; rE[q][b] = em; ra[q][b] = att; re[q][b] = emis;
+                I[b] = fmaf(I[b], att, emis);
+                tau[b] += kds;
+            }
+            x = __fadd_rn(x, dx);
+            y = __fadd_rn(y, dy);
+            z = __fadd_rn(z, dz);
+        }
+        // walk the segment backwards
+#pragma unroll 1
+        for (int q = len - 1; q >= 0; --q) {
+            Sample sm;
+            make_sample(rx[q], ry[q], rz[q], a.n0, a.n1, a.n2, a.kappa_mode, sm);
+            Vec<W> gc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gc[c] = ldg_vec<W>(Gg, sm.cell[c]);
+            float ddj[W], ddk[W];
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                float gk = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) gk = fmaf(sm.w[c], gc[c].v[b], gk);
+                const float lam = fmaf(a_next[b], lam_next[b], gk * a.scale);      // lam_{k+1}
+                ddj[b] = lam * rE[q][b] * ds;
+                ddk[b] = -ds * fmaf(lam * rI[q][b], ra[q][b], mu[b]);              // uses mu_{k+1}
+                mu[b] = fmaf(lam, re[q][b], mu[b]);                                // mu_k
+                lam_next[b] = lam;
+                a_next[b] = ra[q][b];
+            }
+            if (djg) {
+                if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
+                    if (pc[0] >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        pc[c] = sm.cell[c];
+#pragma unroll
+                        for (int b = 0; b < W; ++b) pdj[c][b] = sm.w[c] * ddj[b];
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                        for (int b = 0; b < W; ++b) pdj[c][b] = fmaf(sm.w[c], ddj[b], pdj[c][b]);
+                    }
+                }
+            }
+            if (dkg) {
+                if (sm.nn != pnn) {
+                    if (pnn >= 0) red_vec<W>(dkg, pnn, pdk);
+                    pnn = sm.nn;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) pdk[b] = ddk[b];
+                } else {
+#pragma unroll
+                    for (int b = 0; b < W; ++b) pdk[b] += ddk[b];
+                }
+            }
+        }
+    }
+    if (djg && pc[0] >= 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c]);
+    }
+    if (dkg && pnn >= 0) red_vec<W>(dkg, pnn, pdk);
+}
+
+size_t backward_ckpt_floats(const BackArgs& a, int W) {
+    const int K = a.stride;
+    const long long lanes = (long long)a.ray_count * a.nsrc * ((a.n_freq + W - 1) / W);
+    const long long nck = (a.ns + K - 1) / K;
+    return (size_t)(nck * (3 + 2 * W) * lanes);
+}
+
+cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st) {
+    const int block = a.block > 0 ? a.block : 32;
+    const long long rblocks = (a.ray_count + block - 1) / block;
+    const long long groups = (a.n_freq + W - 1) / W;
+    const long long nblk = rblocks * a.nsrc * groups;
+    if (nblk <= 0) return cudaSuccess;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)nblk;
+    const int key = W * 100 + a.stride;
+    switch (key) {
+        case 108: k_march_bwd<1, 8><<<grid, block, 0, st>>>(a); break;
+        case 116: k_march_bwd<1, 16><<<grid, block, 0, st>>>(a); break;
+        case 132: k_march_bwd<1, 32><<<grid, block, 0, st>>>(a); break;
+        case 208: k_march_bwd<2, 8><<<grid, block, 0, st>>>(a); break;
+        case 216: k_march_bwd<2, 16><<<grid, block, 0, st>>>(a); break;
+        case 232: k_march_bwd<2, 32><<<grid, block, 0, st>>>(a); break;
+        case 408: k_march_bwd<4, 8><<<grid, block, 0, st>>>(a); break;
+        case 416: k_march_bwd<4, 16><<<grid, block, 0, st>>>(a); break;
+        case 432: k_march_bwd<4, 32><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rt

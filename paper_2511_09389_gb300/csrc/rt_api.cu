@@ -132,7 +132,7 @@ struct rt_grid {
     int device = 0;
     std::vector<DirTable> dirs;
     // scratch slots
-    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, NSLOT };
+    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -415,6 +415,9 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     plan.W = pick_width(a.n_freq);
     plan.block = 32;
     plan.prefetch = plan.W == 1 ? 1 : 0;
+    if (g->opt.plan_width) plan.W = g->opt.plan_width;
+    if (g->opt.plan_block) plan.block = g->opt.plan_block;
+    if (g->opt.plan_prefetch) plan.prefetch = g->opt.plan_prefetch == 2 ? 1 : 0;
     g->last_plan_ms = -1.0f;
     if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
     g->last_plan = plan;
@@ -455,6 +458,11 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
     if (opt) o = *opt;
     if (o.kappa_mode != 0 && o.kappa_mode != 1) return fail(RT_ERR_INVALID_ARG, "kappa_mode must be 0 or 1");
     if (o.ns_cap < 0 || o.ckpt_stride < 0) return fail(RT_ERR_INVALID_ARG, "ns_cap and ckpt_stride must be >= 0");
+    if (o.plan_width != 0 && o.plan_width != 1 && o.plan_width != 2 && o.plan_width != 4)
+        return fail(RT_ERR_INVALID_ARG, "plan_width must be 0, 1, 2 or 4");
+    if (o.plan_block != 0 && (o.plan_block < 32 || o.plan_block > 256 || o.plan_block % 32))
+        return fail(RT_ERR_INVALID_ARG, "plan_block must be 0 or a multiple of 32 in [32, 256]");
+    if (o.plan_prefetch < 0 || o.plan_prefetch > 2) return fail(RT_ERR_INVALID_ARG, "plan_prefetch must be 0, 1 or 2");
     rt_grid* g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ERR_OOM, "host allocation failed");
     g->n0 = n0; g->n1 = n1; g->n2 = n2; g->max_freq = max_freq;
@@ -584,10 +592,86 @@ rt_status rt_tuning_report(rt_grid* g, char* buf, int len) {
     return RT_OK;
 }
 
-rt_status rt_backward(rt_grid* g, const float*, const float*, const float*, const float*, int, int, float,
-                      float, float, int, float*, float*, void*) {
+rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,
+                      const float* source_pos, int num_sources, int num_rays, float step_size,
+                      float radiation_velocity, float time_step, int n_freq, float* grad_j, float* grad_kappa,
+                      void* cuda_stream) {
+    Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size, radiation_velocity,
+           time_step, n_freq, grad_j ? grad_j : grad_kappa, 0, (cudaStream_t)cuda_stream};
+    int ns = 0;
     if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
-    return fail(RT_ERR_UNSUPPORTED, "rt_backward is not available yet");
+    if (!grad_out) return fail(RT_ERR_INVALID_ARG, "grad_out is NULL");
+    if (!grad_j && !grad_kappa) return RT_OK;   // nothing requested
+    if (a.out == nullptr) return fail(RT_ERR_INVALID_ARG, "no gradient output");
+    rt_status st = validate(g, a, &ns);
+    if (st != RT_OK) return st;
+    for (const float* o : {(const float*)grad_j, (const float*)grad_kappa})
+        if (o && (o == grad_out || o == j_map || o == kappa_map))
+            return fail(RT_ERR_INVALID_ARG, "a gradient output aliases an input");
+    if (grad_j && grad_j == grad_kappa) return fail(RT_ERR_INVALID_ARG, "grad_j and grad_kappa alias");
+    if ((st = check_device(g)) != RT_OK) return st;
+    const long long ncell = g->ncell();
+    const size_t field_bytes = sizeof(float) * (size_t)n_freq * ncell;
+    if (ns == 0 || num_sources == 0) {
+        if (grad_j) RT_CUDA(cudaMemsetAsync(grad_j, 0, field_bytes, a.st), "cudaMemsetAsync(grad_j)");
+        if (grad_kappa) RT_CUDA(cudaMemsetAsync(grad_kappa, 0, field_bytes, a.st), "cudaMemsetAsync(grad_kappa)");
+        return RT_OK;
+    }
+    const float4* dirs = nullptr;
+    if ((st = g->table(num_rays, 0, num_rays, &dirs)) != RT_OK) return st;
+
+    rt::BackArgs b{};
+    b.dirs = dirs;
+    b.src = source_pos;
+    b.n0 = g->n0; b.n1 = g->n1; b.n2 = g->n2;
+    b.ns = ns;
+    b.ds = step_size;
+    b.scale = (float)(4.0 * 3.14159265358979323846 / (double)num_rays);
+    b.ray_count = num_rays;
+    b.nsrc = num_sources;
+    b.n_freq = n_freq;
+    b.kappa_mode = g->opt.kappa_mode;
+    b.block = 32;
+    // checkpoint stride: the option, rounded to a supported value; automatic = 16
+    const int want = g->opt.ckpt_stride > 0 ? g->opt.ckpt_stride : 16;
+    b.stride = want <= 11 ? 8 : (want <= 23 ? 16 : 32);
+    const int W = pick_width(n_freq);
+    const int groups = (n_freq + W - 1) / W;
+    void* ck;
+    if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(b, W), &ck)) != RT_OK) return st;
+    b.ckpt = (float*)ck;
+    if (W == 1) {
+        b.grad = grad_out; b.j = j_map; b.kappa = kappa_map;
+        b.dj = grad_j; b.dk = grad_kappa;
+        if (grad_j) RT_CUDA(cudaMemsetAsync(grad_j, 0, field_bytes, a.st), "cudaMemsetAsync(grad_j)");
+        if (grad_kappa) RT_CUDA(cudaMemsetAsync(grad_kappa, 0, field_bytes, a.st), "cudaMemsetAsync(grad_kappa)");
+        if ((st = g->mark(0, a.st)) != RT_OK) return st;
+        RT_CUDA(rt::launch_march_bwd(1, b, a.st), "adjoint kernel launch");
+        return g->mark(1, a.st);
+    }
+    const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
+    void *jp, *kp, *gp, *djp = nullptr, *dkp = nullptr;
+    if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::GP, packed, &gp)) != RT_OK) return st;
+    if (grad_j && (st = g->ensure(rt_grid::DJ, packed, &djp)) != RT_OK) return st;
+    if (grad_kappa && (st = g->ensure(rt_grid::DK, packed, &dkp)) != RT_OK) return st;
+    RT_CUDA(rt::launch_pack(j_map, (float*)jp, n_freq, W, groups, ncell, a.st), "pack(j) launch");
+    RT_CUDA(rt::launch_pack(kappa_map, (float*)kp, n_freq, W, groups, ncell, a.st), "pack(kappa) launch");
+    RT_CUDA(rt::launch_pack(grad_out, (float*)gp, n_freq, W, groups, ncell, a.st), "pack(grad) launch");
+    if (djp) RT_CUDA(cudaMemsetAsync(djp, 0, packed, a.st), "cudaMemsetAsync(dj)");
+    if (dkp) RT_CUDA(cudaMemsetAsync(dkp, 0, packed, a.st), "cudaMemsetAsync(dkappa)");
+    b.grad = (const float*)gp; b.j = (const float*)jp; b.kappa = (const float*)kp;
+    b.dj = (float*)djp; b.dk = (float*)dkp;
+    if ((st = g->mark(0, a.st)) != RT_OK) return st;
+    RT_CUDA(rt::launch_march_bwd(W, b, a.st), "adjoint kernel launch");
+    if ((st = g->mark(1, a.st)) != RT_OK) return st;
+    if (grad_j)
+        RT_CUDA(rt::launch_unpack((const float*)djp, grad_j, n_freq, W, ncell, 1.0f, 0, a.st), "unpack(dj) launch");
+    if (grad_kappa)
+        RT_CUDA(rt::launch_unpack((const float*)dkp, grad_kappa, n_freq, W, ncell, 1.0f, 0, a.st),
+                "unpack(dkappa) launch");
+    return RT_OK;
 }
 
 }  // extern "C"

@@ -57,11 +57,11 @@ cudaError_t launch_trace(float sx, float sy, float sz, float nx, float ny, float
 
 // Reverse-mode adjoint.
 struct BackArgs {
-    const float* grad;      // G [n_freq][ncell]
-    const float* j;         // [n_freq][ncell]
-    const float* kappa;     // [n_freq][ncell]
-    float* dj;              // [n_freq][ncell] accumulated
-    float* dk;              // [n_freq][ncell] accumulated
+    const float* grad;      // G, packed like j
+    const float* j;         // packed [groups][ncell][W] (W = 1: plain [n_freq][ncell])
+    const float* kappa;     // packed like j
+    float* dj;              // accumulator packed like j, or NULL (not wanted)
+    float* dk;              // accumulator packed like j, or NULL (not wanted)
     float* ckpt;            // checkpoint scratch
     const float4* dirs;
     const float* src;
@@ -76,7 +76,9 @@ struct BackArgs {
     int kappa_mode;
     int block;
 };
-size_t backward_ckpt_floats(const BackArgs& a);
-cudaError_t launch_march_bwd(const BackArgs& a, cudaStream_t st);
+// Checkpoint scratch (floats) for bin-group width W and stride a.stride.
+size_t backward_ckpt_floats(const BackArgs& a, int W);
+// W in {1, 2, 4}, a.stride in {8, 16, 32}.
+cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st);
 
 }  // namespace rt

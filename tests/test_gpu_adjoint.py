@@ -1,0 +1,154 @@
+"""GPU reverse-march adjoint (rt_backward) against the FP64 oracle's adjoint and FP64 finite
+differences; the autograd wrapper; gradient-based inversion (Sec. 4).
+
+Bar: relative L2 error of dL/dj and dL/dkappa <= 1e-3 per bin against the oracle adjoint
+(itself pinned to FP64 central differences in test_oracle_pins.py) and against GPU-side
+directional finite differences evaluated in FP64 by the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09389_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GRAD_REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2511_09389_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def gpu_backward(torch, p, G, **opts):
+    from paper_2511_09389_gb300.api import Grid
+    g = Grid(p.shape, 8, **opts)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    gj, gk = g.backward(t(G), t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size,
+                        p.radiation_velocity, p.time_step)
+    torch.cuda.synchronize()
+    return gj.cpu().numpy(), gk.cpu().numpy()
+
+
+def oracle_backward(p, G, kappa_mode=0):
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    return oracle.backward(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G, kappa_mode=kappa_mode)
+
+
+@pytest.mark.parametrize("n_freq,stride", [(1, 8), (1, 16), (2, 16), (3, 32), (4, 8), (5, 16)])
+def test_adjoint_matches_oracle(torch_cuda, n_freq, stride):
+    p = inputs.random_small(100 + n_freq, shape=(14, 11, 17), n_freq=n_freq, n_src=4, num_rays=97,
+                            step_size=0.6, horizon=15.0)   # N_s = 25: ragged last segment
+    G = np.random.default_rng(n_freq).standard_normal(p.j.shape)
+    gj, gk = gpu_backward(torch_cuda, p, G, ckpt_stride=stride)
+    rj, rk = oracle_backward(p, G)
+    for b in range(n_freq):
+        assert rel(gj[b], rj[b]) <= GRAD_REL, (b, rel(gj[b], rj[b]))
+        assert rel(gk[b], rk[b]) <= GRAD_REL, (b, rel(gk[b], rk[b]))
+
+
+def test_adjoint_kappa_mode_round(torch_cuda):
+    p = inputs.random_small(120, shape=(12, 12, 12), n_freq=4, n_src=3, num_rays=150, horizon=12.0)
+    G = np.random.default_rng(3).standard_normal(p.j.shape)
+    gj, gk = gpu_backward(torch_cuda, p, G, kappa_mode=1)
+    rj, rk = oracle_backward(p, G, kappa_mode=1)
+    assert rel(gj, rj) <= GRAD_REL and rel(gk, rk) <= GRAD_REL
+
+
+def test_adjoint_vs_central_fd_16cubed(torch_cuda):
+    """dL/dkappa and dL/dj against FP64 central differences (h = 1e-6) on a 16^3 lognormal
+    medium with N_Omega = 192, L = <G, F>: the GPU adjoint's directional derivatives."""
+    n = 16
+    kap = inputs.lognormal_field((n, n, n), 1.0, 0.05, 41)[None]
+    src = np.array([[7.3, 8.1, 6.6], [3.0, 11.5, 9.2]], np.float32)
+    j = inputs.gaussian_blobs((n, n, n), src, 2.0, [1.0, 0.6])[None]
+    p = inputs.Problem("fd", j, kap, src, 192, 0.5, 1.0, 10.0)
+    ns = 20
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal(j.shape)
+    gj, gk = gpu_backward(torch_cuda, p, G)
+    h = 1e-6
+    for target in ("kappa", "j"):
+        for _ in range(3):
+            e = rng.standard_normal(j.shape)
+            jj, kk = (j.astype(np.float64), kap.astype(np.float64))
+            if target == "kappa":
+                Fp = oracle.advance(jj, kk + h * e, src, 192, 0.5, ns)
+                Fm = oracle.advance(jj, kk - h * e, src, 192, 0.5, ns)
+                ad = np.sum(gk * e)
+            else:
+                Fp = oracle.advance(jj + h * e, kk, src, 192, 0.5, ns)
+                Fm = oracle.advance(jj - h * e, kk, src, 192, 0.5, ns)
+                ad = np.sum(gj * e)
+            fd = (np.sum(G * Fp) - np.sum(G * Fm)) / (2 * h)
+            assert abs(ad - fd) <= GRAD_REL * abs(fd), (target, ad, fd)
+
+
+def test_adjoint_full_size_inverse_workload(torch_cuda):
+    """64^3 lognormal, 8 sources at blob centres, N_Omega 3072, N_s 128, one bin."""
+    p = inputs.inverse_problem()
+    G = np.random.default_rng(8).standard_normal(p.j.shape)
+    gj, gk = gpu_backward(torch_cuda, p, G)
+    rj, rk = oracle_backward(p, G)
+    assert rel(gj, rj) <= GRAD_REL and rel(gk, rk) <= GRAD_REL, (rel(gj, rj), rel(gk, rk))
+
+
+def test_autograd_function_and_zero_cases(torch_cuda):
+    torch = torch_cuda
+    from paper_2511_09389_gb300.autograd import render
+    p = inputs.random_small(130, shape=(10, 9, 12), n_freq=2, n_src=2, num_rays=80, horizon=8.0)
+    j = torch.from_numpy(p.j).cuda().requires_grad_(True)
+    k = torch.from_numpy(p.kappa).cuda().requires_grad_(True)
+    s = torch.from_numpy(p.sources).cuda()
+    F = render(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
+    W = torch.randn_like(F)
+    (F * W).sum().backward()
+    rj, rk = oracle_backward(p, W.cpu().numpy().astype(np.float64))
+    assert rel(j.grad.cpu().numpy(), rj) <= GRAD_REL and rel(k.grad.cpu().numpy(), rk) <= GRAD_REL
+    # 3-D (one bin) inputs, gradient only for j
+    j1 = torch.from_numpy(p.j[0]).cuda().requires_grad_(True)
+    F1 = render(j1, torch.from_numpy(p.kappa[0]).cuda(), s, p.num_rays, p.step_size, 1.0, p.time_step)
+    assert F1.shape == j1.shape
+    F1.sum().backward()
+    assert j1.grad.shape == j1.shape and torch.isfinite(j1.grad).all()
+    # no sources: zero gradients
+    from paper_2511_09389_gb300.api import Grid
+    g = Grid(p.shape, 8)
+    gj, gk = g.backward(torch.ones_like(j), j.detach(), k.detach(), s[:0], p.num_rays, p.step_size, 1.0,
+                        p.time_step)
+    assert torch.count_nonzero(gj).item() == 0 and torch.count_nonzero(gk).item() == 0
+
+
+def test_amplitude_inversion_on_gpu(torch_cuda):
+    """Sec. 4: recover a scalar amplitude A of a fixed template e0 from a reference field by
+    gradient descent through the differentiable march; the answer is the closed-form MSE
+    minimiser <F0, I_ref> / <F0, F0> (F is linear in j)."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.autograd import render
+    p = inputs.single_source_uniform(n=24, num_rays=768, horizon=10.0)
+    e0 = torch.from_numpy(p.j).cuda()
+    k = torch.from_numpy(p.kappa).cuda()
+    s = torch.from_numpy(p.sources).cuda()
+    F0 = render(e0, k, s, p.num_rays, p.step_size, 1.0, p.time_step).double()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    Iref = 2.7 * F0 * (1 + 0.05 * torch.randn(F0.shape, generator=gen, device="cuda", dtype=torch.float64))
+    A_star = (F0 * Iref).sum() / (F0 * F0).sum()
+    curv = 2 * (F0 * F0).sum()
+    A = torch.zeros((), device="cuda", dtype=torch.float32, requires_grad=True)
+    for _ in range(25):
+        F = render(A * e0, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
+        loss = ((F.double() - Iref) ** 2).sum()
+        A.grad = None
+        loss.backward()
+        with torch.no_grad():
+            A -= (0.8 * A.grad.double() / curv).float()
+    assert abs(A.item() - A_star.item()) <= 1e-4 * abs(A_star.item()), (A.item(), A_star.item())
