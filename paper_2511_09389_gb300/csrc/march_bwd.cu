@@ -11,7 +11,8 @@
 // substeps; the reverse sweep replays each K-substep segment from its checkpoint into a
 // per-thread record (x_k, I_k, E_k, a_k, e_k) and then walks it backwards, so the forward state
 // is recomputed exactly and never reconstructed by dividing out exp(-kappa ds). Scatters into
-// dj / dkappa are merged in registers while the corner set (or kappa cell) is unchanged.
+// dj / dkappa are merged in registers while the corner set (or kappa cell) is unchanged, and
+// gathers are skipped while it is unchanged (the registers still hold those corner values).
 #include "march_common.cuh"
 #include "rt_internal.h"
 
@@ -49,6 +50,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
         float I[W], tau[W];
 #pragma unroll
         for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+        Vec<W> jc[8], kc;
+        int c0 = -1, c7 = -1, cn = -1;   // cells of the values held in jc / kc
 #pragma unroll 1
         for (int k = 0; k < a.ns; ++k) {
             if (k % K == 0) {
@@ -59,10 +62,12 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
             }
             Sample sm;
             make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
-            Vec<W> jc[8];
+            if (sm.cell[0] != c0 || sm.cell[7] != c7) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
-            const Vec<W> kc = ldg_vec<W>(kg, sm.nn);
+                for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
+                c0 = sm.cell[0]; c7 = sm.cell[7];
+            }
+            if (sm.nn != cn) { kc = ldg_vec<W>(kg, sm.nn); cn = sm.nn; }
 #pragma unroll
             for (int b = 0; b < W; ++b) {
                 float jk = 0.0f;
@@ -95,6 +100,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 #pragma unroll
     for (int b = 0; b < W; ++b) pdk[b] = 0.0f;
 
+    Vec<W> gc[8];                     // G at the corners of pc (the pending dj corner set)
+    int g0 = -1, g7 = -1;
     // per-thread segment record (local memory): x, I_k, E_k, a_k, e_k
     float rx[K], ry[K], rz[K], rI[K][W], rE[K][W], ra[K][W], re[K][W];
     const int nseg = (a.ns + K - 1) / K;
@@ -107,14 +114,18 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 #pragma unroll
         for (int b = 0; b < W; ++b) { I[b] = ck_at(seg, 3 + b); tau[b] = ck_at(seg, 3 + W + b); }
         // replay the segment exactly as the forward sweep ran it
+        Vec<W> jc[8], kc;
+        int c0 = -1, c7 = -1, cn = -1;
 #pragma unroll 1
         for (int q = 0; q < len; ++q) {
             Sample sm;
             make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
-            Vec<W> jc[8];
+            if (sm.cell[0] != c0 || sm.cell[7] != c7) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
-            const Vec<W> kc = ldg_vec<W>(kg, sm.nn);
+                for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
+                c0 = sm.cell[0]; c7 = sm.cell[7];
+            }
+            if (sm.nn != cn) { kc = ldg_vec<W>(kg, sm.nn); cn = sm.nn; }
             rx[q] = x; ry[q] = y; rz[q] = z;
 #pragma unroll
             for (int b = 0; b < W; ++b) {
@@ -137,9 +148,11 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
         for (int q = len - 1; q >= 0; --q) {
             Sample sm;
             make_sample(rx[q], ry[q], rz[q], a.n0, a.n1, a.n2, a.kappa_mode, sm);
-            Vec<W> gc[8];
+            if (sm.cell[0] != g0 || sm.cell[7] != g7) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) gc[c] = ldg_vec<W>(Gg, sm.cell[c]);
+                for (int c = 0; c < 8; ++c) gc[c] = ldg_vec<W>(Gg, sm.cell[c]);
+                g0 = sm.cell[0]; g7 = sm.cell[7];
+            }
             float ddj[W], ddk[W];
 #pragma unroll
             for (int b = 0; b < W; ++b) {

@@ -33,6 +33,8 @@ __device__ __forceinline__ void gather(const float* __restrict__ jg, const float
 
 // PF = 1: the gathers of substep k+1 are issued before the update of substep k (positions do
 // not depend on I, so they can run ahead), which doubles the loads in flight per thread.
+// PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
+// the values from the previous substep, still in registers, are reused.
 template <int W, int PF>
 __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
 
     Sample sm;
     Gathered<W> gd;
+    int gnn = -1;   // kappa cell of the gathered values (PF = 0)
     make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
     if (PF) gather<W>(jg, kg, sm, gd);
 
@@ -79,11 +82,20 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
         z = __fadd_rn(z, dz);
         Sample nx;
         Gathered<W> ng;
+        // same 8 corners as the previous substep: the registers already hold their j values
+        const bool same_cells = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
         if (PF) {
             make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, nx);
             if (k + 1 < a.ns) gather<W>(jg, kg, nx, ng);
         } else {
-            gather<W>(jg, kg, sm, gd);
+            if (!same_cells) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) gd.j[c] = ldg_vec<W>(jg, sm.cell[c]);
+            }
+            if (sm.nn != gnn) {
+                gd.k = ldg_vec<W>(kg, sm.nn);
+                gnn = sm.nn;
+            }
         }
         float dep[W];
 #pragma unroll
@@ -99,7 +111,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
             dep[b] = I[b] * scale;
         }
         // the corner set is fixed by its lowest and highest corner
-        if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
+        if (!same_cells) {
             if (pc[0] >= 0) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
