@@ -191,6 +191,63 @@ def fwd_adjoint(args, dev, flush, stream):
             "adjoint_updates_per_s": U / (tb * 1e-3)}
 
 
+def batched(args, dev, stream):
+    """64 independent instances (edges from {32,48,64,96,128,160}, lognormal kappa with sigma_g in
+    [0.5, 1.5], 1-64 sources, N_Omega from {768, 3072, 12288}, ds 0.5, c dt = edge, 1-8 bins):
+    one autotuned persistent launch replayed from a CUDA graph, against the same instances
+    advanced one rt_advance call at a time. The inputs (2.6 GB) exceed L2, so no flush."""
+    import statistics as st
+    import torch
+    from paper_2511_09389_gb300 import inputs
+    from paper_2511_09389_gb300.api import Batch, Grid
+    probs = inputs.batch_instances(64)
+    dev_in = []
+    for p in probs:
+        d = {k: torch.from_numpy(v).to(dev) for k, v in (("j", p.j), ("kappa", p.kappa), ("sources", p.sources))}
+        d.update(num_rays=p.num_rays, step_size=p.step_size, radiation_velocity=1.0, time_step=p.time_step)
+        dev_in.append(d)
+    b = Batch(dev_in, autotune=True)
+    U = b.updates
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run()
+        e1.record(stream)
+        e1.synchronize()
+        tb.append(e0.elapsed_time(e1))
+    grids = [Grid(p.shape, 8, autotune=True) for p in probs]
+    outs = [torch.empty_like(d["j"]) for d in dev_in]
+
+    def one_by_one():
+        for g, d, o in zip(grids, dev_in, outs):
+            g.advance(d["j"], d["kappa"], d["sources"], d["num_rays"], d["step_size"], 1.0, d["time_step"], out=o)
+    for _ in range(args.warmup):
+        one_by_one()
+    torch.cuda.synchronize()
+    t1 = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_by_one()
+        e1.record(stream)
+        e1.synchronize()
+        t1.append(e0.elapsed_time(e1))
+    rel = max(float((o - bo).norm() / bo.norm()) for o, bo in zip(outs, b.outputs))
+    mb, m1 = st.mean(tb), st.mean(t1)
+    b.close()
+    for g in grids:
+        g.close()
+    return {"value": U / (mb * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": mb,
+            "one_by_one": {"value": U / (m1 * 1e-3), "ms_per_step": m1}, "speedup_vs_one_by_one": m1 / mb,
+            "max_rel_l2_batched_vs_one_by_one": rel,
+            "workload": "64 instances: edges {32..160}, 1-64 sources, N_Omega {768,3072,12288}, 1-8 bins, c*dt = edge",
+            "l2": "inputs (2.6 GB) larger than L2"}
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -302,6 +359,8 @@ def native_arm(args):
     }
 
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
+    if not args.no_batch:
+        line["batched"] = batched(args, dev, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -328,6 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (faster)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched measurement")
     ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_thread,block,prefetch' "
                                                "instead of autotuning (for reproducible profiles)")
     args = ap.parse_args()

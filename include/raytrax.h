@@ -172,6 +172,40 @@ rt_status rt_advance_noalloc(const float* j_map, const float* kappa_map, const f
                              float radiation_velocity, float time_step, int n_freq, float* out_field,
                              void* cuda_stream);
 
+/* ---- Batched persistent launch ----------------------------------------------------------
+   Many independent march problems (each its own grid shape, sources, lattice size, bins and
+   step) advanced by one persistent kernel, the whole run captured once in a CUDA graph. */
+typedef struct rt_batch rt_batch;
+
+typedef struct {
+    const float* j_map;          /* device [n_freq][n0][n1][n2] */
+    const float* kappa_map;      /* device, same shape */
+    const float* source_pos;     /* device [num_sources][3], grid coordinates */
+    int num_sources;             /* >= 1 */
+    int n0, n1, n2, n_freq;      /* >= 1 each */
+    int num_rays;                /* >= 1 */
+    float step_size, radiation_velocity, time_step;   /* as in rt_advance */
+    float* out_field;            /* device, same shape as j_map, OVERWRITTEN by each run */
+} rt_instance;
+
+/* Validate the instances, allocate the batch's scratch (packed copies, accumulators, lattice
+   tables, work queue) and build the work queue of 32-ray items (longest first). The buffers
+   named in inst[] are bound to the batch: each rt_batch_run reads and writes them in place.
+   opt: kappa_mode is honoured; autotune = 1 times the persistent block sizes on the first run.
+   Same results as one rt_advance per instance. */
+rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, const rt_options* opt);
+
+/* Advance every instance by its dt on the stream. The first call (optionally autotunes and)
+   captures clear / pack / persistent march / unpack into a CUDA graph on an internal stream;
+   every call then launches that graph on `cuda_stream` (NULL: legacy default stream). */
+rt_status rt_batch_run(rt_batch* batch, void* cuda_stream);
+
+/* Total updates (substeps x rays x sources x bins over all instances) of one run. */
+long long rt_batch_updates(const rt_batch* batch);
+
+/* Free the batch (synchronises the device). NULL is accepted. */
+rt_status rt_batch_destroy(rt_batch* batch);
+
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
    thread), threads per block, gather prefetch (0/1), and the march time the autotuner
    measured for it in ms (-1 when rt_options.autotune is 0). Any pointer may be NULL.

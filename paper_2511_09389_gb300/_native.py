@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ER
 EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
-           "rt_tuning_report", "rt_advance_noalloc")
+           "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
+           "rt_batch_destroy")
 
 
 class RTError(RuntimeError):
@@ -35,6 +36,14 @@ class rt_options(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
                 ("profile", ctypes.c_int), ("plan_width", ctypes.c_int), ("plan_block", ctypes.c_int),
                 ("plan_prefetch", ctypes.c_int)]
+
+
+class rt_instance(ctypes.Structure):
+    _fields_ = [("j_map", ctypes.c_void_p), ("kappa_map", ctypes.c_void_p), ("source_pos", ctypes.c_void_p),
+                ("num_sources", ctypes.c_int), ("n0", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
+                ("n_freq", ctypes.c_int), ("num_rays", ctypes.c_int), ("step_size", ctypes.c_float),
+                ("radiation_velocity", ctypes.c_float), ("time_step", ctypes.c_float),
+                ("out_field", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -84,6 +93,14 @@ def load(path: str = LIB_PATH):
         lib.rt_tuning_report.restype = i
         lib.rt_advance_noalloc.argtypes = [fp, fp, fp, i, i, i, i, i, f, f, f, i, fp, vp]
         lib.rt_advance_noalloc.restype = i
+        lib.rt_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(rt_instance), i, ctypes.POINTER(rt_options)]
+        lib.rt_batch_create.restype = i
+        lib.rt_batch_run.argtypes = [vp, vp]
+        lib.rt_batch_run.restype = i
+        lib.rt_batch_updates.argtypes = [vp]
+        lib.rt_batch_updates.restype = ctypes.c_longlong
+        lib.rt_batch_destroy.argtypes = [vp]
+        lib.rt_batch_destroy.restype = i
         _lib = lib
         return lib
 

@@ -218,6 +218,61 @@ class Grid:
         return base, nn
 
 
+class Batch:
+    """Many independent problems advanced by one persistent launch replayed from a CUDA graph.
+
+    instances: sequence of dicts with keys j, kappa, sources (CUDA float32 tensors), num_rays,
+    step_size, radiation_velocity, time_step and optionally out. The tensors are bound to the
+    batch: each run() reads them and overwrites the outputs in place (`outputs`).
+    """
+
+    def __init__(self, instances, *, kappa_mode: int = 0, autotune: bool = False, ns_cap: int = 0):
+        self._lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._keep, self.outputs = [], []
+        arr = (_native.rt_instance * len(instances))()
+        for i, d in enumerate(instances):
+            j = _grid_tensor(d["j"], "j")
+            k = _grid_tensor(d["kappa"], "kappa")
+            if j.shape != k.shape:
+                raise ValueError(f"instance {i}: j and kappa shapes differ")
+            src = torch.as_tensor(d["sources"], dtype=torch.float32, device=j.device).reshape(-1, 3).contiguous()
+            out = d.get("out")
+            out = torch.empty_like(j) if out is None else out
+            if out.shape != j.shape or not out.is_contiguous() or out.dtype != torch.float32:
+                raise ValueError(f"instance {i}: bad out tensor")
+            self._keep += [j, k, src, out]
+            self.outputs.append(out)
+            nf, n0, n1, n2 = j.shape
+            arr[i] = _native.rt_instance(j.data_ptr(), k.data_ptr(), src.data_ptr(), src.shape[0], n0, n1, n2, nf,
+                                         int(d["num_rays"]), float(d["step_size"]),
+                                         float(d.get("radiation_velocity", 1.0)), float(d.get("time_step", 1.0)),
+                                         out.data_ptr())
+        opt = _native.rt_options(0, int(kappa_mode), int(ns_cap), int(bool(autotune)), 0, 0, 0, 0, 0)
+        h = ctypes.c_void_p()
+        check(self._lib.rt_batch_create(ctypes.byref(h), arr, len(instances), ctypes.byref(opt)))
+        self._h = h
+
+    @property
+    def updates(self) -> int:
+        return int(self._lib.rt_batch_updates(self._h))
+
+    def run(self, stream=None):
+        check(self._lib.rt_batch_run(self._h, _stream_ptr(stream, self.device)))
+        return self.outputs
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            self._lib.rt_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 _grid_cache: dict = {}
 
 
@@ -239,4 +294,4 @@ def advance(j, kappa, sources, num_rays: int, step_size: float, radiation_veloci
     return out if j.dim() == 4 else out[0]
 
 
-__all__ = ["Grid", "advance", "num_substeps", "direction_table", "RTError"]
+__all__ = ["Grid", "Batch", "advance", "num_substeps", "direction_table", "RTError"]

@@ -1,40 +1,13 @@
-// march_fwd.cu -- forward march (paper Sec. 2, Eq. 2) and its layout kernels, sm_103a.
+// march_fwd.cu -- forward march of one problem (paper Sec. 2, Eq. 2) and its layout kernels.
 //
-// One thread marches one (ray, source, bin-group) lane through all N_s substeps. The W bins
-// of a group share the ray geometry (bins are a batch axis, Sec. 2 "Frequency-bin
-// agnosticism"), so j and kappa are read as W-wide vectors from a cell-major packed copy and
-// each of the 8 deposits is a single W-wide `red.global.add.v{W}.f32`. Rays of a block are
-// angular neighbours (the host sorts the lattice), so their gathers and deposits share
-// cache lines near the source.
-//
-// Consecutive substeps of a ray often fall in the same cell (ds < 1), and once a ray has left
-// the box its clamped corners stay fixed for long stretches. The deposits of such runs are
-// summed in registers and sent to memory once, when the corner set changes: fewer L2 atomics,
-// and far fewer tiny FP32 additions into the large sums that pile up on boundary voxels.
-#include "march_common.cuh"
+// One thread marches one (ray, source, bin-group) lane through all N_s substeps (march_lane.cuh).
+// Rays of a block are angular neighbours (the host sorts the lattice), so their gathers and
+// deposits share cache lines near the source.
+#include "march_lane.cuh"
 #include "rt_internal.h"
 
 namespace rt {
 
-// Gathers of one substep: the 8 j corners and the kappa cell, W bins each.
-template <int W>
-struct Gathered {
-    Vec<W> j[8];
-    Vec<W> k;
-};
-
-template <int W>
-__device__ __forceinline__ void gather(const float* __restrict__ jg, const float* __restrict__ kg,
-                                       const Sample& sm, Gathered<W>& gd) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) gd.j[c] = ldg_vec<W>(jg, sm.cell[c]);
-    gd.k = ldg_vec<W>(kg, sm.nn);
-}
-
-// PF = 1: the gathers of substep k+1 are issued before the update of substep k (positions do
-// not depend on I, so they can run ahead), which doubles the loads in flight per thread.
-// PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
-// the values from the previous substep, still in registers, are reused.
 template <int W, int PF>
 __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
@@ -44,102 +17,19 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     const int g = sg / a.nsrc;
     const int r = rb * blockDim.x + threadIdx.x;
     if (r >= a.ray_count) return;
-
     const long long ncell = (long long)a.n0 * a.n1 * a.n2;
-    const float* __restrict__ jg = a.jp + (size_t)g * ncell * W;
-    const float* __restrict__ kg = a.kp + (size_t)g * ncell * W;
-    float* __restrict__ og = a.acc + (size_t)g * ncell * W;
-
-    const float4 n = a.dirs[r];
-    const float dx = __fmul_rn(n.x, a.ds), dy = __fmul_rn(n.y, a.ds), dz = __fmul_rn(n.z, a.ds);
-    float x = a.src[3 * s + 0], y = a.src[3 * s + 1], z = a.src[3 * s + 2];
-
-    float I[W], tau[W];
-#pragma unroll
-    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
-    const float ds = a.ds, scale = a.dep_scale;
-
-    // pending deposit of the current run of substeps with an unchanged corner set
-    int pc[8];
-    float pend[8][W];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        pc[c] = -1;
-#pragma unroll
-        for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
-    }
-
-    Sample sm;
-    Gathered<W> gd;
-    int gnn = -1;   // kappa cell of the gathered values (PF = 0)
-    make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
-    if (PF) gather<W>(jg, kg, sm, gd);
-
-#pragma unroll 1
-    for (int k = 0; k < a.ns; ++k) {
-        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
-        y = __fadd_rn(y, dy);
-        z = __fadd_rn(z, dz);
-        Sample nx;
-        Gathered<W> ng;
-        // same 8 corners as the previous substep: the registers already hold their j values
-        const bool same_cells = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
-        if (PF) {
-            make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, nx);
-            if (k + 1 < a.ns) gather<W>(jg, kg, nx, ng);
-        } else {
-            if (!same_cells) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) gd.j[c] = ldg_vec<W>(jg, sm.cell[c]);
-            }
-            if (sm.nn != gnn) {
-                gd.k = ldg_vec<W>(kg, sm.nn);
-                gnn = sm.nn;
-            }
-        }
-        float dep[W];
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            float jk = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
-            const float kds = gd.k.v[b] * ds;
-            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
-            const float em = expf(-tau[b]);               // exp(-tau_k)
-            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
-            tau[b] += kds;                                // Eq. 2: tau_{k+1}
-            dep[b] = I[b] * scale;
-        }
-        // the corner set is fixed by its lowest and highest corner
-        if (!same_cells) {
-            if (pc[0] >= 0) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                pc[c] = sm.cell[c];
-#pragma unroll
-                for (int b = 0; b < W; ++b) pend[c][b] = sm.w[c] * dep[b];
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-#pragma unroll
-                for (int b = 0; b < W; ++b) pend[c][b] = fmaf(sm.w[c], dep[b], pend[c][b]);
-            }
-        }
-        if (PF) {
-            sm = nx;
-            gd = ng;
-        } else {
-            make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
-        }
-    }
-    if (pc[0] >= 0) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
-    }
+    Lane L;
+    L.jg = a.jp + (size_t)g * ncell * W;
+    L.kg = a.kp + (size_t)g * ncell * W;
+    L.og = a.acc + (size_t)g * ncell * W;
+    L.n = a.dirs[r];
+    L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
+    L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
+    L.ns = a.ns;
+    L.ds = a.ds;
+    L.scale = a.dep_scale;
+    L.kappa_mode = a.kappa_mode;
+    march_lane<W, PF>(L);
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {

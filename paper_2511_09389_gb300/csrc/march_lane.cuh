@@ -1,0 +1,146 @@
+// march_lane.cuh -- the march of one (ray, source, bin group) lane (paper Sec. 2, Eq. 2).
+//
+// Shared by the single-problem kernel (march_fwd.cu) and the batched persistent kernel
+// (march_batch.cu). The W bins of a group share the ray geometry (bins are a batch axis, Sec. 2
+// "Frequency-bin agnosticism"), so j and kappa are read as W-wide vectors from a cell-major
+// packed copy and each deposit is one W-wide `red.global.add.v{W}.f32`.
+//
+// Consecutive substeps of a ray often fall in the same cell (ds < 1), and once a ray has left
+// the box its clamped corners stay fixed for long stretches. The deposits of such runs are
+// summed in registers and sent to memory once, when the corner set changes: fewer L2 atomics,
+// and far fewer tiny FP32 additions into the large sums that pile up on boundary voxels.
+#pragma once
+
+#include "march_common.cuh"
+
+namespace rt {
+
+// Gathers of one substep: the 8 j corners and the kappa cell, W bins each.
+template <int W>
+struct Gathered {
+    Vec<W> j[8];
+    Vec<W> k;
+};
+
+template <int W>
+__device__ __forceinline__ void gather(const float* __restrict__ jg, const float* __restrict__ kg,
+                                       const Sample& sm, Gathered<W>& gd) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) gd.j[c] = ldg_vec<W>(jg, sm.cell[c]);
+    gd.k = ldg_vec<W>(kg, sm.nn);
+}
+
+// Geometry and data of one lane. jg / kg / og point at the lane's bin group.
+struct Lane {
+    const float* __restrict__ jg;
+    const float* __restrict__ kg;
+    float* __restrict__ og;
+    float4 n;                 // direction
+    float sx, sy, sz;         // source position
+    int n0, n1, n2;
+    int ns;
+    float ds;
+    float scale;              // factor of every deposit
+    int kappa_mode;
+};
+
+// PF = 1: the gathers of substep k+1 are issued before the update of substep k (positions do
+// not depend on I, so they can run ahead), which doubles the loads in flight per thread.
+// PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
+// the values from the previous substep, still in registers, are reused.
+template <int W, int PF>
+__device__ __forceinline__ void march_lane(const Lane& L) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    float* __restrict__ og = L.og;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = L.sx, y = L.sy, z = L.sz;
+
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    const float ds = L.ds, scale = L.scale;
+    // pending deposit of the current run of substeps with an unchanged corner set
+    int pc[8];
+    float pend[8][W];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = -1;
+#pragma unroll
+        for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
+    }
+
+    Sample sm;
+    Gathered<W> gd;
+    int gnn = -1;   // kappa cell of the gathered values (PF = 0)
+    make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+    if (PF) gather<W>(jg, kg, sm, gd);
+
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
+        y = __fadd_rn(y, dy);
+        z = __fadd_rn(z, dz);
+        Sample nx;
+        Gathered<W> ng;
+        // same 8 corners as the previous substep: the registers already hold their j values
+        const bool same_cells = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
+        if (PF) {
+            make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx);
+            if (k + 1 < L.ns) gather<W>(jg, kg, nx, ng);
+        } else {
+            if (!same_cells) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) gd.j[c] = ldg_vec<W>(jg, sm.cell[c]);
+            }
+            if (sm.nn != gnn) {
+                gd.k = ldg_vec<W>(kg, sm.nn);
+                gnn = sm.nn;
+            }
+        }
+        float dep[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float jk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
+            const float kds = gd.k.v[b] * ds;
+            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
+            const float em = expf(-tau[b]);               // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+            tau[b] += kds;                                // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+        // the corner set is fixed by its lowest and highest corner
+        if (!same_cells) {
+            if (pc[0] >= 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                pc[c] = sm.cell[c];
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = sm.w[c] * dep[b];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = fmaf(sm.w[c], dep[b], pend[c][b]);
+            }
+        }
+        if (PF) {
+            sm = nx;
+            gd = ng;
+        } else {
+            make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+        }
+    }
+    if (pc[0] >= 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
+    }
+}
+
+}  // namespace rt

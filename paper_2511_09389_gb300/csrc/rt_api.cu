@@ -219,7 +219,11 @@ struct rt_grid {
 
 namespace {
 
-int num_substeps(float ds, float c, float dt, int cap) {
+int num_substeps(float ds, float c, float dt, int cap) { return rt::substeps(ds, c, dt, cap); }
+
+}  // namespace
+
+int rt::substeps(float ds, float c, float dt, int cap) {
     if (!std::isfinite(ds) || !std::isfinite(c) || !std::isfinite(dt)) return -1;
     if (!(ds > 0.0f) || !(c > 0.0f) || !(dt >= 0.0f)) return -1;
     const double q = (double)c * (double)dt / (double)ds;
@@ -229,6 +233,8 @@ int num_substeps(float ds, float c, float dt, int cap) {
     if (cap > 0 && ns > cap) ns = cap;
     return ns;
 }
+
+namespace {
 
 rt_status check_device(rt_grid* g) {
     int dev = -1;

@@ -1,0 +1,302 @@
+// rt_batch.cu -- host side of the batched persistent launch (rt_batch_* in raytrax.h).
+//
+// At creation the instances are validated, their scratch (packed j / kappa for instances with
+// two or more bins, one contiguous accumulator region for all) and lattice tables are
+// allocated, and the work queue of 32-ray items is built longest-first. The first run captures
+// counter clear, accumulator clear, batched pack, persistent march and batched unpack into one
+// CUDA graph (after an optional timing of persistent block sizes); every run launches it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "raytrax.h"
+#include "rt_internal.h"
+
+namespace {
+
+rt_status err(rt_status st, const char* fmt, ...) {
+    char buf[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return rt::set_error(st, buf);
+}
+
+rt_status cuda_err(cudaError_t e, const char* what) {
+    return err(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_batch: %s: %s", what,
+               cudaGetErrorString(e));
+}
+
+#define B_CUDA(call, what)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_err(e_, what);    \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct rt_batch {
+    int device = 0;
+    rt_options opt{};
+    std::vector<rt::BatchInst> host;
+    rt::BatchInst* d_insts = nullptr;
+    int4* d_items = nullptr;          // items of width 4, then 2, then 1
+    int n_items = 0;
+    int w_first[3] = {0, 0, 0};       // first item of widths 4, 2, 1
+    int w_count[3] = {0, 0, 0};
+    int* d_counter = nullptr;         // one counter per width
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    unsigned char* scratch = nullptr;
+    float* acc = nullptr;
+    size_t acc_bytes = 0;
+    std::map<int, float4*> dirs;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int block = 64, sms = 0;
+    long long updates = 0;
+    long long max_elems = 0;          // largest groups * ncell (sizes the layout kernels)
+
+    static int widx(int W) { return W == 4 ? 0 : (W == 2 ? 1 : 2); }
+    int grid_for(int W) const { return sms * rt::march_batch_blocks_per_sm(W, block); }
+
+    void release() {
+        cudaDeviceSynchronize();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+        for (auto s : side)
+            if (s) cudaStreamDestroy(s);
+        if (fork) cudaEventDestroy(fork);
+        for (auto e : join)
+            if (e) cudaEventDestroy(e);
+        for (auto& d : dirs) cudaFree(d.second);
+        cudaFree(d_insts);
+        cudaFree(d_items);
+        cudaFree(d_counter);
+        cudaFree(scratch);
+    }
+
+    // The three widths run as concurrent branches (streams side[0], side[1] fork from st and
+    // join back), so the tail of one persistent kernel overlaps the start of the next.
+    rt_status march(cudaStream_t st) {
+        const int widths[3] = {4, 2, 1};
+        cudaStream_t on[3] = {st, side[0], side[1]};
+        B_CUDA(cudaEventRecord(fork, st), "fork");
+        for (int i = 1; i < 3; ++i) B_CUDA(cudaStreamWaitEvent(on[i], fork, 0), "fork wait");
+        for (int i = 0; i < 3; ++i)
+            B_CUDA(rt::launch_march_batch(widths[i], d_insts, d_items + w_first[i], w_count[i], d_counter + i,
+                                          grid_for(widths[i]), block, on[i]),
+                   "march launch");
+        for (int i = 1; i < 3; ++i) {
+            B_CUDA(cudaEventRecord(join[i - 1], on[i]), "join");
+            B_CUDA(cudaStreamWaitEvent(st, join[i - 1], 0), "join wait");
+        }
+        return RT_OK;
+    }
+
+    rt_status enqueue(cudaStream_t st) {
+        B_CUDA(cudaMemsetAsync(d_counter, 0, 3 * sizeof(int), st), "clear work counters");
+        B_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, st), "clear accumulators");
+        const int n = (int)host.size();
+        B_CUDA(rt::launch_pack_batch(d_insts, n, max_elems, 0, st), "pack(j) launch");
+        B_CUDA(rt::launch_pack_batch(d_insts, n, max_elems, 1, st), "pack(kappa) launch");
+        rt_status rs = march(st);
+        if (rs != RT_OK) return rs;
+        B_CUDA(rt::launch_unpack_batch(d_insts, n, max_elems, st), "unpack launch");
+        return RT_OK;
+    }
+};
+
+extern "C" {
+
+rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, const rt_options* opt) {
+    if (!out) return err(RT_ERR_INVALID_ARG, "rt_batch_create: out is NULL");
+    *out = nullptr;
+    if (n_inst < 1 || !inst) return err(RT_ERR_INVALID_ARG, "rt_batch_create: need n_inst >= 1 instances");
+    rt_options o{};
+    if (opt) o = *opt;
+    if (o.kappa_mode != 0 && o.kappa_mode != 1) return err(RT_ERR_INVALID_ARG, "rt_batch_create: bad kappa_mode");
+    if (o.deterministic) return err(RT_ERR_UNSUPPORTED, "rt_batch_create: deterministic mode is not supported");
+
+    // ---- validate, size the scratch ----
+    std::vector<rt::BatchInst> h(n_inst);
+    size_t packed_total = 0, acc_total = 0;
+    long long updates = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const rt_instance& q = inst[i];
+        if (q.n0 < 1 || q.n1 < 1 || q.n2 < 1 || q.n_freq < 1 || q.num_sources < 1 || q.num_rays < 1)
+            return err(RT_ERR_INVALID_ARG, "rt_batch_create: instance %d: extents, n_freq, num_sources and "
+                                           "num_rays must be >= 1", i);
+        if (!q.j_map || !q.kappa_map || !q.source_pos || !q.out_field)
+            return err(RT_ERR_INVALID_ARG, "rt_batch_create: instance %d: NULL buffer", i);
+        if (q.out_field == q.j_map || q.out_field == q.kappa_map)
+            return err(RT_ERR_INVALID_ARG, "rt_batch_create: instance %d: out_field aliases an input", i);
+        const int ns = rt::substeps(q.step_size, q.radiation_velocity, q.time_step, o.ns_cap);
+        if (ns < 0 || !(q.step_size > 0.0f) || !(q.radiation_velocity > 0.0f) || !(q.time_step >= 0.0f) ||
+            (double)ns * q.step_size > 1.6e7)
+            return err(RT_ERR_INVALID_ARG, "rt_batch_create: instance %d: invalid step_size / "
+                                           "radiation_velocity / time_step", i);
+        const long long ncell = (long long)q.n0 * q.n1 * q.n2;
+        const int W = q.n_freq == 1 ? 1 : (q.n_freq == 2 ? 2 : 4);
+        const int groups = (q.n_freq + W - 1) / W;
+        if (ncell * groups * W >= (1LL << 31))
+            return err(RT_ERR_INVALID_ARG, "rt_batch_create: instance %d: grid too large", i);
+        rt::BatchInst& b = h[i];
+        b = rt::BatchInst{};
+        b.j = q.j_map; b.kappa = q.kappa_map; b.out = q.out_field; b.src = q.source_pos;
+        b.n0 = q.n0; b.n1 = q.n1; b.n2 = q.n2; b.n_freq = q.n_freq; b.W = W; b.groups = groups;
+        b.ns = ns; b.nsrc = q.num_sources; b.ray_count = q.num_rays; b.kappa_mode = o.kappa_mode;
+        b.ds = q.step_size;
+        b.scale = (float)(4.0 * 3.14159265358979323846 / (double)q.num_rays);
+        const size_t field = sizeof(float) * (size_t)groups * ncell * W;
+        if (W > 1) packed_total += 2 * align256(field);
+        acc_total += align256(field);
+        updates += (long long)ns * q.num_rays * q.num_sources * q.n_freq;
+    }
+
+    rt_batch* B = new (std::nothrow) rt_batch();
+    if (!B) return err(RT_ERR_OOM, "rt_batch_create: host allocation failed");
+    B->opt = o;
+    B->updates = updates;
+    for (const auto& b : h) B->max_elems = std::max(B->max_elems, (long long)b.groups * b.n0 * b.n1 * b.n2);
+    auto fail_free = [&](rt_status st) { B->release(); delete B; return st; };
+    cudaError_t e = cudaGetDevice(&B->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device);
+    if (e == cudaSuccess) e = cudaMalloc(&B->scratch, packed_total + acc_total);
+    if (e != cudaSuccess) return fail_free(cuda_err(e, "scratch allocation"));
+
+    // ---- lay out scratch, lattice tables ----
+    size_t off = 0;
+    for (auto& b : h) {
+        const size_t field = sizeof(float) * (size_t)b.groups * b.n0 * b.n1 * b.n2 * b.W;
+        if (b.W > 1) {
+            b.jp_w = (float*)(B->scratch + off); off += align256(field);
+            b.kp_w = (float*)(B->scratch + off); off += align256(field);
+            b.jp = b.jp_w; b.kp = b.kp_w;
+        } else {
+            b.jp = b.j; b.kp = b.kappa;
+        }
+    }
+    B->acc = (float*)(B->scratch + off);
+    B->acc_bytes = acc_total;
+    for (auto& b : h) {
+        b.acc = (float*)(B->scratch + off);
+        off += align256(sizeof(float) * (size_t)b.groups * b.n0 * b.n1 * b.n2 * b.W);
+        auto it = B->dirs.find(b.ray_count);
+        if (it == B->dirs.end()) {
+            std::vector<float4> t(b.ray_count);
+            std::vector<uint32_t> key(b.ray_count);
+            std::vector<int> order(b.ray_count);
+            rt::sorted_lattice(b.ray_count, 0, b.ray_count, t.data(), key.data(), order.data());
+            float4* d = nullptr;
+            e = cudaMalloc(&d, sizeof(float4) * t.size());
+            if (e == cudaSuccess) e = cudaMemcpy(d, t.data(), sizeof(float4) * t.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cudaFree(d); return fail_free(cuda_err(e, "lattice table")); }
+            it = B->dirs.emplace(b.ray_count, d).first;
+        }
+        b.dirs = it->second;
+    }
+
+    // ---- work queue: 32-ray items, longest march first ----
+    // bin group outside sources: one group's packed j, kappa and accumulator stay L2-resident
+    // while all of its sources march
+    std::vector<int4> items;
+    for (int i = 0; i < n_inst; ++i)
+        for (int g = 0; g < h[i].groups; ++g)
+            for (int s = 0; s < h[i].nsrc; ++s)
+                for (int r = 0; r < h[i].ray_count; r += 32) items.push_back(make_int4(i, s, g, r));
+    // grouped by width (4, 2, 1), longest march first within a width
+    std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) {
+        const int wa = rt_batch::widx(h[a.x].W), wb = rt_batch::widx(h[b.x].W);
+        if (wa != wb) return wa < wb;
+        return h[a.x].ns > h[b.x].ns;
+    });
+    for (size_t k = 0; k < items.size(); ++k) B->w_count[rt_batch::widx(h[items[k].x].W)]++;
+    B->w_first[1] = B->w_count[0];
+    B->w_first[2] = B->w_count[0] + B->w_count[1];
+    if (items.size() > 0x7fffffff) return fail_free(err(RT_ERR_INVALID_ARG, "rt_batch_create: too many work items"));
+    B->n_items = (int)items.size();
+    e = cudaMalloc(&B->d_insts, sizeof(rt::BatchInst) * h.size());
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_insts, h.data(), sizeof(rt::BatchInst) * h.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(int4) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(B->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&B->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail_free(cuda_err(e, "work queue"));
+    B->host = std::move(h);
+    B->block = 64;
+    *out = B;
+    return RT_OK;
+}
+
+rt_status rt_batch_run(rt_batch* B, void* cuda_stream) {
+    if (!B) return err(RT_ERR_INVALID_ARG, "rt_batch_run: batch is NULL");
+    int dev = -1;
+    B_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != B->device) return err(RT_ERR_INVALID_ARG, "rt_batch_run: current device differs from the batch's");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!B->exec) {
+        if (B->opt.autotune) {
+            // time the persistent march for a few block sizes on the real inputs (untimed clears)
+            cudaEvent_t e0, e1;
+            B_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+            B_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+            float best = 3.0e38f;
+            int best_block = B->block;
+            rt_status rs = RT_OK;
+            for (int blk : {32, 64, 128, 256}) {
+                B->block = blk;
+                if ((rs = B->enqueue(B->cap)) != RT_OK) break;   // warm, packs the inputs
+                cudaError_t e = cudaMemsetAsync(B->d_counter, 0, 3 * sizeof(int), B->cap);
+                if (e == cudaSuccess) e = cudaMemsetAsync(B->acc, 0, B->acc_bytes, B->cap);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, B->cap);
+                if (e == cudaSuccess && (rs = B->march(B->cap)) != RT_OK) break;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, B->cap);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) { rs = cuda_err(e, "autotune run"); break; }
+                if (ms < best) { best = ms; best_block = blk; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rs != RT_OK) return rs;
+            B->block = best_block;
+        }
+        cudaGraph_t graph = nullptr;
+        B_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        rt_status rs = B->enqueue(B->cap);
+        cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+        if (rs != RT_OK) { if (graph) cudaGraphDestroy(graph); return rs; }
+        if (e != cudaSuccess) return cuda_err(e, "end capture");
+        e = cudaGraphInstantiate(&B->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { B->exec = nullptr; return cuda_err(e, "graph instantiate"); }
+    }
+    B_CUDA(cudaGraphLaunch(B->exec, st), "graph launch");
+    return RT_OK;
+}
+
+long long rt_batch_updates(const rt_batch* B) { return B ? B->updates : 0; }
+
+rt_status rt_batch_destroy(rt_batch* B) {
+    if (!B) return RT_OK;
+    B->release();
+    delete B;
+    return RT_OK;
+}
+
+}  // extern "C"

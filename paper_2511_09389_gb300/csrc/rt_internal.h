@@ -13,6 +13,10 @@ namespace rt {
 // entries (the function allocates nothing).
 void sorted_lattice(int n, int begin, int end, float4* out, uint32_t* key, int* order);
 
+// N_s = ceil(c dt / ds) in FP64 with a 1e-9 relative guard, capped when cap > 0; -1 if the
+// arguments are invalid or N_s does not fit in an int (paper Sec. 2 after Eq. 2).
+int substeps(float ds, float c, float dt, int cap);
+
 // Record a message for rt_last_error() on this thread and return st.
 rt_status set_error(rt_status st, const char* msg);
 
@@ -80,5 +84,30 @@ struct BackArgs {
 size_t backward_ckpt_floats(const BackArgs& a, int W);
 // W in {1, 2, 4}, a.stride in {8, 16, 32}.
 cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st);
+
+// One instance of a batched launch (device-resident table entry).
+struct BatchInst {
+    const float* j;         // caller's j   [n_freq][ncell]
+    const float* kappa;     // caller's kappa
+    float* out;             // caller's field (overwritten)
+    const float* jp;        // march inputs: packed copies (W > 1) or the caller's arrays (W = 1)
+    const float* kp;
+    float* jp_w;            // writable packed copies (W > 1), else NULL
+    float* kp_w;
+    float* acc;             // packed accumulator [groups][ncell][W]
+    const float4* dirs;     // sorted lattice of ray_count rays
+    const float* src;       // device [nsrc][3]
+    int n0, n1, n2, n_freq, W, groups, ns, nsrc, ray_count, kappa_mode;
+    float ds, scale;
+};
+
+int march_batch_blocks_per_sm(int W, int block);
+// items of width-W instances: (instance, source, bin group, first ray) x n_items;
+// counter: device int, zero at launch
+cudaError_t launch_march_batch(int W, const BatchInst* insts, const int4* items, int n_items, int* counter,
+                               int grid, int block, cudaStream_t st);
+// max_elems: the largest groups * ncell over the instances (sizes the grid)
+cudaError_t launch_pack_batch(const BatchInst* insts, int n_inst, long long max_elems, int which, cudaStream_t st);
+cudaError_t launch_unpack_batch(const BatchInst* insts, int n_inst, long long max_elems, cudaStream_t st);
 
 }  // namespace rt
