@@ -53,7 +53,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("march_fwd.cu", "march_common.cuh"):
+    for name in ("march_fwd.cu", "march_lane.cuh", "march_common.cuh"):
         with open(os.path.join(ROOT, "paper_2511_09389_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
