@@ -172,3 +172,37 @@ def trace_ray(j, kappa, source, num_rays: int, ray: int, step_size: float, num_s
     if rc != 0:
         raise ValueError("oracle_trace_ray: invalid arguments")
     return base, nn, I
+
+
+def conv3d_fwd(x, w, bias=None, dilation: int = 1) -> np.ndarray:
+    """3x3x3 'same' cross-correlation with zero padding and dilation (conv_oracle.c), FP64.
+    x: [B, Ci, D, H, W]; w: [Co, Ci, 3, 3, 3]; bias: [Co] or None. Returns [B, Co, D, H, W]."""
+    x = _f64(x)
+    w = _f64(w)
+    B, Ci, D, H, W = x.shape
+    Co = w.shape[0]
+    assert w.shape == (Co, Ci, 3, 3, 3)
+    b = None if bias is None else _f64(bias)
+    y = np.empty((B, Co, D, H, W), np.float64)
+    rc = _load().oracle_conv3d_fwd(_ptr(x), _ptr(w), _ptr(b) if b is not None else None, B, Ci, Co, D, H, W,
+                                   int(dilation), _ptr(y))
+    if rc != 0:
+        raise ValueError("oracle_conv3d_fwd: invalid arguments")
+    return y
+
+
+def conv3d_bwd(x, w, gy, dilation: int = 1):
+    """(dL/dx, dL/dw, dL/dbias) of conv3d_fwd for dL/dy = gy, FP64."""
+    x = _f64(x)
+    w = _f64(w)
+    gy = _f64(gy)
+    B, Ci, D, H, W = x.shape
+    Co = w.shape[0]
+    gx = np.empty_like(x)
+    gw = np.empty_like(w)
+    gb = np.empty(Co, np.float64)
+    rc = _load().oracle_conv3d_bwd(_ptr(x), _ptr(w), None, B, Ci, Co, D, H, W, int(dilation), _ptr(gy),
+                                   _ptr(gx), _ptr(gw), _ptr(gb))
+    if rc != 0:
+        raise ValueError("oracle_conv3d_bwd: invalid arguments")
+    return gx, gw, gb
