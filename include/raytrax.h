@@ -206,6 +206,43 @@ long long rt_batch_updates(const rt_batch* batch);
 /* Free the batch (synchronises the device). NULL is accepted. */
 rt_status rt_batch_destroy(rt_batch* batch);
 
+/* ---- Convolutional surrogate: building blocks ----------------------------------------
+   A 3-D CNN maps (log kappa, log(1 + j)) to the log of the field. Its 3x3x3 convolutions run on
+   the tensor cores (tcgen05, BF16 operands, FP32 accumulate). Activations use the CP8 layout:
+   bf16 [B][P][D][H][W][8] holding channel c at plane c / 8, lane c % 8, with
+   P = rt_cp8_planes(C) = 2 * ceil(C / 16) planes (channels beyond C are zero). The
+   convolution is the "same" cross-correlation with zero padding and dilation d:
+     y[b][o][p] = bias[o] + sum_{i, tap} w[o][i][tap] x[b][i][p + (tap - centre) * d].
+   All buffers are device memory; calls are asynchronous on the stream. */
+int rt_cp8_planes(int channels);
+
+/* FP32 [B][C][D][H][W] -> CP8 (dst holds B * P * D*H*W * 8 bf16), and back. */
+rt_status rt_cp8_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* cuda_stream);
+rt_status rt_cp8_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* cuda_stream);
+
+/* Pack FP32 weights w[c_out][c_in][27] (tap = kz*9 + ky*3 + kx) into the kernel's bf16 layout
+   [27][P_k][N][8]. transpose = 0: for the forward convolution (P_k = P(c_in), N = c_out rounded
+   up to 16). transpose = 1: for the data gradient, i.e. the convolution with flipped taps that
+   maps c_out channels back to c_in (P_k = P(c_out), N = c_in rounded up to 16).
+   1 <= c_in, c_out <= 32. */
+rt_status rt_conv3d_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed,
+                                 void* cuda_stream);
+
+/* One convolution layer on the tensor cores. x: CP8 with P(c_in) planes; w_packed from
+   rt_conv3d_pack_weights; bias [c_out] or NULL; act 0 = identity, 1 = LeakyReLU(slope).
+   mask (CP8, P(c_out) planes, or NULL): outputs where mask <= 0 are multiplied by slope before
+   the activation (the LeakyReLU derivative when back-propagating). Outputs: y (CP8, P(c_out)
+   planes) and/or y_f32 ([B][D][H][W], FP32 channel 0). Requires W == 64, even H,
+   1 <= c_in, c_out <= 32. Waits inside the kernel are bounded: a timeout is reported by
+   rt_device_status. */
+rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in, const void* w_packed,
+                            const float* bias, int c_out, int dilation, int act, float slope,
+                            const void* mask, void* y, float* y_f32, void* cuda_stream);
+
+/* Synchronising read-and-clear of this device's kernel error word: RT_OK, or RT_ERR_TIMEOUT
+   with *code = which wait gave up (1: stage free, 2: stage loaded, 3: accumulator ready). */
+rt_status rt_device_status(int* code);
+
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
    thread), threads per block, gather prefetch (0/1), and the march time the autotuner
    measured for it in ms (-1 when rt_options.autotune is 0). Any pointer may be NULL.

@@ -20,7 +20,8 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
-           "rt_batch_destroy")
+           "rt_batch_destroy", "rt_cp8_planes", "rt_cp8_from_f32", "rt_cp8_to_f32", "rt_conv3d_pack_weights",
+           "rt_conv3d_forward", "rt_device_status")
 
 
 class RTError(RuntimeError):
@@ -101,6 +102,18 @@ def load(path: str = LIB_PATH):
         lib.rt_batch_updates.restype = ctypes.c_longlong
         lib.rt_batch_destroy.argtypes = [vp]
         lib.rt_batch_destroy.restype = i
+        lib.rt_cp8_planes.argtypes = [i]
+        lib.rt_cp8_planes.restype = i
+        lib.rt_cp8_from_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
+        lib.rt_cp8_from_f32.restype = i
+        lib.rt_cp8_to_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
+        lib.rt_cp8_to_f32.restype = i
+        lib.rt_conv3d_pack_weights.argtypes = [vp, i, i, i, vp, vp]
+        lib.rt_conv3d_pack_weights.restype = i
+        lib.rt_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, i, f, vp, vp, vp, vp]
+        lib.rt_conv3d_forward.restype = i
+        lib.rt_device_status.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        lib.rt_device_status.restype = i
         _lib = lib
         return lib
 

@@ -1,0 +1,384 @@
+// conv3d_tc.cu -- 3x3x3 convolution ("same" zero padding, dilation d) as an implicit GEMM on the
+// 5th-generation tensor cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory).
+//
+// Activations use the chunk-planar layout CP8: bf16 [batch][C/8][D][H][W][8], i.e. planes of
+// 8 channels in which consecutive voxels are consecutive 16-byte rows. For one output tile of
+// M = 128 voxels (two x-rows of 64 at fixed batch, z, y0) and one kernel tap (dz, dy, dx), the
+// input rows the tap needs form a box (8 ch, 64 x, 2 y, 1 z, C/8 planes) of that tensor,
+// shifted by (dx, dy, dz) * d. One TMA tensor load fetches it; out-of-range coordinates read
+// zeros, which is exactly the convolution's zero padding. In shared memory the box is, per
+// plane, 128 consecutive 16-byte rows: the canonical no-swizzle K-major operand layout (core
+// matrices of 8 rows x 16 B; 128 B between row groups, one plane between K halves). So A is
+// read by the tensor core straight from the TMA destination, and the 27 taps are 27 boxes.
+//
+// B (weights) sits in shared memory for the whole kernel as [tap][C_in/8][C_out][8] (same
+// layout, N = C_out rows). Per tap: C_in/16 MMAs of M=128, N=C_out(16 or 32), K=16 into one
+// TMEM accumulator of 32 columns. Roles: thread 0 of warp 0 issues TMA loads into a 4-stage
+// ring, thread 0 of warp 1 issues MMAs and commits each stage back to its "empty" barrier, and
+// all four warps read the accumulator (32 TMEM lanes each) for the epilogue: bias, optional
+// sign mask from another activation (the LeakyReLU derivative in the backward pass), LeakyReLU,
+// bf16 store in CP8 and/or an FP32 copy of channel 0.
+//
+// Every wait is bounded (about one second of global time): on timeout the kernel records an
+// error word, stops issuing work, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_internal.h"
+
+namespace rt {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Wait until the phase with the given parity has completed; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((i & 63) == 63 && global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading (K-direction) and stride
+// (M/N-direction) byte offsets between 8x16-byte core matrices; bits 46-48 hold 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kStages = 4;
+constexpr int kTmemCols = 32;
+
+struct ConvArgs {
+    const uint4* w_packed;            // [27][KC][NCO][8] bf16 in 16-byte units
+    const float* bias;                // [c_out] or NULL
+    const __nv_bfloat16* mask_src;    // CP8 [B][NCO/8][D][H][W][8] or NULL
+    __nv_bfloat16* y;                 // CP8 [B][NCO/8][D][H][W][8] or NULL
+    float* y_f32;                     // [B][D][H][W] (channel 0) or NULL
+    int B, D, H, W, c_out, dil, act;
+    float slope;
+    int n_tiles;
+    int* err;
+};
+
+template <int KC, int NCO>
+struct ConvSmem {
+    static constexpr int kWBytes = 27 * KC * NCO * 16;
+    static constexpr int kWAligned = (kWBytes + 1023) / 1024 * 1024;
+    static constexpr int kAStage = KC * 2048;               // KC planes x 128 rows x 16 B
+    static constexpr int kBarOff = kWAligned + kStages * kAStage;
+    static constexpr int kBytes = kBarOff + (2 * kStages + 1) * 8 + 16;
+};
+
+}  // namespace
+
+template <int KC, int NCO>
+__global__ void __launch_bounds__(128, 1) k_conv3d_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
+    using L = ConvSmem<KC, NCO>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sw = smem;
+    unsigned char* sa = smem + L::kWAligned;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+    uint64_t* empty = full + kStages;
+    uint64_t* accum = empty + kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights -> shared memory with ordinary stores, made visible to the tensor core below
+    for (int i = tid; i < L::kWBytes / 16; i += 128)
+        reinterpret_cast<uint4*>(sw)[i] = __ldg(a.w_packed + i);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    constexpr uint32_t idesc = idesc_bf16(128, NCO);
+    const int half_h = a.H >> 1;
+    const int tiles_per_b = a.D * half_h;
+    constexpr int KCO = NCO / 8;
+    int it = 0;       // running (tile, tap) counter: stage = it % kStages, phase = (it / kStages) & 1
+    int tcount = 0;   // tiles finished by this CTA: parity of the accumulator barrier
+
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++tcount, it += 27) {
+        if (*abort_flag) break;
+        const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
+        const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
+        if (warp == 0 && lane == 0) {
+            // producer: one TMA box per tap
+            for (int tap = 0; tap < 27; ++tap) {
+                const int q = it + tap, s = q % kStages;
+                const uint32_t ph = (uint32_t)(q / kStages) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 1); break; }
+                mbar_expect_tx(&full[s], L::kAStage);
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                tma_load_5d(sa + s * L::kAStage, &tmap, &full[s], 0, dx * a.dil, y0 + dy * a.dil, z + dz * a.dil,
+                            b * KC);
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer: KC/2 MMAs (K = 16 each) per tap, then release the stage
+            bool ok = true;
+            for (int tap = 0; tap < 27; ++tap) {
+                const int q = it + tap, s = q % kStages;
+                const uint32_t ph = (uint32_t)(q / kStages) & 1u;
+                if (!mbar_wait(&full[s], ph)) { *abort_flag = 1; atomicExch(a.err, 2); ok = false; break; }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(sa + s * L::kAStage);
+                const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * KC * NCO * 16);
+#pragma unroll
+                for (int k = 0; k < KC / 2; ++k) {
+                    const uint64_t ad = sdesc(abase + (uint32_t)(k * 2 * 2048), 2048, 128);
+                    const uint64_t bd = sdesc(bbase + (uint32_t)(k * 2 * NCO * 16), NCO * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, (tap | k) != 0 ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+            }
+            if (ok) mma_commit(accum);
+        }
+        // epilogue: every thread owns one accumulator row (= TMEM lane = output voxel)
+        __syncwarp();
+        const bool ready = mbar_wait(accum, (uint32_t)tcount & 1u);
+        if (!ready) { *abort_flag = 1; atomicExch(a.err, 3); }
+        __syncwarp();
+        tc_fence_after();
+        if (ready && !*abort_flag) {
+            float v[NCO];
+            tmem_load<NCO>(tmem + ((uint32_t)(warp * 32) << 16), v);
+            const int row = warp * 32 + lane;
+            const int yy = y0 + (row >> 6), xx = row & 63;
+            const size_t plane = (size_t)a.D * a.H * a.W;
+            const size_t vox = ((size_t)z * a.H + yy) * a.W + xx;
+#pragma unroll
+            for (int c = 0; c < NCO; ++c) {
+                float t = v[c];
+                if (c < a.c_out) {
+                    if (a.bias) t += __ldg(a.bias + c);
+                } else {
+                    t = 0.0f;
+                }
+                v[c] = t;
+            }
+            if (a.mask_src) {
+#pragma unroll
+                for (int kc = 0; kc < KCO; ++kc) {
+                    const uint4 m = __ldg(reinterpret_cast<const uint4*>(a.mask_src) +
+                                          ((size_t)(b * KCO + kc) * plane + vox));
+                    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (!(__bfloat162float(mb[e]) > 0.0f)) v[kc * 8 + e] *= a.slope;
+                }
+            }
+            if (a.act == 1) {
+#pragma unroll
+                for (int c = 0; c < NCO; ++c) v[c] = v[c] > 0.0f ? v[c] : a.slope * v[c];
+            }
+            if (a.y) {
+#pragma unroll
+                for (int kc = 0; kc < KCO; ++kc) {
+                    uint4 o;
+                    __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) ob[e] = __floats2bfloat162_rn(v[kc * 8 + 2 * e], v[kc * 8 + 2 * e + 1]);
+                    reinterpret_cast<uint4*>(a.y)[(size_t)(b * KCO + kc) * plane + vox] = o;
+                }
+            }
+            if (a.y_f32) a.y_f32[(size_t)b * plane + vox] = v[0];
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// ---- host side -----------------------------------------------------------------------------
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+template <int KC, int NCO>
+cudaError_t launch_one(const ConvLaunch& c, cudaStream_t st) {
+    using L = ConvSmem<KC, NCO>;
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.D, (cuuint64_t)c.B * KC};
+    const cuuint64_t strides[4] = {16, 16ull * c.W, 16ull * c.W * c.H, 16ull * c.W * c.H * c.D};
+    const cuuint32_t box[5] = {8, 64, 2, 1, (cuuint32_t)KC};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(c.x), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc<KC, NCO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             L::kBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    ConvArgs a{};
+    a.w_packed = reinterpret_cast<const uint4*>(c.w_packed);
+    a.bias = c.bias;
+    a.mask_src = reinterpret_cast<const __nv_bfloat16*>(c.mask_src);
+    a.y = reinterpret_cast<__nv_bfloat16*>(c.y);
+    a.y_f32 = c.y_f32;
+    a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
+    a.c_out = c.c_out;
+    a.dil = c.dil;
+    a.act = c.act;
+    a.slope = c.slope;
+    a.n_tiles = c.B * c.D * (c.H / 2);
+    a.err = c.err;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = (228 * 1024) / (L::kBytes + 1024) > 1 ? 2 : 1;
+    int grid = sms * per_sm;
+    if (grid > a.n_tiles) grid = a.n_tiles;
+    if (grid < 1) return cudaSuccess;
+    k_conv3d_tc<KC, NCO><<<grid, 128, L::kBytes, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
+    if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2) return cudaErrorInvalidValue;
+    if (c.kc_in == 2 && c.nco == 32) return launch_one<2, 32>(c, st);
+    if (c.kc_in == 4 && c.nco == 32) return launch_one<4, 32>(c, st);
+    if (c.kc_in == 4 && c.nco == 16) return launch_one<4, 16>(c, st);
+    if (c.kc_in == 2 && c.nco == 16) return launch_one<2, 16>(c, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rt

@@ -110,4 +110,31 @@ cudaError_t launch_march_batch(int W, const BatchInst* insts, const int4* items,
 cudaError_t launch_pack_batch(const BatchInst* insts, int n_inst, long long max_elems, int which, cudaStream_t st);
 cudaError_t launch_unpack_batch(const BatchInst* insts, int n_inst, long long max_elems, cudaStream_t st);
 
+// One 3x3x3 convolution layer on the tensor cores (conv3d_tc.cu). Activations in CP8 layout:
+// bf16 [B][C/8][D][H][W][8] with C padded to a multiple of 16; W must be 64, H even.
+struct ConvLaunch {
+    const void* x;            // CP8 input, kc_in planes per sample
+    const void* w_packed;     // bf16 [27][kc_in][nco][8] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1))
+    const float* bias;        // [c_out] or NULL
+    const void* mask_src;     // CP8 with nco/8 planes: outputs where it is <= 0 are scaled by slope
+    void* y;                  // CP8 output with nco/8 planes, or NULL
+    float* y_f32;             // [B][D][H][W] FP32 copy of output channel 0, or NULL
+    int B, D, H, W;
+    int kc_in;                // input planes (2 or 4)
+    int nco;                  // padded output channels (16 or 32)
+    int c_out;                // real output channels (the rest are written as 0)
+    int dil;                  // dilation
+    int act;                  // 0: identity, 1: LeakyReLU(slope)
+    float slope;
+    int* err;                 // device error word (timeouts)
+};
+cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st);
+
+// FP32 [B][C][vox] <-> CP8 bf16 [B][kc][vox][8] (channels >= C are zero).
+cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st);
+cudaError_t launch_from_cp8(const void* src, int B, int C, int kc, long long vox, float* dst, cudaStream_t st);
+// FP32 [c_out][c_in][27] -> bf16 [27][kc][nco][8] (transpose = 1: flipped taps, c_in <-> c_out).
+cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int kc, int nco, int transpose, void* packed,
+                                cudaStream_t st);
+
 }  // namespace rt

@@ -1,0 +1,110 @@
+// rt_surrogate.cu -- C ABI of the convolutional surrogate's building blocks (raytrax.h).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "raytrax.h"
+#include "rt_internal.h"
+
+namespace {
+
+rt_status err(rt_status st, const char* fmt, ...) {
+    char buf[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return rt::set_error(st, buf);
+}
+
+rt_status cuda_err(cudaError_t e, const char* what) {
+    return err(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int planes(int c) { return 2 * ((c + 15) / 16); }
+
+std::mutex g_mu;
+int* g_err[64] = {};
+
+// Device word that kernels with bounded waits set on timeout (one per device, allocated once).
+int* error_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) { cudaFree(p); return nullptr; }
+        g_err[dev] = p;
+    }
+    return g_err[dev];
+}
+
+rt_status check_shape(int B, int D, int H, int W) {
+    if (B < 1 || D < 1 || H < 2 || W != 64 || H % 2)
+        return err(RT_ERR_INVALID_ARG, "conv3d: need B, D >= 1, even H >= 2 and W == 64 (got %d %d %d %d)", B, D,
+                   H, W);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_cp8_planes(int channels) { return channels < 1 ? 0 : planes(channels); }
+
+rt_status rt_cp8_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* stream) {
+    if (!src || !dst || B < 1 || C < 1 || D < 1 || H < 1 || W < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_from_f32: bad arguments");
+    cudaError_t e = rt::launch_to_cp8(src, B, C, planes(C), (long long)D * H * W, dst, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_from_f32");
+}
+
+rt_status rt_cp8_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* stream) {
+    if (!src || !dst || B < 1 || C < 1 || D < 1 || H < 1 || W < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_to_f32: bad arguments");
+    cudaError_t e = rt::launch_from_cp8(src, B, C, planes(C), (long long)D * H * W, dst, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_to_f32");
+}
+
+rt_status rt_conv3d_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed, void* stream) {
+    if (!w || !packed || c_in < 1 || c_in > 32 || c_out < 1 || c_out > 32)
+        return err(RT_ERR_INVALID_ARG, "rt_conv3d_pack_weights: need 1 <= c_in, c_out <= 32");
+    // forward: K = c_in planes, N = c_out padded; data gradient: K = c_out planes, N = c_in padded
+    const int kc = transpose ? planes(c_out) : planes(c_in);
+    const int nco = ((transpose ? c_in : c_out) + 15) / 16 * 16;
+    cudaError_t e = rt::launch_pack_weights(w, c_in, c_out, kc, nco, transpose ? 1 : 0, packed, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_conv3d_pack_weights");
+}
+
+rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in, const void* w_packed,
+                            const float* bias, int c_out, int dilation, int act, float slope, const void* mask,
+                            void* y, float* y_f32, void* stream) {
+    rt_status s = check_shape(B, D, H, W);
+    if (s != RT_OK) return s;
+    if (!x || !w_packed || (!y && !y_f32)) return err(RT_ERR_INVALID_ARG, "rt_conv3d_forward: NULL buffer");
+    if (c_in < 1 || c_in > 32 || c_out < 1 || c_out > 32 || dilation < 1 || (act != 0 && act != 1))
+        return err(RT_ERR_INVALID_ARG, "rt_conv3d_forward: need 1 <= c_in, c_out <= 32, dilation >= 1, act 0/1");
+    int* ew = error_word();
+    if (!ew) return err(RT_ERR_CUDA, "rt_conv3d_forward: no device error word");
+    rt::ConvLaunch c{};
+    c.x = x; c.w_packed = w_packed; c.bias = bias; c.mask_src = mask; c.y = y; c.y_f32 = y_f32;
+    c.B = B; c.D = D; c.H = H; c.W = W;
+    c.kc_in = planes(c_in);
+    c.nco = (c_out + 15) / 16 * 16;
+    c.c_out = c_out; c.dil = dilation; c.act = act; c.slope = slope; c.err = ew;
+    cudaError_t e = rt::launch_conv3d_tc(c, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_conv3d_forward launch");
+}
+
+rt_status rt_device_status(int* code) {
+    if (!code) return err(RT_ERR_INVALID_ARG, "rt_device_status: NULL");
+    int* ew = error_word();
+    if (!ew) return err(RT_ERR_CUDA, "rt_device_status: no device error word");
+    cudaError_t e = cudaMemcpy(code, ew, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ew, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_err(e, "rt_device_status");
+    return *code ? RT_ERR_TIMEOUT : RT_OK;
+}
+
+}  // extern "C"
