@@ -239,8 +239,16 @@ rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in,
                             const float* bias, int c_out, int dilation, int act, float slope,
                             const void* mask, void* y, float* y_f32, void* cuda_stream);
 
+/* Weight and bias gradients of rt_conv3d_forward for dz = dL/d(pre-activation output):
+     dw[co][ci][tap] += sum_{b, p} dz[b][co][p] x[b][ci][p + (tap - centre) * d],
+     db[co] += sum_{b, p} dz[b][co][p]          (ACCUMULATED: zero them first).
+   x: CP8 with P(c_in) planes, dz: CP8 with P(c_out) planes; dw (FP32 [c_out][c_in][27]) or db
+   may be NULL. The sums over voxels run on the tensor cores with FP32 accumulation. */
+rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int H, int W, int c_in,
+                                int c_out, int dilation, float* dw, float* db, void* cuda_stream);
+
 /* Synchronising read-and-clear of this device's kernel error word: RT_OK, or RT_ERR_TIMEOUT
-   with *code = which wait gave up (1: stage free, 2: stage loaded, 3: accumulator ready). */
+   with *code = which wait gave up (1-3: convolution ring / accumulator, 4-8: weight gradient). */
 rt_status rt_device_status(int* code);
 
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per

@@ -21,7 +21,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_destroy", "rt_cp8_planes", "rt_cp8_from_f32", "rt_cp8_to_f32", "rt_conv3d_pack_weights",
-           "rt_conv3d_forward", "rt_device_status")
+           "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad")
 
 
 class RTError(RuntimeError):
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
         lib.rt_conv3d_pack_weights.restype = i
         lib.rt_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, i, f, vp, vp, vp, vp]
         lib.rt_conv3d_forward.restype = i
+        lib.rt_conv3d_weight_grad.argtypes = [vp, vp, i, i, i, i, i, i, i, vp, vp, vp]
+        lib.rt_conv3d_weight_grad.restype = i
         lib.rt_device_status.argtypes = [ctypes.POINTER(ctypes.c_int)]
         lib.rt_device_status.restype = i
         _lib = lib

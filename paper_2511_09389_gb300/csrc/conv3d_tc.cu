@@ -90,9 +90,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major (or, with
+// mn_major = 1, both MN-major).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int mn_major = 0) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)mn_major << 15) | ((uint32_t)mn_major << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -144,6 +146,13 @@ __device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float* v) {
 
 constexpr int kStages = 4;
 constexpr int kTmemCols = 32;
+
+struct WgradArgs {
+    float* dw;                        // [c_out][c_in][27], accumulated
+    int B, D, H, W, c_in, c_out, dil;
+    int n_tiles;
+    int* err;
+};
 
 struct ConvArgs {
     const uint4* w_packed;            // [27][KC][NCO][8] bf16 in 16-byte units
@@ -308,6 +317,146 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_tc(const __grid_constant__ CU
     }
 }
 
+// ---- weight gradient ------------------------------------------------------------------------
+// dW[co][ci][tap] = sum over voxels v of dZ[v][co] * X[v + off(tap)][ci] (zero outside). As a
+// GEMM: M = (tap, ci) rows, N = co, K = voxels. Both operands are the CP8 boxes the forward
+// kernel loads, read MN-major (for a fixed voxel, 8 consecutive channels are one 16-byte row):
+// A = G taps' input boxes stored back to back, so the 8-channel core matrices of all G * 8 * KC
+// rows are uniformly 2048 bytes apart (G = 128 / (8 KC)); B = the dZ box of the tile. Each CTA
+// accumulates its share of tiles in tensor memory (one 128 x NCO accumulator per tap group) and
+// adds the result to dW once, with FP32 atomics.
+
+namespace {
+template <int KC>
+struct WgradSmem {
+    static constexpr int kBox = KC * 2048;                  // one tap box (128 voxels, KC planes)
+    static constexpr int kG = 128 / (8 * KC);               // taps per group
+    static constexpr int kGroups = (27 + kG - 1) / kG;
+    static constexpr int kGroupBytes = kG * kBox;           // 32 KB
+    static constexpr int kZBytes = 4 * 2048;                // dZ box (up to 4 planes)
+    static constexpr int kBarOff = 2 * kGroupBytes + kZBytes;
+    static constexpr int kBytes = kBarOff + 6 * 8 + 16;
+};
+}  // namespace
+
+template <int KC, int NCO>
+__global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__ CUtensorMap tmap_x,
+                                                         const __grid_constant__ CUtensorMap tmap_dz, WgradArgs a) {
+    using L = WgradSmem<KC>;
+    constexpr int KCO = NCO / 8;
+    constexpr int kCols = (L::kGroups * NCO) <= 128 ? 128 : 256;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sg = smem;                                   // two group buffers
+    unsigned char* sz = smem + 2 * L::kGroupBytes;              // dZ box
+    uint64_t* gfull = reinterpret_cast<uint64_t*>(smem + L::kBarOff);   // [2]
+    uint64_t* gempty = gfull + 2;                                       // [2]
+    uint64_t* zfull = gempty + 2;
+    uint64_t* zempty = zfull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(zempty + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&gfull[i], 1); mbar_init(&gempty[i], 1); }
+        mbar_init(zfull, 1);
+        mbar_init(zempty, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = idesc_bf16(128, NCO, 1);
+
+    const int half_h = a.H >> 1;
+    const int tiles_per_b = a.D * half_h;
+    const int t_begin = (int)((long long)a.n_tiles * blockIdx.x / gridDim.x);
+    const int t_end = (int)((long long)a.n_tiles * (blockIdx.x + 1) / gridDim.x);
+    int done_tiles = 0;
+    if (warp == 0 && lane == 0) {
+        // producer: per tile, the dZ box, then the tap groups through two group buffers
+        int gq = 0;
+        for (int tile = t_begin; tile < t_end && !*abort_flag; ++tile, ++done_tiles) {
+            const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
+            const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
+            if (!mbar_wait(zempty, ((uint32_t)done_tiles & 1u) ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 4); break; }
+            mbar_expect_tx(zfull, KCO * 2048);
+            tma_load_5d(sz, &tmap_dz, zfull, 0, 0, y0, z, b * KCO);
+            for (int g = 0; g < L::kGroups; ++g, ++gq) {
+                const int buf = gq & 1;
+                if (!mbar_wait(&gempty[buf], ((uint32_t)(gq >> 1) & 1u) ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 5); break; }
+                const int ntap = min(L::kG, 27 - g * L::kG);
+                mbar_expect_tx(&gfull[buf], ntap * L::kBox);
+                for (int t = 0; t < ntap; ++t) {
+                    const int tap = g * L::kG + t;
+                    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                    tma_load_5d(sg + buf * L::kGroupBytes + t * L::kBox, &tmap_x, &gfull[buf], 0, dx * a.dil,
+                                y0 + dy * a.dil, z + dz * a.dil, b * KC);
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 8 MMAs (K = 16 voxels each) per tap group and tile
+        int gq = 0;
+        for (int tile = t_begin; tile < t_end && !*abort_flag; ++tile, ++done_tiles) {
+            if (!mbar_wait(zfull, (uint32_t)done_tiles & 1u)) { *abort_flag = 1; atomicExch(a.err, 6); break; }
+            const uint32_t zb = smem_u32(sz);
+            for (int g = 0; g < L::kGroups; ++g, ++gq) {
+                const int buf = gq & 1;
+                if (!mbar_wait(&gfull[buf], (uint32_t)(gq >> 1) & 1u)) { *abort_flag = 1; atomicExch(a.err, 7); break; }
+                tc_fence_after();
+                const uint32_t ab = smem_u32(sg + buf * L::kGroupBytes);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    // MN-major: leading (K) offset 128 B = 8 voxels, stride (MN) offset 2048 B = 8 channels
+                    const uint64_t ad = sdesc(ab + (uint32_t)(k * 256), 128, 2048);
+                    const uint64_t bd = sdesc(zb + (uint32_t)(k * 256), 128, 2048);
+                    mma_bf16(tmem + (uint32_t)(g * NCO), ad, bd, idesc, (tile != t_begin || k != 0) ? 1u : 0u);
+                }
+                mma_commit(&gempty[buf]);
+            }
+            mma_commit(zempty);
+        }
+    }
+    __syncthreads();
+    // Wait for the last MMAs: the dZ-box barrier's phase of the last tile completes only when
+    // every earlier MMA has. It lags by at most one phase here (the producer waited on the one
+    // before), so the parity test is unambiguous.
+    const int ntile = t_end - t_begin;
+    bool ok = !*abort_flag;
+    if (ok && ntile > 0) ok = mbar_wait(zempty, (uint32_t)(ntile - 1) & 1u);
+    if (!ok) { *abort_flag = 1; atomicExch(a.err, 8); }
+    tc_fence_after();
+    if (ok && ntile > 0) {
+        // row m = warp * 32 + lane -> (tap within group, input channel)
+        const int m = warp * 32 + lane;
+        const int tl = m / (8 * KC), ci = m % (8 * KC);
+        for (int g = 0; g < L::kGroups; ++g) {
+            float v[NCO];
+            tmem_load<NCO>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * NCO), v);
+            const int tap = g * L::kG + tl;
+            if (tap < 27 && ci < a.c_in) {
+#pragma unroll
+                for (int co = 0; co < NCO; ++co)
+                    if (co < a.c_out) atomicAdd(a.dw + ((size_t)co * a.c_in + ci) * 27 + tap, v[co]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
 // ---- host side -----------------------------------------------------------------------------
 
 namespace {
@@ -370,7 +519,58 @@ cudaError_t launch_one(const ConvLaunch& c, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+bool make_map(CUtensorMap* map, const void* base, int B, int planes, int D, int H, int W) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B * planes};
+    const cuuint64_t strides[4] = {16, 16ull * W, 16ull * W * H, 16ull * W * H * D};
+    const cuuint32_t box[5] = {8, 64, 2, 1, (cuuint32_t)planes};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KC, int NCO>
+cudaError_t launch_wgrad_one(const WgradLaunch& c, cudaStream_t st) {
+    using L = WgradSmem<KC>;
+    CUtensorMap mx, mz;
+    if (!make_map(&mx, c.x, c.B, KC, c.D, c.H, c.W) || !make_map(&mz, c.dz, c.B, NCO / 8, c.D, c.H, c.W))
+        return cudaErrorInvalidValue;
+    // at most two CTAs per SM: each holds up to 256 tensor-memory columns of the SM's 512
+    const int bytes = L::kBytes < 100 * 1024 ? 100 * 1024 : L::kBytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad<KC, NCO>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    WgradArgs a{};
+    a.dw = c.dw;
+    a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
+    a.c_in = c.c_in; a.c_out = c.c_out; a.dil = c.dil;
+    a.n_tiles = c.B * c.D * (c.H / 2);
+    a.err = c.err;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = 2 * sms;
+    if (grid > a.n_tiles) grid = a.n_tiles;
+    if (grid < 1) return cudaSuccess;
+    k_conv3d_wgrad<KC, NCO><<<grid, 128, bytes, st>>>(mx, mz, a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st) {
+    if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2) return cudaErrorInvalidValue;
+    if (c.kc_in == 4 && c.nco == 32) return launch_wgrad_one<4, 32>(c, st);
+    if (c.kc_in == 2 && c.nco == 32) return launch_wgrad_one<2, 32>(c, st);
+    if (c.kc_in == 4 && c.nco == 16) return launch_wgrad_one<4, 16>(c, st);
+    if (c.kc_in == 2 && c.nco == 16) return launch_wgrad_one<2, 16>(c, st);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
     if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2) return cudaErrorInvalidValue;

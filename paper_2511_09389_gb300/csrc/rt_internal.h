@@ -130,6 +130,19 @@ struct ConvLaunch {
 };
 cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st);
 
+// Weight gradient of one layer on the tensor cores: dw[co][ci][27] += sum over voxels of
+// dz[v][co] * x[v + off(tap)][ci]. x: CP8 with kc_in planes; dz: CP8 with nco/8 planes.
+struct WgradLaunch {
+    const void* x;
+    const void* dz;
+    float* dw;
+    int B, D, H, W, kc_in, nco, c_in, c_out, dil;
+    int* err;
+};
+cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st);
+// db[co] += sum over voxels of dz[v][co] (dz: CP8 with kc planes).
+cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st);
+
 // FP32 [B][C][vox] <-> CP8 bf16 [B][kc][vox][8] (channels >= C are zero).
 cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st);
 cudaError_t launch_from_cp8(const void* src, int B, int C, int kc, long long vox, float* dst, cudaStream_t st);

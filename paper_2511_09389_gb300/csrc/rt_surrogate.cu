@@ -97,6 +97,33 @@ rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in,
     return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_conv3d_forward launch");
 }
 
+rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int H, int W, int c_in, int c_out,
+                                int dilation, float* dw, float* db, void* stream) {
+    rt_status s = check_shape(B, D, H, W);
+    if (s != RT_OK) return s;
+    if (!x || !dz || (!dw && !db)) return err(RT_ERR_INVALID_ARG, "rt_conv3d_weight_grad: NULL buffer");
+    if (c_in < 1 || c_in > 32 || c_out < 1 || c_out > 32 || dilation < 1)
+        return err(RT_ERR_INVALID_ARG, "rt_conv3d_weight_grad: need 1 <= c_in, c_out <= 32, dilation >= 1");
+    int* ew = error_word();
+    if (!ew) return err(RT_ERR_CUDA, "rt_conv3d_weight_grad: no device error word");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dw) {
+        rt::WgradLaunch c{};
+        c.x = x; c.dz = dz; c.dw = dw;
+        c.B = B; c.D = D; c.H = H; c.W = W;
+        c.kc_in = planes(c_in);
+        c.nco = (c_out + 15) / 16 * 16;
+        c.c_in = c_in; c.c_out = c_out; c.dil = dilation; c.err = ew;
+        cudaError_t e = rt::launch_conv3d_wgrad(c, st);
+        if (e != cudaSuccess) return cuda_err(e, "rt_conv3d_weight_grad launch");
+    }
+    if (db) {
+        cudaError_t e = rt::launch_bias_grad(dz, B, planes(c_out), (long long)D * H * W, c_out, db, st);
+        if (e != cudaSuccess) return cuda_err(e, "bias gradient launch");
+    }
+    return RT_OK;
+}
+
 rt_status rt_device_status(int* code) {
     if (!code) return err(RT_ERR_INVALID_ARG, "rt_device_status: NULL");
     int* ew = error_word();

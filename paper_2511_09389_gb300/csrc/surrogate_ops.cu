@@ -70,7 +70,40 @@ __global__ void k_pack_weights(const float* __restrict__ w, int c_in, int c_out,
     }
 }
 
+// db[co] += sum_v dz[b][co/8][v][co%8]: one block per (sample, plane) reduces 8 channels.
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dz, int kc, long long vox, int c_out,
+                            float* __restrict__ db) {
+    const int b = blockIdx.y, k = blockIdx.x;
+    const uint4* p = reinterpret_cast<const uint4*>(dz) + ((long long)b * kc + k) * vox;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long v = threadIdx.x; v < vox; v += blockDim.x) {
+        const uint4 q = __ldg(p + v);
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] += __bfloat162float(e[i]);
+    }
+    __shared__ float red[8][33];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float x = acc[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float x = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
+        const int co = k * 8 + threadIdx.x;
+        if (co < c_out) atomicAdd(db + co, x);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st) {
+    k_bias_grad<<<dim3(kc, B), 1024, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dz), kc, vox, c_out, db);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st) {
     k_to_cp8<<<grid1d((long long)B * kc * vox, 256), 256, 0, st>>>(src, C, kc, vox, B,

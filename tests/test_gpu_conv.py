@@ -126,3 +126,25 @@ def test_cp8_round_trip(env):
     torch, lib = env
     x = bf16_round(np.random.default_rng(1).standard_normal((3, 19, 2, 4, 64)))
     assert np.array_equal(from_cp8(torch, lib, to_cp8(torch, lib, x), 3, 19, 2, 4, 64), x)
+
+
+@pytest.mark.parametrize("c_in,c_out,dil", [(32, 32, 1), (32, 32, 4), (2, 32, 1), (32, 1, 2), (9, 5, 1)])
+def test_conv_weight_and_bias_gradients_match_oracle(env, c_in, c_out, dil):
+    """dL/dw and dL/db, summed over the batch and every voxel, on the tensor cores."""
+    torch, lib = env
+    rng = np.random.default_rng(31 * c_in + c_out + dil)
+    B, D, H, W = 2, 6, 4, 64
+    x = bf16_round(rng.standard_normal((B, c_in, D, H, W)))
+    gy = bf16_round(rng.standard_normal((B, c_out, D, H, W)))
+    w = np.zeros((c_out, c_in, 3, 3, 3))
+    _, gw, gb = oracle.conv3d_bwd(x, w, gy, dil)
+    dw = torch.zeros(c_out * c_in * 27, dtype=torch.float32, device="cuda")
+    db = torch.zeros(c_out, dtype=torch.float32, device="cuda")
+    xc, gc = to_cp8(torch, lib, x), to_cp8(torch, lib, gy)      # keep both alive until the kernel ran
+    st = lib.rt_conv3d_weight_grad(xc.data_ptr(), gc.data_ptr(), B, D, H, W, c_in, c_out, dil, dw.data_ptr(),
+                                   db.data_ptr(), None)
+    assert st == 0, lib.rt_last_error()
+    code = ctypes.c_int()
+    assert lib.rt_device_status(ctypes.byref(code)) == 0, code.value
+    assert rel(dw.cpu().numpy().reshape(gw.shape), gw) <= 1e-4
+    assert rel(db.cpu().numpy(), gb) <= 1e-4
