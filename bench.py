@@ -248,6 +248,37 @@ def batched(args, dev, stream):
             "l2": "inputs (2.6 GB) larger than L2"}
 
 
+def surrogate_leg(args, dev):
+    """Learned surrogate vs the plain march on 64^3 one-bin problems (lognormal kappa with
+    sigma_g in [0.5, 1.5], 1-8 Gaussian sources, N_Omega 3072, ds 0.5, c dt 64): train on march
+    fields with the library's kernels, fit the per-field error estimate, then time fields/s of
+    (surrogate + estimate + fallback march, bound rel-L2 <= 1e-2) against the plain march on
+    held-out seeds, batch 32."""
+    import time as _t
+    import numpy as np
+    import torch
+    from paper_2511_09389_gb300 import surrogate as S
+    from paper_2511_09389_gb300.api import Grid
+    grid = Grid((64, 64, 64), 1)
+    t0 = _t.perf_counter()
+    train = S.Dataset(range(args.surrogate_train), grid)
+    held = S.Dataset(range(10_000_000, 10_000_000 + args.surrogate_heldout), grid)
+    t_data = _t.perf_counter() - t0
+    model = S.Surrogate(seed=0)
+    t0 = _t.perf_counter()
+    losses = S.train(model, train, epochs=args.surrogate_epochs, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    errs, est = S.fit_estimator(model, train, batch=32)
+    res = S.evaluate(model, grid, held, batch=32)
+    grid.close()
+    res.update({"train_fields": len(train), "epochs": args.surrogate_epochs, "loss_per_epoch": losses,
+                "train_rel_l2_median": float(np.median(errs)), "estimate_threshold_log10": model.est_threshold,
+                "data_generation_s": t_data, "training_s": t_train,
+                "workload": "64^3, 1-8 sources, N_Omega 3072, ds 0.5, c*dt 64, 1 bin; batch 32"})
+    return res
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -361,6 +392,8 @@ def native_arm(args):
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
     if not args.no_batch:
         line["batched"] = batched(args, dev, stream)
+    if args.surrogate_train > 0:
+        line["surrogate"] = surrogate_leg(args, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -388,6 +421,9 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (faster)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched measurement")
+    ap.add_argument("--surrogate-train", type=int, default=4096, help="surrogate training fields (0: skip)")
+    ap.add_argument("--surrogate-heldout", type=int, default=512)
+    ap.add_argument("--surrogate-epochs", type=int, default=3)
     ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_thread,block,prefetch' "
                                                "instead of autotuning (for reproducible profiles)")
     args = ap.parse_args()

@@ -247,6 +247,33 @@ rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in,
 rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int H, int W, int c_in,
                                 int c_out, int dilation, float* dw, float* db, void* cuda_stream);
 
+/* Surrogate input features from FP32 kappa, j [B][D][H][W]: CP8 with 2 planes holding
+   channel 0 = log(kappa / 0.05), channel 1 = log(1 + j), other channels 0. */
+rt_status rt_surrogate_features(const float* kappa, const float* j, int B, int D, int H, int W, void* x,
+                                void* cuda_stream);
+
+/* out[b] = max over vox of field[b][vox] (field >= 0). */
+rt_status rt_field_max(const float* field, int B, long long vox, float* out, void* cuda_stream);
+
+/* Training loss of the surrogate: *loss += mean over b, v of (pred - T)^2 with the target
+   T = (log(field + eps_rel * fmax[b]) - mu) / sigma (the log field, standardised); when grad is
+   non-NULL its gradient 2 (pred - T) / (B vox) is written to channel 0 of the CP8 tensor grad
+   (2 planes). pred, field: FP32 [B][vox]. */
+rt_status rt_log_field_loss(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                            float eps_rel, float mu, float sigma, void* grad, float* loss, void* cuda_stream);
+
+/* Per-field error sums of the surrogate: out[2b] = sum (F' - F)^2, out[2b+1] = sum F^2 with the
+   prediction F' = exp(pred sigma + mu) - eps_rel * fmax[b]; out is overwritten. */
+rt_status rt_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                         float eps_rel, float mu, float sigma, float* out, void* cuda_stream);
+
+/* out[b][c] = mean over voxels of channel c of a CP8 tensor with C channels (overwritten). */
+rt_status rt_cp8_channel_mean(const void* x, int B, int C, long long vox, float* out, void* cuda_stream);
+
+/* One bias-corrected Adam step on n FP32 parameters (step >= 1 counts from 1). */
+rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, long long n, float lr,
+                       float beta1, float beta2, float eps, int step, void* cuda_stream);
+
 /* Synchronising read-and-clear of this device's kernel error word: RT_OK, or RT_ERR_TIMEOUT
    with *code = which wait gave up (1-3: convolution ring / accumulator, 4-8: weight gradient). */
 rt_status rt_device_status(int* code);

@@ -21,7 +21,9 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_destroy", "rt_cp8_planes", "rt_cp8_from_f32", "rt_cp8_to_f32", "rt_conv3d_pack_weights",
-           "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad")
+           "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
+           "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_cp8_channel_mean",
+           "rt_adam_step")
 
 
 class RTError(RuntimeError):
@@ -114,6 +116,19 @@ def load(path: str = LIB_PATH):
         lib.rt_conv3d_forward.restype = i
         lib.rt_conv3d_weight_grad.argtypes = [vp, vp, i, i, i, i, i, i, i, vp, vp, vp]
         lib.rt_conv3d_weight_grad.restype = i
+        ll = ctypes.c_longlong
+        lib.rt_surrogate_features.argtypes = [vp, vp, i, i, i, i, vp, vp]
+        lib.rt_surrogate_features.restype = i
+        lib.rt_field_max.argtypes = [vp, i, ll, vp, vp]
+        lib.rt_field_max.restype = i
+        lib.rt_log_field_loss.argtypes = [vp, vp, i, ll, vp, f, f, f, vp, vp, vp]
+        lib.rt_log_field_loss.restype = i
+        lib.rt_field_error.argtypes = [vp, vp, i, ll, vp, f, f, f, vp, vp]
+        lib.rt_field_error.restype = i
+        lib.rt_cp8_channel_mean.argtypes = [vp, i, i, ll, vp, vp]
+        lib.rt_cp8_channel_mean.restype = i
+        lib.rt_adam_step.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, i, vp]
+        lib.rt_adam_step.restype = i
         lib.rt_device_status.argtypes = [ctypes.POINTER(ctypes.c_int)]
         lib.rt_device_status.restype = i
         _lib = lib

@@ -52,6 +52,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Wait until the phase with the given parity has completed; false after ~1 s.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint64_t t0 = global_ns();
@@ -166,46 +170,61 @@ struct ConvArgs {
     int* err;
 };
 
+constexpr int kConvThreads = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+
+// The ring is as deep as shared memory allows (about 200 KB with the weights): the tap boxes
+// come from L2 with microsecond latency, so the bytes in flight set the throughput.
 template <int KC, int NCO>
 struct ConvSmem {
     static constexpr int kWBytes = 27 * KC * NCO * 16;
     static constexpr int kWAligned = (kWBytes + 1023) / 1024 * 1024;
     static constexpr int kAStage = KC * 2048;               // KC planes x 128 rows x 16 B
+    static constexpr int kStages = (200 * 1024 - kWAligned) / kAStage > 32 ? 32 : (200 * 1024 - kWAligned) / kAStage;
     static constexpr int kBarOff = kWAligned + kStages * kAStage;
-    static constexpr int kBytes = kBarOff + (2 * kStages + 1) * 8 + 16;
+    // full[S], empty[S], acc_full[2], acc_empty[2], tmem slot, abort flag
+    static constexpr int kBytes = kBarOff + (2 * kStages + 4) * 8 + 16;
 };
 
 }  // namespace
 
+// Persistent, warp-specialised: warp 0 streams the 27 tap boxes of every tile through a deep
+// ring, warp 1 issues the MMAs into one of two TMEM accumulators (64 columns), and
+// warps 2-5 drain the other accumulator (epilogue) meanwhile, so loads, MMAs and stores of
+// consecutive tiles overlap.
 template <int KC, int NCO>
-__global__ void __launch_bounds__(128, 1) k_conv3d_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
     using L = ConvSmem<KC, NCO>;
+    constexpr int S = L::kStages;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sw = smem;
     unsigned char* sa = smem + L::kWAligned;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
-    uint64_t* empty = full + kStages;
-    uint64_t* accum = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    uint64_t* empty = full + S;
+    uint64_t* acc_full = empty + S;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // weights -> shared memory with ordinary stores, made visible to the tensor core below
-    for (int i = tid; i < L::kWBytes / 16; i += 128)
+    for (int i = tid; i < L::kWBytes / 16; i += kConvThreads)
         reinterpret_cast<uint4*>(sw)[i] = __ldg(a.w_packed + i);
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
         }
-        mbar_init(accum, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], 128);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(2 * kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -216,69 +235,100 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_tc(const __grid_constant__ CU
     const uint32_t tmem = *tmem_slot;
 
     constexpr uint32_t idesc = idesc_bf16(128, NCO);
+    constexpr int KCO = NCO / 8;
     const int half_h = a.H >> 1;
     const int tiles_per_b = a.D * half_h;
-    constexpr int KCO = NCO / 8;
-    int it = 0;       // running (tile, tap) counter: stage = it % kStages, phase = (it / kStages) & 1
-    int tcount = 0;   // tiles finished by this CTA: parity of the accumulator barrier
 
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++tcount, it += 27) {
-        if (*abort_flag) break;
-        const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
-        const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
-        if (warp == 0 && lane == 0) {
-            // producer: one TMA box per tap
-            for (int tap = 0; tap < 27; ++tap) {
-                const int q = it + tap, s = q % kStages;
-                const uint32_t ph = (uint32_t)(q / kStages) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 1); break; }
-                mbar_expect_tx(&full[s], L::kAStage);
-                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                tma_load_5d(sa + s * L::kAStage, &tmap, &full[s], 0, dx * a.dil, y0 + dy * a.dil, z + dz * a.dil,
-                            b * KC);
-            }
-        } else if (warp == 1 && lane == 0) {
-            // MMA issuer: KC/2 MMAs (K = 16 each) per tap, then release the stage
-            bool ok = true;
-            for (int tap = 0; tap < 27; ++tap) {
-                const int q = it + tap, s = q % kStages;
-                const uint32_t ph = (uint32_t)(q / kStages) & 1u;
-                if (!mbar_wait(&full[s], ph)) { *abort_flag = 1; atomicExch(a.err, 2); ok = false; break; }
-                tc_fence_after();
-                const uint32_t abase = smem_u32(sa + s * L::kAStage);
-                const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * KC * NCO * 16);
-#pragma unroll
-                for (int k = 0; k < KC / 2; ++k) {
-                    const uint64_t ad = sdesc(abase + (uint32_t)(k * 2 * 2048), 2048, 128);
-                    const uint64_t bd = sdesc(bbase + (uint32_t)(k * 2 * NCO * 16), NCO * 16, 128);
-                    mma_bf16(tmem, ad, bd, idesc, (tap | k) != 0 ? 1u : 0u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: one TMA box per (tile, tap)
+            int q = 0;
+            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x) {
+                const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
+                const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
+                for (int tap = 0; tap < 27; ++tap, ++q) {
+                    const int st = q % S;
+                    if (!mbar_wait(&empty[st], ((uint32_t)(q / S) & 1u) ^ 1u)) {
+                        *abort_flag = 1;
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    mbar_expect_tx(&full[st], L::kAStage);
+                    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                    tma_load_5d(sa + st * L::kAStage, &tmap, &full[st], 0, dx * a.dil, y0 + dy * a.dil,
+                                z + dz * a.dil, b * KC);
                 }
-                mma_commit(&empty[s]);
             }
-            if (ok) mma_commit(accum);
         }
-        // epilogue: every thread owns one accumulator row (= TMEM lane = output voxel)
-        __syncwarp();
-        const bool ready = mbar_wait(accum, (uint32_t)tcount & 1u);
-        if (!ready) { *abort_flag = 1; atomicExch(a.err, 3); }
-        __syncwarp();
-        tc_fence_after();
-        if (ready && !*abort_flag) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: KC/2 MMAs (K = 16) per tap into accumulator t & 1
+            int q = 0, t = 0;
+            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x, ++t) {
+                const int acc = t & 1;
+                if (!mbar_wait(&acc_empty[acc], ((uint32_t)(t >> 1) & 1u) ^ 1u)) {
+                    *abort_flag = 1;
+                    atomicExch(a.err, 3);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * kTmemCols);
+                bool ok = true;
+                for (int tap = 0; tap < 27; ++tap, ++q) {
+                    const int st = q % S;
+                    if (!mbar_wait(&full[st], (uint32_t)(q / S) & 1u)) {
+                        *abort_flag = 1;
+                        atomicExch(a.err, 2);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t abase = smem_u32(sa + st * L::kAStage);
+                    const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * KC * NCO * 16);
+#pragma unroll
+                    for (int k = 0; k < KC / 2; ++k) {
+                        const uint64_t ad = sdesc(abase + (uint32_t)(k * 2 * 2048), 2048, 128);
+                        const uint64_t bd = sdesc(bbase + (uint32_t)(k * 2 * NCO * 16), NCO * 16, 128);
+                        mma_bf16(d, ad, bd, idesc, (tap | k) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[acc]);
+            }
+        }
+    } else {
+        // epilogue warps 2-5: warp w reads TMEM lanes 32 (w % 4) .. +31 = accumulator rows
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const size_t plane = (size_t)a.D * a.H * a.W;
+        int t = 0;
+        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++t) {
+            const int acc = t & 1;
+            const bool ready = mbar_wait(&acc_full[acc], (uint32_t)(t >> 1) & 1u);
+            if (!ready || *abort_flag) {
+                if (!ready) { *abort_flag = 1; atomicExch(a.err, 4); }
+                break;
+            }
+            __syncwarp();
+            tc_fence_after();
             float v[NCO];
-            tmem_load<NCO>(tmem + ((uint32_t)(warp * 32) << 16), v);
-            const int row = warp * 32 + lane;
+            tmem_load<NCO>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * kTmemCols), v);
+            tc_fence_before();
+            mbar_arrive(&acc_empty[acc]);
+            const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
+            const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
             const int yy = y0 + (row >> 6), xx = row & 63;
-            const size_t plane = (size_t)a.D * a.H * a.W;
             const size_t vox = ((size_t)z * a.H + yy) * a.W + xx;
 #pragma unroll
             for (int c = 0; c < NCO; ++c) {
-                float t = v[c];
+                float x = v[c];
                 if (c < a.c_out) {
-                    if (a.bias) t += __ldg(a.bias + c);
+                    if (a.bias) x += __ldg(a.bias + c);
                 } else {
-                    t = 0.0f;
+                    x = 0.0f;
                 }
-                v[c] = t;
+                v[c] = x;
             }
             if (a.mask_src) {
 #pragma unroll
@@ -307,13 +357,13 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_tc(const __grid_constant__ CU
             }
             if (a.y_f32) a.y_f32[(size_t)b * plane + vox] = v[0];
         }
-        tc_fence_before();
-        __syncthreads();
     }
+    tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols)
+                     : "memory");
     }
 }
 
@@ -511,11 +561,10 @@ cudaError_t launch_one(const ConvLaunch& c, cudaStream_t st) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = (228 * 1024) / (L::kBytes + 1024) > 1 ? 2 : 1;
-    int grid = sms * per_sm;
+    int grid = sms;
     if (grid > a.n_tiles) grid = a.n_tiles;
     if (grid < 1) return cudaSuccess;
-    k_conv3d_tc<KC, NCO><<<grid, 128, L::kBytes, st>>>(map, a);
+    k_conv3d_tc<KC, NCO><<<grid, kConvThreads, L::kBytes, st>>>(map, a);
     return cudaGetLastError();
 }
 

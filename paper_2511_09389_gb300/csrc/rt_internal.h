@@ -143,6 +143,17 @@ cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st);
 // db[co] += sum over voxels of dz[v][co] (dz: CP8 with kc planes).
 cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st);
 
+// Surrogate element-wise and reduction kernels (surrogate_ops.cu).
+cudaError_t launch_features(const float* kappa, const float* j, int B, long long vox, void* x, cudaStream_t st);
+cudaError_t launch_field_max(const float* f, int B, long long vox, float* out, cudaStream_t st);
+cudaError_t launch_log_loss(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                            float eps_rel, float mu, float sigma, void* grad, float* loss, cudaStream_t st);
+cudaError_t launch_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                               float eps_rel, float mu, float sigma, float* out, cudaStream_t st);
+cudaError_t launch_channel_mean(const void* x, int B, int C, int kc, long long vox, float* out, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t st);
+
 // FP32 [B][C][vox] <-> CP8 bf16 [B][kc][vox][8] (channels >= C are zero).
 cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st);
 cudaError_t launch_from_cp8(const void* src, int B, int C, int kc, long long vox, float* dst, cudaStream_t st);

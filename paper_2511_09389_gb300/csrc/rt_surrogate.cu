@@ -124,6 +124,47 @@ rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int
     return RT_OK;
 }
 
+rt_status rt_surrogate_features(const float* kappa, const float* j, int B, int D, int H, int W, void* x,
+                                void* stream) {
+    if (!kappa || !j || !x || B < 1 || D < 1 || H < 1 || W < 1) return err(RT_ERR_INVALID_ARG, "rt_surrogate_features: bad arguments");
+    cudaError_t e = rt::launch_features(kappa, j, B, (long long)D * H * W, x, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_surrogate_features");
+}
+
+rt_status rt_field_max(const float* field, int B, long long vox, float* out, void* stream) {
+    if (!field || !out || B < 1 || vox < 1) return err(RT_ERR_INVALID_ARG, "rt_field_max: bad arguments");
+    cudaError_t e = rt::launch_field_max(field, B, vox, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_field_max");
+}
+
+rt_status rt_log_field_loss(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                            float eps_rel, float mu, float sigma, void* grad, float* loss, void* stream) {
+    if (!pred || !field || !fmax || !loss || B < 1 || vox < 1 || !(sigma > 0.0f) || !(eps_rel > 0.0f))
+        return err(RT_ERR_INVALID_ARG, "rt_log_field_loss: bad arguments");
+    cudaError_t e = rt::launch_log_loss(pred, field, B, vox, fmax, eps_rel, mu, sigma, grad, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_log_field_loss");
+}
+
+rt_status rt_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                         float eps_rel, float mu, float sigma, float* out, void* stream) {
+    if (!pred || !field || !fmax || !out || B < 1 || vox < 1) return err(RT_ERR_INVALID_ARG, "rt_field_error: bad arguments");
+    cudaError_t e = rt::launch_field_error(pred, field, B, vox, fmax, eps_rel, mu, sigma, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_field_error");
+}
+
+rt_status rt_cp8_channel_mean(const void* x, int B, int C, long long vox, float* out, void* stream) {
+    if (!x || !out || B < 1 || C < 1 || vox < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_channel_mean: bad arguments");
+    cudaError_t e = rt::launch_channel_mean(x, B, C, planes(C), vox, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_channel_mean");
+}
+
+rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, long long n, float lr, float beta1,
+                       float beta2, float eps, int step, void* stream) {
+    if (!params || !grads || !m || !v || n < 1 || step < 1) return err(RT_ERR_INVALID_ARG, "rt_adam_step: bad arguments");
+    cudaError_t e = rt::launch_adam(params, grads, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_adam_step");
+}
+
 rt_status rt_device_status(int* code) {
     if (!code) return err(RT_ERR_INVALID_ARG, "rt_device_status: NULL");
     int* ew = error_word();

@@ -98,7 +98,174 @@ __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dz, int kc, long l
     }
 }
 
+// Surrogate inputs: channel 0 = log(kappa / 0.05), channel 1 = log(1 + j); CP8 with 2 planes.
+__global__ void k_features(const float* __restrict__ kappa, const float* __restrict__ j, long long vox, int B,
+                           __nv_bfloat16* __restrict__ x) {
+    const long long total = (long long)B * vox;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / vox, v = i - b * vox;
+        const float k = fmaxf(__ldg(kappa + i), 1e-30f);
+        __align__(16) __nv_bfloat16 o[8];
+        o[0] = __float2bfloat16_rn(logf(k * 20.0f));
+        o[1] = __float2bfloat16_rn(log1pf(fmaxf(__ldg(j + i), 0.0f)));
+#pragma unroll
+        for (int e = 2; e < 8; ++e) o[e] = __float2bfloat16_rn(0.0f);
+        uint4* X = reinterpret_cast<uint4*>(x);
+        X[(b * 2) * vox + v] = *reinterpret_cast<uint4*>(o);
+        X[(b * 2 + 1) * vox + v] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+__device__ __forceinline__ float block_sum(float x, float* red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Per-sample maximum of a non-negative field (grid: blocks x B).
+__global__ void k_field_max(const float* __restrict__ f, long long vox, float* __restrict__ out) {
+    const int b = blockIdx.y;
+    float m = 0.0f;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vox; v += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, __ldg(f + (long long)b * vox + v));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out + b), __float_as_int(m));
+}
+
+// Loss sum_{b,v} (pred - T)^2 / (B vox) with T = (log(F + eps_b) - mu) / sigma,
+// eps_b = eps_rel * max_b F; its gradient 2 (pred - T) / (B vox) goes to channel 0 of a CP8
+// tensor with 2 planes (the other channels zero).
+__global__ void k_log_loss(const float* __restrict__ pred, const float* __restrict__ field, long long vox, int B,
+                           const float* __restrict__ fmax, float eps_rel, float mu, float inv_sigma,
+                           __nv_bfloat16* __restrict__ grad, float* __restrict__ loss) {
+    __shared__ float red[32];
+    const long long total = (long long)B * vox;
+    const float norm = 1.0f / (float)total;
+    float acc = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / vox, v = i - b * vox;
+        const float eps = eps_rel * __ldg(fmax + b);
+        const float T = (logf(__ldg(field + i) + eps) - mu) * inv_sigma;
+        const float d = __ldg(pred + i) - T;
+        acc += d * d;
+        if (grad) {
+            __align__(16) __nv_bfloat16 o[8];
+            o[0] = __float2bfloat16_rn(2.0f * d * norm);
+#pragma unroll
+            for (int e = 1; e < 8; ++e) o[e] = __float2bfloat16_rn(0.0f);
+            uint4* G = reinterpret_cast<uint4*>(grad);
+            G[(b * 2) * vox + v] = *reinterpret_cast<uint4*>(o);
+            G[(b * 2 + 1) * vox + v] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    const float t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(loss, t * norm);
+}
+
+// Per-sample sums for the relative L2 error of the predicted field F' = exp(pred sigma + mu) - eps:
+// out[b] = (sum (F' - F)^2, sum F^2).
+__global__ void k_field_error(const float* __restrict__ pred, const float* __restrict__ field, long long vox,
+                              const float* __restrict__ fmax, float eps_rel, float mu, float sigma,
+                              float* __restrict__ out) {
+    __shared__ float red[32];
+    const int b = blockIdx.y;
+    const float eps = eps_rel * __ldg(fmax + b);
+    float e2 = 0.0f, f2 = 0.0f;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vox; v += (long long)gridDim.x * blockDim.x) {
+        const long long i = (long long)b * vox + v;
+        const float F = __ldg(field + i);
+        const float Fp = expf(__ldg(pred + i) * sigma + mu) - eps;
+        e2 += (Fp - F) * (Fp - F);
+        f2 += F * F;
+    }
+    const float a = block_sum(e2, red);
+    const float c = block_sum(f2, red);
+    if (threadIdx.x == 0) { atomicAdd(out + 2 * b, a); atomicAdd(out + 2 * b + 1, c); }
+}
+
+// out[b][c] = mean over voxels of channel c of a CP8 tensor (kc planes).
+__global__ void k_channel_mean(const __nv_bfloat16* __restrict__ x, int kc, long long vox, int C,
+                               float* __restrict__ out) {
+    const int b = blockIdx.y, k = blockIdx.z;
+    const uint4* p = reinterpret_cast<const uint4*>(x) + ((long long)b * kc + k) * vox;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vox; v += (long long)gridDim.x * blockDim.x) {
+        const uint4 q = __ldg(p + v);
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] += __bfloat162float(e[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float t = acc[i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        const int c = k * 8 + i;
+        if ((threadIdx.x & 31) == 0 && c < C) atomicAdd(out + (long long)b * C + c, t / (float)vox);
+    }
+}
+
+// Adam (bias-corrected), FP32 master parameters.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_features(const float* kappa, const float* j, int B, long long vox, void* x, cudaStream_t st) {
+    k_features<<<grid1d((long long)B * vox, 256), 256, 0, st>>>(kappa, j, vox, B, reinterpret_cast<__nv_bfloat16*>(x));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_max(const float* f, int B, long long vox, float* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * B, st);
+    if (e != cudaSuccess) return e;
+    k_field_max<<<dim3(64, B), 256, 0, st>>>(f, vox, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_log_loss(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                            float eps_rel, float mu, float sigma, void* grad, float* loss, cudaStream_t st) {
+    k_log_loss<<<grid1d((long long)B * vox, 256), 256, 0, st>>>(pred, field, vox, B, fmax, eps_rel, mu, 1.0f / sigma,
+                                                                 reinterpret_cast<__nv_bfloat16*>(grad), loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
+                               float eps_rel, float mu, float sigma, float* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * 2 * B, st);
+    if (e != cudaSuccess) return e;
+    k_field_error<<<dim3(64, B), 256, 0, st>>>(pred, field, vox, fmax, eps_rel, mu, sigma, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_channel_mean(const void* x, int B, int C, int kc, long long vox, float* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * B * C, st);
+    if (e != cudaSuccess) return e;
+    k_channel_mean<<<dim3(32, B, kc), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(x), kc, vox, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t st) {
+    const float c1 = 1.0f / (1.0f - powf(b1, (float)step)), c2 = 1.0f / (1.0f - powf(b2, (float)step));
+    k_adam<<<grid1d(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st) {
     k_bias_grad<<<dim3(kc, B), 1024, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dz), kc, vox, c_out, db);

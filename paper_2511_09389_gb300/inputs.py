@@ -172,3 +172,42 @@ def random_small(seed: int, shape=(9, 7, 11), n_freq: int = 2, n_src: int = 3, n
     src = np.stack([rng.uniform(lo, s - 1 - lo, size=n_src) for s in shape], axis=1)
     return Problem(f"random_small{seed}", j, kap, src.astype(np.float32), num_rays, step_size, 1.0,
                    horizon)
+
+
+def surrogate_batch_torch(seeds, n: int = 64, device="cuda"):
+    """Surrogate training / held-out inputs generated on the GPU (torch), one per seed: the
+    same recipe as surrogate_sample (lognormal kappa with sigma_g in [0.5, 1.5] and mean 0.05,
+    1..8 Gaussian sources of sigma 1.5 with amplitude log-uniform in [0.1, 10], placed in
+    [4, n-5]^3), drawn from torch generators seeded per sample. Returns kappa [B, n, n, n],
+    j [B, n, n, n] (float32, on `device`) and a list of [n_src, 3] float32 source tensors."""
+    import torch
+    B = len(seeds)
+    kap = torch.empty((B, n, n, n), dtype=torch.float32, device=device)
+    jj = torch.zeros((B, n, n, n), dtype=torch.float32, device=device)
+    f = torch.fft.fftfreq(n, device=device, dtype=torch.float64)
+    fr = torch.fft.rfftfreq(n, device=device, dtype=torch.float64)
+    k2 = f[:, None, None] ** 2 + f[None, :, None] ** 2 + fr[None, None, :] ** 2
+    amp = torch.where(k2 > 0, k2.clamp_min(1e-30) ** (-11.0 / 12.0), torch.zeros_like(k2))
+    ax = torch.arange(n, device=device, dtype=torch.float32)
+    sources = []
+    for b, s in enumerate(seeds):
+        g = torch.Generator(device=device)
+        g.manual_seed(7_000_000 + int(s))
+        h = torch.Generator(device="cpu")
+        h.manual_seed(8_000_000 + int(s))
+        sg = 0.5 + torch.rand((), generator=h).item()
+        ns = int(torch.randint(1, 9, (), generator=h).item())
+        noise = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float64)
+        gr = torch.fft.irfftn(torch.fft.rfftn(noise) * amp, s=(n, n, n))
+        gr = gr / gr.std() * sg
+        kk = torch.exp(gr)
+        kap[b] = (kk * (0.05 / kk.mean())).float()
+        src = 4.0 + torch.rand((ns, 3), generator=h) * (n - 9.0)
+        amps = 10.0 ** (torch.rand(ns, generator=h) * 2.0 - 1.0)
+        for c, a in zip(src.to(device), amps.to(device)):
+            g0 = torch.exp(-(ax - c[0]) ** 2 / 4.5)
+            g1 = torch.exp(-(ax - c[1]) ** 2 / 4.5)
+            g2 = torch.exp(-(ax - c[2]) ** 2 / 4.5)
+            jj[b] += a * g0[:, None, None] * g1[None, :, None] * g2[None, None, :]
+        sources.append(src.float().to(device))
+    return kap, jj, sources

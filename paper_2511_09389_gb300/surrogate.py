@@ -1,0 +1,355 @@
+"""Learned surrogate of the march: a 3-D CNN from (log kappa, log(1 + j)) to the log field.
+
+Five 3x3x3 convolution layers, 32 channels, dilations 1, 2, 4, 8, 16 (a receptive field of
++-31 cells, half the box), LeakyReLU(0.1) between layers. Every convolution, its data and weight
+gradients, the loss, the input features and the optimiser run in the library's kernels (the
+convolutions on the tensor cores, BF16 operands with FP32 accumulation); this module only holds
+the parameter buffers and sequences the calls.
+
+The surrogate is trained on fields the plain march computes, and the march stays its fallback:
+a per-field error estimate (a linear model on the channel means of the last hidden layer,
+fitted to the true errors of the training fields) decides, against a bound, which fields are
+re-solved by the march.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import check
+
+LAYERS = [(2, 32, 1, 1), (32, 32, 2, 1), (32, 32, 4, 1), (32, 32, 8, 1), (32, 1, 16, 0)]  # c_in, c_out, dil, act
+SLOPE = 0.1
+EPS_REL = 1e-8           # the target is log(F + 1e-8 max F)
+
+
+def _p(t):
+    return t.data_ptr() if t is not None else None
+
+
+class Surrogate:
+    def __init__(self, seed: int = 0, device=None):
+        self.lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.shapes = []
+        off = 0
+        for ci, co, _, _ in LAYERS:
+            self.shapes.append((off, co * ci * 27, off + co * ci * 27, co))
+            off += co * ci * 27 + co
+        self.n_params = off
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        p = torch.zeros(off, dtype=torch.float32)
+        for (wo, wn, bo, bn), (ci, co, _, act) in zip(self.shapes, LAYERS):
+            std = math.sqrt(2.0 / (27 * ci)) if act else 0.1 * math.sqrt(1.0 / (27 * ci))
+            p[wo:wo + wn] = torch.randn(wn, generator=g) * std
+        self.params = p.to(self.device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = 0
+        self.mu, self.sigma = 0.0, 1.0
+        self.est_coef = None          # error-estimator coefficients (33,), log10 rel-L2
+        self.est_threshold = -math.inf
+        self._packed = []
+        self._buf = {}
+        self.repack()
+
+    # -- parameters -----------------------------------------------------------------------
+    def w(self, l):
+        wo, wn, _, _ = self.shapes[l]
+        return self.params[wo:wo + wn]
+
+    def b(self, l):
+        _, _, bo, bn = self.shapes[l]
+        return self.params[bo:bo + bn]
+
+    def repack(self):
+        """Pack every layer's FP32 weights into the kernels' bf16 layout (forward and, for the
+        data gradient, flipped/transposed)."""
+        lib = self.lib
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        if not self._packed:
+            for ci, co, _, _ in LAYERS:
+                kf = lib.rt_cp8_planes(ci) * ((co + 15) // 16 * 16) * 8 * 27
+                kt = lib.rt_cp8_planes(co) * ((ci + 15) // 16 * 16) * 8 * 27
+                self._packed.append((torch.empty(kf, dtype=torch.bfloat16, device=self.device),
+                                     torch.empty(kt, dtype=torch.bfloat16, device=self.device)))
+        for l, (ci, co, _, _) in enumerate(LAYERS):
+            fw, tw = self._packed[l]
+            check(lib.rt_conv3d_pack_weights(_p(self.w(l)), ci, co, 0, _p(fw), st))
+            check(lib.rt_conv3d_pack_weights(_p(self.w(l)), ci, co, 1, _p(tw), st))
+
+    def state_dict(self):
+        return {"params": self.params.cpu(), "mu": self.mu, "sigma": self.sigma,
+                "est_coef": None if self.est_coef is None else self.est_coef.copy(),
+                "est_threshold": self.est_threshold}
+
+    def load_state_dict(self, d):
+        self.params.copy_(d["params"].to(self.device))
+        self.mu, self.sigma = float(d["mu"]), float(d["sigma"])
+        self.est_coef = d["est_coef"]
+        self.est_threshold = float(d["est_threshold"])
+        self.repack()
+
+    # -- buffers --------------------------------------------------------------------------
+    def _get(self, name, n, dtype):
+        t = self._buf.get(name)
+        if t is None or t.numel() < n or t.dtype != dtype:
+            t = torch.empty(n, dtype=dtype, device=self.device)
+            self._buf[name] = t
+        return t[:n]
+
+    def _act(self, name, B, C, vox):
+        return self._get(name, B * self.lib.rt_cp8_planes(C) * vox * 8, torch.bfloat16)
+
+    # -- forward / backward ---------------------------------------------------------------
+    def forward(self, kappa, j, keep=False):
+        """kappa, j: FP32 [B, D, H, 64] CUDA tensors. Returns the standardised log-field
+        prediction [B, D, H, 64] (FP32); keep=True keeps the activations for backward()."""
+        lib = self.lib
+        B, D, H, W = kappa.shape
+        vox = D * H * W
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        x = self._act("x0", B, 2, vox)
+        check(lib.rt_surrogate_features(_p(kappa.contiguous()), _p(j.contiguous()), B, D, H, W, _p(x), st))
+        acts = [x]
+        pred = self._get("pred", B * vox, torch.float32)
+        for l, (ci, co, dil, act) in enumerate(LAYERS):
+            fw, _ = self._packed[l]
+            last = l == len(LAYERS) - 1
+            y = None if last else self._act(f"a{l + 1}", B, co, vox)
+            check(lib.rt_conv3d_forward(_p(acts[-1]), B, D, H, W, ci, _p(fw), _p(self.b(l)), co, dil, act, SLOPE,
+                                        None, _p(y), _p(pred) if last else None, st))
+            if not last:
+                acts.append(y)
+        if keep:
+            self._acts = (acts, B, D, H, W)
+        return pred.view(B, D, H, W)
+
+    def loss_and_backward(self, pred, field, fmax):
+        """Loss against the standardised log field and the parameter gradients (self.grads)."""
+        lib = self.lib
+        acts, B, D, H, W = self._acts
+        vox = D * H * W
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        loss = self._get("loss", 1, torch.float32)
+        loss.zero_()
+        g = self._act("g_out", B, 1, vox)
+        check(lib.rt_log_field_loss(_p(pred), _p(field), B, vox, _p(fmax), EPS_REL, self.mu, self.sigma, _p(g),
+                                    _p(loss), st))
+        self.grads.zero_()
+        for l in range(len(LAYERS) - 1, -1, -1):
+            ci, co, dil, _ = LAYERS[l]
+            wo, _, bo, _ = self.shapes[l]
+            check(lib.rt_conv3d_weight_grad(_p(acts[l]), _p(g), B, D, H, W, ci, co, dil,
+                                            self.grads.data_ptr() + 4 * wo, self.grads.data_ptr() + 4 * bo, st))
+            if l > 0:
+                _, tw = self._packed[l]
+                gn = self._act(f"g{l % 2}", B, ci, vox)
+                # gradient w.r.t. the previous layer's pre-activation: transposed convolution,
+                # times the LeakyReLU derivative (sign of the stored activation)
+                check(lib.rt_conv3d_forward(_p(g), B, D, H, W, co, _p(tw), None, ci, dil, 0, SLOPE, _p(acts[l]),
+                                            _p(gn), None, st))
+                g = gn
+        return loss
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step_count += 1
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        check(self.lib.rt_adam_step(_p(self.params), _p(self.grads), _p(self.m), _p(self.v), self.n_params, lr,
+                                    beta1, beta2, eps, self.step_count, st))
+        self.repack()
+
+    def status(self):
+        code = ctypes.c_int()
+        st = self.lib.rt_device_status(ctypes.byref(code))
+        if st != 0:
+            raise RuntimeError(f"surrogate kernel wait timed out (code {code.value})")
+
+    # -- error estimate -------------------------------------------------------------------
+    def features_for_estimate(self, B, D, H, W):
+        """Channel means of the last hidden layer of the last forward (plus a constant)."""
+        acts, *_ = self._acts
+        vox = D * H * W
+        out = self._get("pool", B * 32, torch.float32)
+        check(self.lib.rt_cp8_channel_mean(_p(acts[-1]), B, 32, vox, _p(out),
+                                           torch.cuda.current_stream(self.device).cuda_stream))
+        f = out.view(B, 32).cpu().numpy().astype(np.float64)
+        return np.concatenate([f, np.ones((B, 1))], axis=1)
+
+    def field_errors(self, pred, field, fmax):
+        """True relative L2 error of each predicted field against the march's field."""
+        B = pred.shape[0]
+        vox = pred[0].numel()
+        out = self._get("ferr", 2 * B, torch.float32)
+        check(self.lib.rt_field_error(_p(pred), _p(field), B, vox, _p(fmax), EPS_REL, self.mu, self.sigma, _p(out),
+                                      torch.cuda.current_stream(self.device).cuda_stream))
+        o = out.view(B, 2).cpu().numpy().astype(np.float64)
+        return np.sqrt(o[:, 0] / np.maximum(o[:, 1], 1e-300))
+
+    def estimate(self, feats):
+        """Estimated log10 relative L2 error per field (+inf before the estimator is fitted)."""
+        if self.est_coef is None:
+            return np.full(feats.shape[0], np.inf)
+        return feats @ self.est_coef
+
+
+def field_max(lib, field, device):
+    B = field.shape[0]
+    out = torch.empty(B, dtype=torch.float32, device=device)
+    check(lib.rt_field_max(_p(field), B, field[0].numel(), _p(out), torch.cuda.current_stream(device).cuda_stream))
+    return out
+
+
+def march_fields(grid, kappa, j, sources, num_rays=3072, step_size=0.5, time_step=64.0, out=None):
+    """The plain march for a batch of one-bin problems (the surrogate's teacher and fallback)."""
+    out = torch.empty_like(kappa) if out is None else out
+    for b in range(kappa.shape[0]):
+        grid.advance(j[b].unsqueeze(0), kappa[b].unsqueeze(0), sources[b], num_rays, step_size, 1.0, time_step,
+                     out=out[b].unsqueeze(0))
+    return out
+
+
+class Dataset:
+    """Inputs and march fields of a list of seeds, resident on the GPU."""
+
+    def __init__(self, seeds, grid, n=64, chunk=64, num_rays=3072):
+        from .inputs import surrogate_batch_torch
+        self.seeds = list(seeds)
+        self.num_rays = num_rays
+        N = len(self.seeds)
+        dev = grid.device
+        self.kappa = torch.empty((N, n, n, n), dtype=torch.float32, device=dev)
+        self.j = torch.empty_like(self.kappa)
+        self.field = torch.empty_like(self.kappa)
+        self.sources = []
+        for a in range(0, N, chunk):
+            k, jj, src = surrogate_batch_torch(self.seeds[a:a + chunk], n=n, device=dev)
+            self.kappa[a:a + len(src)] = k
+            self.j[a:a + len(src)] = jj
+            self.sources += src
+            march_fields(grid, k, jj, src, num_rays=num_rays, out=self.field[a:a + len(src)])
+        self.fmax = field_max(_native.load(), self.field, dev)
+
+    def __len__(self):
+        return len(self.seeds)
+
+
+def target_stats(ds, count=256):
+    """Mean and standard deviation of the log-field target log(F + 1e-8 max F)."""
+    idx = slice(0, min(count, len(ds)))
+    F = ds.field[idx]
+    eps = (EPS_REL * ds.fmax[idx]).view(-1, 1, 1, 1)
+    t = torch.log(F + eps)
+    return float(t.mean()), float(t.std())
+
+
+def train(model, ds, epochs=4, batch=32, lr=2e-3, seed=0, log=None):
+    """Adam on the standardised log-field MSE; returns the mean loss of every epoch."""
+    model.mu, model.sigma = target_stats(ds)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses = []
+    n = len(ds)
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g)
+        tot, cnt = 0.0, 0
+        for a in range(0, n - batch + 1, batch):
+            idx = perm[a:a + batch].to(ds.kappa.device)
+            k, jj, F, fm = ds.kappa[idx], ds.j[idx], ds.field[idx], ds.fmax[idx]
+            pred = model.forward(k, jj, keep=True)
+            loss = model.loss_and_backward(pred, F, fm)
+            model.adam(lr=lr * (0.5 ** (ep / max(1, epochs - 1))) if epochs > 1 else lr)
+            tot += float(loss)
+            cnt += 1
+        model.status()
+        losses.append(tot / max(cnt, 1))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.5f}")
+    return losses
+
+
+def fit_estimator(model, ds, batch=32, bound=1e-2, coverage=0.99):
+    """Fit the error estimate (least squares of log10 rel-L2 on pooled features) on ds and pick
+    the largest estimate threshold under which at least `coverage` of ds's fields meet the bound
+    (-inf when no threshold does: every field then falls back to the march)."""
+    feats, errs = [], []
+    for a in range(0, len(ds), batch):
+        sl = slice(a, min(a + batch, len(ds)))
+        k, jj = ds.kappa[sl], ds.j[sl]
+        B, D, H, W = k.shape
+        pred = model.forward(k, jj, keep=True)
+        feats.append(model.features_for_estimate(B, D, H, W))
+        errs.append(model.field_errors(pred, ds.field[sl], ds.fmax[sl]))
+    X = np.concatenate(feats)
+    e = np.concatenate(errs)
+    y = np.log10(np.maximum(e, 1e-30))
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    model.est_coef = coef
+    est = X @ coef
+    order = np.argsort(est)
+    ok = e[order] <= bound
+    frac = np.cumsum(ok) / np.arange(1, len(ok) + 1)
+    good = np.nonzero(frac >= coverage)[0]
+    model.est_threshold = float(est[order][good[-1]]) if len(good) else -math.inf
+    return e, est
+
+
+def evaluate(model, grid, ds, batch=32, bound=1e-2):
+    """Fields/s of (surrogate + estimate + fallback march) and of the plain march on ds, with the
+    surrogate's true errors. Timed with CUDA events on the current stream."""
+    st = torch.cuda.current_stream(grid.device)
+    out = torch.empty_like(ds.kappa[:batch])
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        r = fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def plain():
+        for a in range(0, len(ds), batch):
+            sl = slice(a, min(a + batch, len(ds)))
+            march_fields(grid, ds.kappa[sl], ds.j[sl], ds.sources[sl], num_rays=ds.num_rays,
+                         out=out[: sl.stop - sl.start])
+
+    def with_surrogate():
+        n_fb = 0
+        for a in range(0, len(ds), batch):
+            sl = slice(a, min(a + batch, len(ds)))
+            k, jj = ds.kappa[sl], ds.j[sl]
+            B, D, H, W = k.shape
+            model.forward(k, jj, keep=True)
+            est = model.estimate(model.features_for_estimate(B, D, H, W))
+            bad = np.nonzero(~(est <= model.est_threshold))[0]
+            n_fb += len(bad)
+            for b in bad:
+                grid.advance(jj[b].unsqueeze(0), k[b].unsqueeze(0), ds.sources[a + b], ds.num_rays, 0.5, 1.0,
+                             64.0, out=out[b].unsqueeze(0))
+        return n_fb
+
+    plain()
+    t_plain, _ = timed(plain)
+    with_surrogate()
+    t_sur, n_fb = timed(with_surrogate)
+    errs = []
+    for a in range(0, len(ds), batch):
+        sl = slice(a, min(a + batch, len(ds)))
+        pred = model.forward(ds.kappa[sl], ds.j[sl])
+        errs.append(model.field_errors(pred, ds.field[sl], ds.fmax[sl]))
+    e = np.concatenate(errs)
+    t_net, _ = timed(lambda: [model.forward(ds.kappa[a:a + batch], ds.j[a:a + batch])
+                              for a in range(0, len(ds), batch)])
+    n = len(ds)
+    return {"fields": n, "plain_fields_per_s": n / (t_plain * 1e-3),
+            "surrogate_with_fallback_fields_per_s": n / (t_sur * 1e-3),
+            "network_only_fields_per_s": n / (t_net * 1e-3),
+            "gain_vs_plain": t_plain / t_sur, "fallback_fraction": n_fb / n,
+            "true_rel_l2_median": float(np.median(e)), "true_rel_l2_min": float(e.min()),
+            "fields_within_bound": int(np.sum(e <= bound)), "bound": bound}
