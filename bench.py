@@ -389,6 +389,21 @@ def native_arm(args):
                    "samples": clk["samples"]},
     }
 
+    # the same step with the deterministic (64-bit fixed-point) accumulation
+    gd = Grid(p.shape, 8, deterministic=True)
+    tdet = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gd.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            tdet.append(e0.elapsed_time(e1))
+    gd.close()
+    line["deterministic"] = {"value": U / (statistics.mean(tdet) * 1e-3), "unit": UNIT,
+                             "ms_per_step": statistics.mean(tdet), "note": "64-bit fixed-point deposits, bitwise reproducible"}
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
     if not args.no_batch:
         line["batched"] = batched(args, dev, stream)

@@ -55,8 +55,12 @@ typedef enum {
 } rt_status;
 
 typedef struct {
-    int deterministic;  /* 0: FP32 atomic accumulation (default). 1: 64-bit fixed-point
-                           accumulation, bitwise identical for any launch order or split */
+    int deterministic;  /* 0: FP32 atomic accumulation (default). 1: every deposit is rounded
+                           to a 64-bit fixed-point integer (unit 1 / 2^k with the largest k that
+                           keeps the a-priori bound 4 pi N_src ds max|j| N_s (N_s+1) / 2 below
+                           2^62; needs kappa >= 0) and added as an integer: rt_advance's field is
+                           bitwise identical for every launch plan and deposit order.
+                           rt_advance / rt_advance_rays only (no autotuning, no batch) */
     int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
     int ns_cap;         /* 0: none; > 0: cap on the substep count (Sec. 2 "user cap") */
     int autotune;       /* 1: time the launch shapes once per shape class and keep the best */

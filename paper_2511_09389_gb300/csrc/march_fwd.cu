@@ -8,7 +8,7 @@
 
 namespace rt {
 
-template <int W, int PF>
+template <int W, int PF, int DET>
 __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
     const int rb = blockIdx.x % rblocks;
@@ -29,7 +29,11 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
-    march_lane<W, PF>(L);
+    L.og64 = a.acc64 ? a.acc64 + (size_t)g * W * ncell : nullptr;
+    L.ncell = ncell;
+    L.nbins = min(W, a.n_freq - g * W);
+    L.fix = a.fix;
+    march_lane<W, PF, DET>(L);
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
@@ -39,13 +43,22 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int pf = a.prefetch ? 1 : 0;
+    if (a.acc64) {
+        switch (W) {   // deterministic mode: gather reuse (PF = 0) only
+            case 1: k_march_fwd<1, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 2: k_march_fwd<2, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd<4, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (W * 2 + pf) {
-        case 2: k_march_fwd<1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 3: k_march_fwd<1, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 4: k_march_fwd<2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 5: k_march_fwd<2, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 8: k_march_fwd<4, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 9: k_march_fwd<4, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 2: k_march_fwd<1, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 3: k_march_fwd<1, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 4: k_march_fwd<2, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 5: k_march_fwd<2, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 8: k_march_fwd<4, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 9: k_march_fwd<4, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -133,6 +146,44 @@ cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long 
         case 4: k_unpack<4><<<grid, 256, 0, st>>>(acc, out, n_freq, ncell, total, scale, accumulate); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// ---- deterministic mode: fixed-point scale and conversion -------------------------------------
+__global__ void k_abs_max(const float* __restrict__ x, long long n, float* __restrict__ out) {
+    float m = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__ldg(x + i)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
+// fix = the largest power of two with fix * bound <= 2^62, bound = per_jmax * max|j|
+__global__ void k_fix_scale(const float* __restrict__ jmax, double per_jmax, double* __restrict__ fix) {
+    const double bound = per_jmax * (double)*jmax;
+    *fix = bound > 0.0 ? exp2(floor(log2(4.611686018427388e18 / bound))) : 1.0;
+}
+
+__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, long long n, const double* __restrict__ fix,
+                                 float* __restrict__ out, int accumulate) {
+    const double inv = 1.0 / *fix;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)((double)(long long)acc[i] * inv);
+        out[i] = accumulate ? out[i] + v : v;
+    }
+}
+
+cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, double* fix, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(jmax_tmp, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    k_abs_max<<<grid_for(n, 256), 256, 0, st>>>(j, n, jmax_tmp);
+    k_fix_scale<<<1, 1, 0, st>>>(jmax_tmp, per_jmax, fix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_to_float(const unsigned long long* acc, long long n, const double* fix, float* out,
+                                  int accumulate, cudaStream_t st) {
+    k_fixed_to_float<<<grid_for(n, 256), 256, 0, st>>>(acc, n, fix, out, accumulate);
     return cudaGetLastError();
 }
 

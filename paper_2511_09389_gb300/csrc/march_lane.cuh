@@ -35,6 +35,10 @@ struct Lane {
     const float* __restrict__ jg;
     const float* __restrict__ kg;
     float* __restrict__ og;
+    unsigned long long* __restrict__ og64;   // deterministic mode: bin-major fixed-point accumulator
+    long long ncell;                          //   (og64 + b * ncell + cell for the group's bin b)
+    int nbins;                                //   real bins in this group (the rest are padding)
+    const double* fix;                        //   units per unit deposit (device scalar)
     float4 n;                 // direction
     float sx, sy, sz;         // source position
     int n0, n1, n2;
@@ -44,11 +48,28 @@ struct Lane {
     int kappa_mode;
 };
 
+// Send one merged deposit (the sums for one corner) to memory: a W-wide FP32 reduction, or in
+// deterministic mode one 64-bit fixed-point reduction per real bin (integer addition is
+// associative, so the result does not depend on the order of the deposits).
+template <int W, int DET>
+__device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
+    if (DET) {
+        const double f = *L.fix;
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            if (b < L.nbins)
+                red_add_u64(L.og64 + (size_t)b * L.ncell + cell,
+                            (unsigned long long)__double2ll_rn((double)v[b] * f));
+    } else {
+        red_vec<W>(L.og, cell, v);
+    }
+}
+
 // PF = 1: the gathers of substep k+1 are issued before the update of substep k (positions do
 // not depend on I, so they can run ahead), which doubles the loads in flight per thread.
 // PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
 // the values from the previous substep, still in registers, are reused.
-template <int W, int PF>
+template <int W, int PF, int DET = 0>
 __device__ __forceinline__ void march_lane(const Lane& L) {
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
@@ -115,7 +136,7 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
         if (!same_cells) {
             if (pc[0] >= 0) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
+                for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -139,8 +160,9 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
     }
     if (pc[0] >= 0) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) red_vec<W>(og, pc[c], pend[c]);
+        for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
     }
+    (void)og;
 }
 
 }  // namespace rt

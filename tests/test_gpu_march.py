@@ -184,3 +184,35 @@ def test_invalid_arguments_raise(torch_cuda):
         Grid((8, 8, 8), 1).advance(j, j, s, 10, 0.5, 1.0, 2.0)      # n_freq above max_freq
     with pytest.raises(RTError, match="INVALID_ARG"):
         g.advance(j, j, s, 10, 0.5, 1.0, 2.0, out=j)                  # out aliases an input
+
+
+def test_deterministic_mode_parity_and_bitwise_reproducible(torch_cuda):
+    """Fixed-point accumulation: the field meets the same bar against the oracle and is bitwise
+    identical across runs and across launch plans (bins per thread, block size), i.e. for any
+    order in which the deposits arrive."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.random_small(51, shape=(20, 16, 24), n_freq=5, n_src=4, num_rays=300, horizon=18.0)
+    j, k, s = (torch.from_numpy(a).cuda() for a in (p.j, p.kappa, p.sources))
+    outs = []
+    for plan in [(4, 32, 0), (4, 32, 0), (1, 64, 0), (2, 128, 0), (4, 256, 0)]:
+        g = Grid(p.shape, 8, deterministic=True, plan=plan)
+        outs.append(g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy())
+        g.close()
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint32), outs[0].view(np.uint32))
+    assert_parity(outs[0], run_oracle(p))
+
+
+def test_deterministic_mode_full_size(torch_cuda):
+    """The benchmark workload in deterministic mode: 128^3, 16 sources, N_Omega 3072, N_s 256,
+    4 bins -- parity with the oracle and run-to-run bit equality."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.turbulent()
+    g = Grid(p.shape, 8, deterministic=True)
+    j, k, s = (torch.from_numpy(a).cuda() for a in (p.j, p.kappa, p.sources))
+    a = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy()
+    b = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert_parity(a, run_oracle(p))
