@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
-    L.og64 = a.acc64 ? a.acc64 + (size_t)g * W * ncell : nullptr;
+    L.og64 = a.acc64 ? a.acc64 + (size_t)g * ncell * W : nullptr;
     L.ncell = ncell;
     L.nbins = min(W, a.n_freq - g * W);
     L.fix = a.fix;
@@ -159,21 +159,28 @@ __global__ void k_abs_max(const float* __restrict__ x, long long n, float* __res
 }
 
 // fix = the largest power of two with fix * bound <= 2^62, bound = per_jmax * max|j|
-__global__ void k_fix_scale(const float* __restrict__ jmax, double per_jmax, double* __restrict__ fix) {
+__global__ void k_fix_scale(const float* __restrict__ jmax, double per_jmax, float* __restrict__ fix) {
     const double bound = per_jmax * (double)*jmax;
-    *fix = bound > 0.0 ? exp2(floor(log2(4.611686018427388e18 / bound))) : 1.0;
+    double e = bound > 0.0 ? floor(log2(4.611686018427388e18 / bound)) : 0.0;
+    if (e > 126.0) e = 126.0;
+    if (e < -126.0) e = -126.0;
+    *fix = (float)exp2(e);
 }
 
-__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, long long n, const double* __restrict__ fix,
-                                 float* __restrict__ out, int accumulate) {
-    const double inv = 1.0 / *fix;
+// out[b][c] (+)= acc[g][c][w] / fix for bin b = g * W + w (the packed fixed-point layout)
+__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int n_freq, int W, long long ncell,
+                                 const float* __restrict__ fix, float* __restrict__ out, int accumulate) {
+    const double inv = 1.0 / (double)*fix;
+    const long long n = (long long)n_freq * ncell;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float v = (float)((double)(long long)acc[i] * inv);
+        const long long b = i / ncell, c = i - b * ncell;
+        const long long g = b / W, w = b - g * W;
+        const float v = (float)((double)(long long)acc[(g * ncell + c) * W + w] * inv);
         out[i] = accumulate ? out[i] + v : v;
     }
 }
 
-cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, double* fix, cudaStream_t st) {
+cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, float* fix, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(jmax_tmp, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;
     k_abs_max<<<grid_for(n, 256), 256, 0, st>>>(j, n, jmax_tmp);
@@ -181,9 +188,10 @@ cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixed_to_float(const unsigned long long* acc, long long n, const double* fix, float* out,
-                                  int accumulate, cudaStream_t st) {
-    k_fixed_to_float<<<grid_for(n, 256), 256, 0, st>>>(acc, n, fix, out, accumulate);
+cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
+                                  float* out, int accumulate, cudaStream_t st) {
+    k_fixed_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, W, ncell, fix, out,
+                                                                               accumulate);
     return cudaGetLastError();
 }
 

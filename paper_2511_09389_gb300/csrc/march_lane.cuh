@@ -35,10 +35,11 @@ struct Lane {
     const float* __restrict__ jg;
     const float* __restrict__ kg;
     float* __restrict__ og;
-    unsigned long long* __restrict__ og64;   // deterministic mode: bin-major fixed-point accumulator
-    long long ncell;                          //   (og64 + b * ncell + cell for the group's bin b)
+    unsigned long long* __restrict__ og64;   // deterministic mode: fixed-point accumulator of the
+                                              //   group, packed like og ([cell][W], 8-byte units)
+    long long ncell;
     int nbins;                                //   real bins in this group (the rest are padding)
-    const double* fix;                        //   units per unit deposit (device scalar)
+    const float* fix;                         //   units per unit deposit, a power of two (device)
     float4 n;                 // direction
     float sx, sy, sz;         // source position
     int n0, n1, n2;
@@ -54,12 +55,12 @@ struct Lane {
 template <int W, int DET>
 __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
     if (DET) {
-        const double f = *L.fix;
+        // v * 2^k is exact in FP32; its rounding to an integer is the fixed-point quantisation
+        const float f = __ldg(L.fix);
 #pragma unroll
         for (int b = 0; b < W; ++b)
             if (b < L.nbins)
-                red_add_u64(L.og64 + (size_t)b * L.ncell + cell,
-                            (unsigned long long)__double2ll_rn((double)v[b] * f));
+                red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * f));
     } else {
         red_vec<W>(L.og, cell, v);
     }

@@ -428,23 +428,23 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         rt::MarchArgs m;
         if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
         void *acc64, *dets;
-        if ((st = g->ensure(rt_grid::ACC64, sizeof(unsigned long long) * (size_t)a.n_freq * ncell, &acc64)) != RT_OK)
-            return st;
+        const int groups = (a.n_freq + plan.W - 1) / plan.W;
+        const size_t acc64_bytes = sizeof(unsigned long long) * (size_t)groups * plan.W * ncell;
+        if ((st = g->ensure(rt_grid::ACC64, acc64_bytes, &acc64)) != RT_OK) return st;
         if ((st = g->ensure(rt_grid::DETS, 16, &dets)) != RT_OK) return st;
-        double* fix = (double*)dets;
+        float* fix = (float*)dets;
         float* jmax = (float*)((char*)dets + 8);
         const double per_jmax = 4.0 * 3.14159265358979323846 * (double)a.nsrc * (double)a.ds * (double)ns *
                                 ((double)ns + 1.0) * 0.5;
         RT_CUDA(rt::launch_fix_scale(a.j, (long long)a.n_freq * ncell, per_jmax, jmax, fix, a.st), "fixed-point scale");
-        RT_CUDA(cudaMemsetAsync(acc64, 0, sizeof(unsigned long long) * (size_t)a.n_freq * ncell, a.st),
-                "cudaMemsetAsync(fixed-point accumulator)");
+        RT_CUDA(cudaMemsetAsync(acc64, 0, acc64_bytes, a.st), "cudaMemsetAsync(fixed-point accumulator)");
         m.acc64 = (unsigned long long*)acc64;
         m.fix = fix;
         m.dep_scale = scale;
         if ((st = g->mark(0, a.st)) != RT_OK) return st;
         RT_CUDA(rt::launch_march_fwd(plan.W, m, a.st), "march kernel launch");
         if ((st = g->mark(1, a.st)) != RT_OK) return st;
-        RT_CUDA(rt::launch_fixed_to_float((const unsigned long long*)acc64, (long long)a.n_freq * ncell, fix, a.out,
+        RT_CUDA(rt::launch_fixed_to_float((const unsigned long long*)acc64, a.n_freq, plan.W, ncell, fix, a.out,
                                           a.accumulate, a.st),
                 "fixed-point conversion");
         return RT_OK;

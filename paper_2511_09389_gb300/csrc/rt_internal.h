@@ -25,8 +25,8 @@ struct MarchArgs {
     const float* jp;        // packed j    [groups][ncell][W]   (W = 1: plain [n_freq][ncell])
     const float* kp;        // packed kappa, same layout
     float* acc;             // FP32 accumulator, same layout (W = 1: may be the output itself)
-    unsigned long long* acc64;  // fixed-point accumulator [n_freq][ncell] (deterministic mode) or NULL
-    const double* fix;          // fixed-point units per unit deposit (device scalar, deterministic mode)
+    unsigned long long* acc64;  // fixed-point accumulator [groups][ncell][W] (deterministic mode) or NULL
+    const float* fix;           // fixed-point units per unit deposit, a power of two (device scalar)
     const float4* dirs;     // ray directions (xyz, w unused), ray_count entries
     const float* src;       // device [nsrc][3]
     int n0, n1, n2;
@@ -51,10 +51,10 @@ cudaError_t launch_pack(const float* in, float* out, int n_freq, int W, int grou
 cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long long ncell,
                           float scale, int accumulate, cudaStream_t st);
 // Deterministic mode: *fix = largest power of two with fix * per_jmax * max|j| <= 2^62
-// (jmax_tmp: device float scratch), and out[i] (+)= acc[i] / *fix.
-cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, double* fix, cudaStream_t st);
-cudaError_t launch_fixed_to_float(const unsigned long long* acc, long long n, const double* fix, float* out,
-                                  int accumulate, cudaStream_t st);
+// (jmax_tmp: device float scratch), and out[b][c] (+)= acc[b / W][c][b % W] / *fix.
+cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, float* fix, cudaStream_t st);
+cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
+                                  float* out, int accumulate, cudaStream_t st);
 
 // Geometry trace of one ray (test hook).
 cudaError_t launch_trace(float sx, float sy, float sz, float nx, float ny, float nz, float ds,
