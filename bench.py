@@ -301,8 +301,7 @@ def native_arm(args):
     p = inputs.turbulent()
     U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
     if args.plan:
-        w, b, pf = (int(x) for x in args.plan.split(","))
-        g = Grid(p.shape, 8, profile=True, plan=(w, b, pf))
+        g = Grid(p.shape, 8, profile=True, plan=tuple(int(x) for x in args.plan.split(",")))
     else:
         g = Grid(p.shape, 8, profile=True, autotune=True)   # tuned during the warm-up calls
     j = torch.from_numpy(p.j).to(dev)
@@ -439,7 +438,7 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=4096, help="surrogate training fields (0: skip)")
     ap.add_argument("--surrogate-heldout", type=int, default=512)
     ap.add_argument("--surrogate-epochs", type=int, default=3)
-    ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_thread,block,prefetch' "
+    ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_group,block,prefetch[,lanes_per_ray]' "
                                                "instead of autotuning (for reproducible profiles)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -68,8 +68,10 @@ typedef struct {
     int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
                            call's stream, readable with rt_kernel_ms */
     int plan_width;     /* forward launch plan, used when autotune = 0 (0: default for each):  */
-    int plan_block;     /*   bins per thread (1, 2 or 4), threads per block (32..256, multiple */
-    int plan_prefetch;  /*   of 32), gather prefetch (1: off, 2: on)                           */
+    int plan_block;     /*   bins per group (1, 2 or 4), threads per block (32..256, multiple  */
+    int plan_prefetch;  /*   of 32), gathers (1: reused while the corner set is unchanged, 2:   */
+    int plan_lanes;     /*   one step ahead, 3: both), lanes per ray (1, or 2 / 4 adjacent      */
+                        /*   lanes sharing one ray of a 4-bin group, with gathers mode 1)      */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
@@ -283,14 +285,16 @@ rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, lo
 rt_status rt_device_status(int* code);
 
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
-   thread), threads per block, gather prefetch (0/1), and the march time the autotuner
-   measured for it in ms (-1 when rt_options.autotune is 0). Any pointer may be NULL.
+   group), threads per block, gather mode (0: reuse, 1: ahead, 2: both), lanes per ray, and the march
+   time the autotuner measured for it in ms (-1 when rt_options.autotune is 0). Any pointer
+   may be NULL.
    With autotune = 1, the first call of each shape class (n_freq, num_sources, rays, N_s)
    times every candidate plan on its own inputs before running; it synchronises the stream. */
-rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, float* tuned_ms);
+rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray,
+                       float* tuned_ms);
 
 /* Text of the last autotuning pass on this handle: one line per candidate plan with its best
-   march time ("W=4 block=64 prefetch=1 0.5123 ms"), copied NUL-terminated into the HOST
+   march time ("W=4 block=64 prefetch=0 lanes=2 0.5123 ms"), copied NUL-terminated into the HOST
    buffer buf of len bytes (truncated if needed; "" if the handle never tuned). */
 rt_status rt_tuning_report(rt_grid* grid, char* buf, int len);
 

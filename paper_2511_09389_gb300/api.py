@@ -53,8 +53,9 @@ def direction_table(num_rays: int) -> np.ndarray:
 class Grid:
     """A library handle for one grid shape (owns its scratch on one device).
 
-    plan=(bins_per_thread, block, prefetch) pins the forward launch plan (ignored when
-    autotune=True, which times the candidates on the first call of each shape class)."""
+    plan=(bins_per_group, block, gathers[, lanes_per_ray]) pins the forward launch plan, gathers
+    0 = reused, 1 = one step ahead, 2 = both (ignored
+    when autotune=True, which times the candidates on the first call of each shape class)."""
 
     def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
                  ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
@@ -66,9 +67,10 @@ class Grid:
         self.max_freq = int(max_freq)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
-        pw, pb, pp = (0, 0, 0) if plan is None else (int(plan[0]), int(plan[1]), 2 if plan[2] else 1)
+        pw, pb, pp, pl = (0, 0, 0, 0) if plan is None else (int(plan[0]), int(plan[1]), int(plan[2]) + 1,
+                                                             int(plan[3]) if len(plan) > 3 else 1)
         opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
-                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp)
+                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl)
         self.options = opt
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -194,9 +196,10 @@ class Grid:
 
     def last_plan(self) -> dict:
         """Launch plan of the last forward call (width, block, prefetch, tuned_ms)."""
-        w, b, p, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
-        check(self._lib.rt_last_plan(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(p), ctypes.byref(t)))
-        return {"width": w.value, "block": b.value, "prefetch": p.value, "tuned_ms": t.value}
+        w, b, p, n, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(self._lib.rt_last_plan(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(p), ctypes.byref(n),
+                                     ctypes.byref(t)))
+        return {"width": w.value, "block": b.value, "prefetch": p.value, "lanes_per_ray": n.value, "tuned_ms": t.value}
 
     def tuning_report(self) -> str:
         """Candidates and times of the last autotuning pass ("" if none)."""
@@ -248,7 +251,7 @@ class Batch:
                                          int(d["num_rays"]), float(d["step_size"]),
                                          float(d.get("radiation_velocity", 1.0)), float(d.get("time_step", 1.0)),
                                          out.data_ptr())
-        opt = _native.rt_options(0, int(kappa_mode), int(ns_cap), int(bool(autotune)), 0, 0, 0, 0, 0)
+        opt = _native.rt_options(0, int(kappa_mode), int(ns_cap), int(bool(autotune)), 0, 0, 0, 0, 0, 0)
         h = ctypes.c_void_p()
         check(self._lib.rt_batch_create(ctypes.byref(h), arr, len(instances), ctypes.byref(opt)))
         self._h = h

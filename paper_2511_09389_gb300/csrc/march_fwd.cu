@@ -36,13 +36,58 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     march_lane<W, PF, DET>(L);
 }
 
+// Split lanes over a 4-bin packed group: LPR lanes per (ray, source, group), adjacent in a warp.
+template <int LPR>
+__global__ void __launch_bounds__(256) k_march_fwd_split(MarchArgs a) {
+    constexpr int WL = 4 / LPR;
+    const int rays_per_block = blockDim.x / LPR;
+    const int rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
+    const int rb = blockIdx.x % rblocks;
+    const int sg = blockIdx.x / rblocks;
+    const int s = sg % a.nsrc;
+    const int g = sg / a.nsrc;
+    const int sub = threadIdx.x % LPR;
+    const int r = rb * rays_per_block + threadIdx.x / LPR;
+    if (r >= a.ray_count) return;
+    const long long ncell = (long long)a.n0 * a.n1 * a.n2;
+    Lane L;
+    L.jg = a.jp + (size_t)g * ncell * 4;
+    L.kg = a.kp + (size_t)g * ncell * 4;
+    L.og = a.acc + (size_t)g * ncell * 4;
+    L.n = a.dirs[r];
+    L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
+    L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
+    L.ns = a.ns;
+    L.ds = a.ds;
+    L.scale = a.dep_scale;
+    L.kappa_mode = a.kappa_mode;
+    march_lane_split<WL, 4>(L, sub);
+}
+
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
+    if (a.lanes_per_ray > 1) {
+        // split lanes (4-bin packed groups only): block counts threads, lanes_per_ray per ray
+        if (W != 4 || a.acc64) return cudaErrorInvalidValue;
+        const int block = a.block > 0 ? a.block : 128;
+        const int rpb = block / a.lanes_per_ray;
+        if (rpb < 1) return cudaErrorInvalidValue;
+        const long long rblocks = (a.ray_count + rpb - 1) / rpb;
+        const long long nblk = rblocks * a.nsrc * a.groups;
+        if (nblk <= 0) return cudaSuccess;
+        if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        switch (a.lanes_per_ray) {
+            case 2: k_march_fwd_split<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd_split<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int block = a.block > 0 ? a.block : 128;
     const long long rblocks = (a.ray_count + block - 1) / block;
     const long long nblk = rblocks * a.nsrc * a.groups;
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const int pf = a.prefetch ? 1 : 0;
+    if (a.prefetch < 0 || a.prefetch > 2) return cudaErrorInvalidValue;
     if (a.acc64) {
         switch (W) {   // deterministic mode: gather reuse (PF = 0) only
             case 1: k_march_fwd<1, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
@@ -52,13 +97,16 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
         }
         return cudaGetLastError();
     }
-    switch (W * 2 + pf) {
-        case 2: k_march_fwd<1, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 3: k_march_fwd<1, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 4: k_march_fwd<2, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 5: k_march_fwd<2, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 8: k_march_fwd<4, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 9: k_march_fwd<4, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+    switch (W * 4 + a.prefetch) {
+        case 4: k_march_fwd<1, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 5: k_march_fwd<1, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 6: k_march_fwd<1, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 8: k_march_fwd<2, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 9: k_march_fwd<2, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 10: k_march_fwd<2, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 16: k_march_fwd<4, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 17: k_march_fwd<4, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        case 18: k_march_fwd<4, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

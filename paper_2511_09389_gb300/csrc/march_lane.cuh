@@ -49,6 +49,32 @@ struct Lane {
     int kappa_mode;
 };
 
+// A slice of WL bins out of a packed WP-wide cell vector (split lanes: WP / WL adjacent lanes
+// share one ray, lane `sub` owns bins [sub * WL, sub * WL + WL)).
+template <int WL, int WP>
+__device__ __forceinline__ Vec<WL> ldg_slice(const float* __restrict__ p, int cell, int sub) {
+    const float* q = p + (size_t)cell * WP + sub * WL;
+    Vec<WL> r;
+    if (WL == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(q));
+        r.v[0] = t.x; r.v[1 % WL] = t.y; r.v[2 % WL] = t.z; r.v[3 % WL] = t.w;
+    } else if (WL == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(q));
+        r.v[0] = t.x; r.v[1 % WL] = t.y;
+    } else {
+        r.v[0] = __ldg(q);
+    }
+    return r;
+}
+
+template <int WL, int WP>
+__device__ __forceinline__ void red_slice(float* __restrict__ p, int cell, int sub, const float* v) {
+    float* q = p + (size_t)cell * WP + sub * WL;
+    if (WL == 4) red_add4(q, v[0], v[1 % WL], v[2 % WL], v[3 % WL]);
+    else if (WL == 2) red_add2(q, v[0], v[1 % WL]);
+    else red_add(q, v[0]);
+}
+
 // Send one merged deposit (the sums for one corner) to memory: a W-wide FP32 reduction, or in
 // deterministic mode one 64-bit fixed-point reduction per real bin (integer addition is
 // associative, so the result does not depend on the order of the deposits).
@@ -70,8 +96,161 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
 // not depend on I, so they can run ahead), which doubles the loads in flight per thread.
 // PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
 // the values from the previous substep, still in registers, are reused.
+// Split lanes: WP / WL adjacent lanes march the same ray of a WP-packed bin group, lane `sub`
+// carrying bins [sub * WL, sub * WL + WL). Same algorithm as march_lane with PF = 0 (gathers
+// reused while the corner set is unchanged, deposits merged); the lanes of a ray touch the same
+// 16-byte cell vectors, so they share cache sectors while giving the GPU more warps.
+template <int WL, int WP>
+__device__ __forceinline__ void march_lane_split(const Lane& L, int sub) {
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = L.sx, y = L.sy, z = L.sz;
+    float I[WL], tau[WL];
+#pragma unroll
+    for (int b = 0; b < WL; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    const float ds = L.ds, scale = L.scale;
+    int pc[8];
+    float pend[8][WL];
+    Vec<WL> gj[8];
+    Vec<WL> gk;
+    int gnn = -1;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = -1;
+#pragma unroll
+        for (int b = 0; b < WL; ++b) pend[c][b] = 0.0f;
+    }
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        Sample sm;
+        make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+        const bool same = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
+        if (!same) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gj[c] = ldg_slice<WL, WP>(L.jg, sm.cell[c], sub);
+        }
+        if (sm.nn != gnn) {
+            gk = ldg_slice<WL, WP>(L.kg, sm.nn, sub);
+            gnn = sm.nn;
+        }
+        float dep[WL];
+#pragma unroll
+        for (int b = 0; b < WL; ++b) {
+            float jk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gj[c].v[b], jk);
+            const float kds = gk.v[b] * ds;
+            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
+            const float em = expf(-tau[b]);               // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+            tau[b] += kds;                                // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+        if (!same) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (pc[c] >= 0) red_slice<WL, WP>(L.og, pc[c], sub, pend[c]);
+                pc[c] = sm.cell[c];
+#pragma unroll
+                for (int b = 0; b < WL; ++b) pend[c][b] = sm.w[c] * dep[b];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                for (int b = 0; b < WL; ++b) pend[c][b] = fmaf(sm.w[c], dep[b], pend[c][b]);
+            }
+        }
+        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
+        y = __fadd_rn(y, dy);
+        z = __fadd_rn(z, dz);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (pc[c] >= 0) red_slice<WL, WP>(L.og, pc[c], sub, pend[c]);
+}
+
+// PF = 2: prefetch and reuse combined. The corner set of substep k+1 is computed one step
+// ahead; its gathers are issued (only if it differs from the current set, else the registers
+// are carried over) before the update of substep k, so their latency overlaps that update.
+template <int W, int DET>
+__device__ __forceinline__ void march_lane_ahead(const Lane& L) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = L.sx, y = L.sy, z = L.sz;
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    const float ds = L.ds, scale = L.scale;
+    int pc[8];
+    float pend[8][W];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = -1;
+#pragma unroll
+        for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
+    }
+    Sample sm;
+    Gathered<W> gd;
+    make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+    gather<W>(jg, kg, sm, gd);
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
+        y = __fadd_rn(y, dy);
+        z = __fadd_rn(z, dz);
+        Sample nx;
+        make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx);
+        Gathered<W> ng = gd;
+        if (k + 1 < L.ns) {
+            if (nx.cell[0] != sm.cell[0] || nx.cell[7] != sm.cell[7]) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) ng.j[c] = ldg_vec<W>(jg, nx.cell[c]);
+            }
+            if (nx.nn != sm.nn) ng.k = ldg_vec<W>(kg, nx.nn);
+        }
+        float dep[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float jk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
+            const float kds = gd.k.v[b] * ds;
+            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
+            const float em = expf(-tau[b]);               // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+            tau[b] += kds;                                // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+        if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (pc[c] >= 0) flush<W, DET>(L, pc[c], pend[c]);
+                pc[c] = sm.cell[c];
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = sm.w[c] * dep[b];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = fmaf(sm.w[c], dep[b], pend[c][b]);
+            }
+        }
+        sm = nx;
+        gd = ng;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (pc[c] >= 0) flush<W, DET>(L, pc[c], pend[c]);
+}
+
 template <int W, int PF, int DET = 0>
 __device__ __forceinline__ void march_lane(const Lane& L) {
+    if (PF == 2) {
+        march_lane_ahead<W, DET>(L);
+        return;
+    }
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
     float* __restrict__ og = L.og;

@@ -39,7 +39,9 @@ struct MarchArgs {
     int n_freq;             // real bins (deterministic mode writes only these)
     int kappa_mode;
     int block;              // threads per block
-    int prefetch;           // 1: issue the next substep's gathers before the current update
+    int prefetch;           // 0: gathers reused while the corner set is unchanged; 1: the next
+                            // substep's gathers issued before the current update; 2: both
+    int lanes_per_ray;      // 1, or 2 / 4 adjacent lanes sharing a ray of a 4-bin group
 };
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);

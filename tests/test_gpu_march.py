@@ -216,3 +216,14 @@ def test_deterministic_mode_full_size(torch_cuda):
     b = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy()
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
     assert_parity(a, run_oracle(p))
+
+
+@pytest.mark.parametrize("plan", [(4, 64, 0, 2), (4, 128, 0, 4), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
+                                  (1, 32, 0, 1)])
+def test_every_launch_plan_meets_parity(torch_cuda, plan):
+    """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray)
+    on a ragged multi-bin problem."""
+    p = inputs.random_small(60, shape=(18, 14, 22), n_freq=6, n_src=3, num_rays=257, horizon=16.0)
+    from paper_2511_09389_gb300.api import Grid
+    g = Grid(p.shape, 8, plan=plan)
+    assert_parity(run_gpu(torch_cuda, p, grid=g), run_oracle(p))
