@@ -214,33 +214,32 @@ rt_status rt_batch_destroy(rt_batch* batch);
 
 /* ---- Convolutional surrogate: building blocks ----------------------------------------
    A 3-D CNN maps (log kappa, log(1 + j)) to the log of the field. Its 3x3x3 convolutions run on
-   the tensor cores (tcgen05, BF16 operands, FP32 accumulate). Activations use the CP8 layout:
-   bf16 [B][P][D][H][W][8] holding channel c at plane c / 8, lane c % 8, with
-   P = rt_cp8_planes(C) = 2 * ceil(C / 16) planes (channels beyond C are zero). The
-   convolution is the "same" cross-correlation with zero padding and dilation d:
+   the tensor cores (tcgen05, BF16 operands, FP32 accumulate). Activations use the C32 layout:
+   bf16 [B][D][H][W][32], 32 channels (64 bytes) per voxel, channels beyond the real count C
+   zero, so every activation buffer holds B * D*H*W * 32 bf16 whatever C is (1 <= C <= 32).
+   The convolution is the "same" cross-correlation with zero padding and dilation d:
      y[b][o][p] = bias[o] + sum_{i, tap} w[o][i][tap] x[b][i][p + (tap - centre) * d].
    All buffers are device memory; calls are asynchronous on the stream. */
-int rt_cp8_planes(int channels);
 
-/* FP32 [B][C][D][H][W] -> CP8 (dst holds B * P * D*H*W * 8 bf16), and back. */
-rt_status rt_cp8_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* cuda_stream);
-rt_status rt_cp8_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* cuda_stream);
+/* FP32 [B][C][D][H][W] -> C32 (all 32 channels written), and back (the first C channels). */
+rt_status rt_c32_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* cuda_stream);
+rt_status rt_c32_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* cuda_stream);
 
 /* Pack FP32 weights w[c_out][c_in][27] (tap = kz*9 + ky*3 + kx) into the kernel's bf16 layout
-   [27][P_k][N][8]. transpose = 0: for the forward convolution (P_k = P(c_in), N = c_out rounded
-   up to 16). transpose = 1: for the data gradient, i.e. the convolution with flipped taps that
-   maps c_out channels back to c_in (P_k = P(c_out), N = c_in rounded up to 16).
-   1 <= c_in, c_out <= 32. */
+   [27][32][32] = [tap][n][k], 27 * 1024 bf16, unused entries zero. transpose = 0: for the forward
+   convolution (n = output, k = input channel). transpose = 1: for the data gradient, the
+   convolution with flipped taps that maps c_out channels back to c_in (n = input channel of the
+   forward layer, k = its output channel). 1 <= c_in, c_out <= 32. */
 rt_status rt_conv3d_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed,
                                  void* cuda_stream);
 
-/* One convolution layer on the tensor cores. x: CP8 with P(c_in) planes; w_packed from
-   rt_conv3d_pack_weights; bias [c_out] or NULL; act 0 = identity, 1 = LeakyReLU(slope).
-   mask (CP8, P(c_out) planes, or NULL): outputs where mask <= 0 are multiplied by slope before
-   the activation (the LeakyReLU derivative when back-propagating). Outputs: y (CP8, P(c_out)
-   planes) and/or y_f32 ([B][D][H][W], FP32 channel 0). Requires W == 64, even H,
-   1 <= c_in, c_out <= 32. Waits inside the kernel are bounded: a timeout is reported by
-   rt_device_status. */
+/* One convolution layer on the tensor cores. x: C32; w_packed from rt_conv3d_pack_weights;
+   bias [c_out] or NULL; act 0 = identity, 1 = LeakyReLU(slope). mask (C32, or NULL): outputs
+   where mask <= 0 are multiplied by slope before the activation (the LeakyReLU derivative when
+   back-propagating). Outputs: y (C32, channels >= c_out written as 0) and/or y_f32
+   ([B][D][H][W], FP32 channel 0). Requires W == 64, even H, 1 <= c_in, c_out <= 32; x must be
+   16-byte aligned (a cudaMalloc pointer is). Waits inside the kernel are bounded: a timeout is
+   reported by rt_device_status. */
 rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in, const void* w_packed,
                             const float* bias, int c_out, int dilation, int act, float slope,
                             const void* mask, void* y, float* y_f32, void* cuda_stream);
@@ -248,12 +247,12 @@ rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in,
 /* Weight and bias gradients of rt_conv3d_forward for dz = dL/d(pre-activation output):
      dw[co][ci][tap] += sum_{b, p} dz[b][co][p] x[b][ci][p + (tap - centre) * d],
      db[co] += sum_{b, p} dz[b][co][p]          (ACCUMULATED: zero them first).
-   x: CP8 with P(c_in) planes, dz: CP8 with P(c_out) planes; dw (FP32 [c_out][c_in][27]) or db
-   may be NULL. The sums over voxels run on the tensor cores with FP32 accumulation. */
+   x, dz: C32; dw (FP32 [c_out][c_in][27]) or db may be NULL. The sums over voxels run on the
+   tensor cores with FP32 accumulation. */
 rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int H, int W, int c_in,
                                 int c_out, int dilation, float* dw, float* db, void* cuda_stream);
 
-/* Surrogate input features from FP32 kappa, j [B][D][H][W]: CP8 with 2 planes holding
+/* Surrogate input features from FP32 kappa, j [B][D][H][W]: C32 holding
    channel 0 = log(kappa / 0.05), channel 1 = log(1 + j), other channels 0. */
 rt_status rt_surrogate_features(const float* kappa, const float* j, int B, int D, int H, int W, void* x,
                                 void* cuda_stream);
@@ -263,8 +262,8 @@ rt_status rt_field_max(const float* field, int B, long long vox, float* out, voi
 
 /* Training loss of the surrogate: *loss += mean over b, v of (pred - T)^2 with the target
    T = (log(field + eps_rel * fmax[b]) - mu) / sigma (the log field, standardised); when grad is
-   non-NULL its gradient 2 (pred - T) / (B vox) is written to channel 0 of the CP8 tensor grad
-   (2 planes). pred, field: FP32 [B][vox]. */
+   non-NULL its gradient 2 (pred - T) / (B vox) is written to channel 0 of the C32 tensor grad
+   (the other channels 0). pred, field: FP32 [B][vox]. */
 rt_status rt_log_field_loss(const float* pred, const float* field, int B, long long vox, const float* fmax,
                             float eps_rel, float mu, float sigma, void* grad, float* loss, void* cuda_stream);
 
@@ -273,15 +272,16 @@ rt_status rt_log_field_loss(const float* pred, const float* field, int B, long l
 rt_status rt_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
                          float eps_rel, float mu, float sigma, float* out, void* cuda_stream);
 
-/* out[b][c] = mean over voxels of channel c of a CP8 tensor with C channels (overwritten). */
-rt_status rt_cp8_channel_mean(const void* x, int B, int C, long long vox, float* out, void* cuda_stream);
+/* out[b][c] = mean over voxels of channel c < C of a C32 tensor (overwritten). */
+rt_status rt_c32_channel_mean(const void* x, int B, int C, long long vox, float* out, void* cuda_stream);
 
 /* One bias-corrected Adam step on n FP32 parameters (step >= 1 counts from 1). */
 rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, long long n, float lr,
                        float beta1, float beta2, float eps, int step, void* cuda_stream);
 
 /* Synchronising read-and-clear of this device's kernel error word: RT_OK, or RT_ERR_TIMEOUT
-   with *code = which wait gave up (1-3: convolution ring / accumulator, 4-8: weight gradient). */
+   with *code = which wait gave up (1-4, 11: convolution ring / accumulator / completion, 5-9:
+   weight gradient, 10: shared memory not 1024-byte aligned). */
 rt_status rt_device_status(int* code);
 
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per

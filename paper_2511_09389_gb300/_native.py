@@ -20,9 +20,9 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
-           "rt_batch_destroy", "rt_cp8_planes", "rt_cp8_from_f32", "rt_cp8_to_f32", "rt_conv3d_pack_weights",
+           "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
-           "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_cp8_channel_mean",
+           "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_c32_channel_mean",
            "rt_adam_step")
 
 
@@ -104,12 +104,10 @@ def load(path: str = LIB_PATH):
         lib.rt_batch_updates.restype = ctypes.c_longlong
         lib.rt_batch_destroy.argtypes = [vp]
         lib.rt_batch_destroy.restype = i
-        lib.rt_cp8_planes.argtypes = [i]
-        lib.rt_cp8_planes.restype = i
-        lib.rt_cp8_from_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
-        lib.rt_cp8_from_f32.restype = i
-        lib.rt_cp8_to_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
-        lib.rt_cp8_to_f32.restype = i
+        lib.rt_c32_from_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
+        lib.rt_c32_from_f32.restype = i
+        lib.rt_c32_to_f32.argtypes = [vp, i, i, i, i, i, vp, vp]
+        lib.rt_c32_to_f32.restype = i
         lib.rt_conv3d_pack_weights.argtypes = [vp, i, i, i, vp, vp]
         lib.rt_conv3d_pack_weights.restype = i
         lib.rt_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, i, f, vp, vp, vp, vp]
@@ -125,8 +123,8 @@ def load(path: str = LIB_PATH):
         lib.rt_log_field_loss.restype = i
         lib.rt_field_error.argtypes = [vp, vp, i, ll, vp, f, f, f, vp, vp]
         lib.rt_field_error.restype = i
-        lib.rt_cp8_channel_mean.argtypes = [vp, i, i, ll, vp, vp]
-        lib.rt_cp8_channel_mean.restype = i
+        lib.rt_c32_channel_mean.argtypes = [vp, i, i, ll, vp, vp]
+        lib.rt_c32_channel_mean.restype = i
         lib.rt_adam_step.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, i, vp]
         lib.rt_adam_step.restype = i
         lib.rt_device_status.argtypes = [ctypes.POINTER(ctypes.c_int)]

@@ -114,18 +114,16 @@ cudaError_t launch_march_batch(int W, const BatchInst* insts, const int4* items,
 cudaError_t launch_pack_batch(const BatchInst* insts, int n_inst, long long max_elems, int which, cudaStream_t st);
 cudaError_t launch_unpack_batch(const BatchInst* insts, int n_inst, long long max_elems, cudaStream_t st);
 
-// One 3x3x3 convolution layer on the tensor cores (conv3d_tc.cu). Activations in CP8 layout:
-// bf16 [B][C/8][D][H][W][8] with C padded to a multiple of 16; W must be 64, H even.
+// One 3x3x3 convolution layer on the tensor cores (conv3d_tc.cu). Activations in the C32
+// layout: bf16 [B][D][H][W][32], channels beyond the real count zero; W must be 64, H even.
 struct ConvLaunch {
-    const void* x;            // CP8 input, kc_in planes per sample
-    const void* w_packed;     // bf16 [27][kc_in][nco][8] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1))
+    const void* x;            // C32 input
+    const void* w_packed;     // bf16 [27][32 out][32 in] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1))
     const float* bias;        // [c_out] or NULL
-    const void* mask_src;     // CP8 with nco/8 planes: outputs where it is <= 0 are scaled by slope
-    void* y;                  // CP8 output with nco/8 planes, or NULL
+    const void* mask_src;     // C32 or NULL: outputs where it is <= 0 are scaled by slope
+    void* y;                  // C32 output, or NULL
     float* y_f32;             // [B][D][H][W] FP32 copy of output channel 0, or NULL
     int B, D, H, W;
-    int kc_in;                // input planes (2 or 4)
-    int nco;                  // padded output channels (16 or 32)
     int c_out;                // real output channels (the rest are written as 0)
     int dil;                  // dilation
     int act;                  // 0: identity, 1: LeakyReLU(slope)
@@ -135,17 +133,17 @@ struct ConvLaunch {
 cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st);
 
 // Weight gradient of one layer on the tensor cores: dw[co][ci][27] += sum over voxels of
-// dz[v][co] * x[v + off(tap)][ci]. x: CP8 with kc_in planes; dz: CP8 with nco/8 planes.
+// dz[v][co] * x[v + off(tap)][ci]. x, dz: C32.
 struct WgradLaunch {
     const void* x;
     const void* dz;
     float* dw;
-    int B, D, H, W, kc_in, nco, c_in, c_out, dil;
+    int B, D, H, W, c_in, c_out, dil;
     int* err;
 };
 cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st);
-// db[co] += sum over voxels of dz[v][co] (dz: CP8 with kc planes).
-cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st);
+// db[co] += sum over voxels of dz[v][co] (dz: C32).
+cudaError_t launch_bias_grad(const void* dz, int B, long long vox, int c_out, float* db, cudaStream_t st);
 
 // Surrogate element-wise and reduction kernels (surrogate_ops.cu).
 cudaError_t launch_features(const float* kappa, const float* j, int B, long long vox, void* x, cudaStream_t st);
@@ -154,15 +152,15 @@ cudaError_t launch_log_loss(const float* pred, const float* field, int B, long l
                             float eps_rel, float mu, float sigma, void* grad, float* loss, cudaStream_t st);
 cudaError_t launch_field_error(const float* pred, const float* field, int B, long long vox, const float* fmax,
                                float eps_rel, float mu, float sigma, float* out, cudaStream_t st);
-cudaError_t launch_channel_mean(const void* x, int B, int C, int kc, long long vox, float* out, cudaStream_t st);
+cudaError_t launch_channel_mean(const void* x, int B, int C, long long vox, float* out, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                         float eps, int step, cudaStream_t st);
 
-// FP32 [B][C][vox] <-> CP8 bf16 [B][kc][vox][8] (channels >= C are zero).
-cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st);
-cudaError_t launch_from_cp8(const void* src, int B, int C, int kc, long long vox, float* dst, cudaStream_t st);
-// FP32 [c_out][c_in][27] -> bf16 [27][kc][nco][8] (transpose = 1: flipped taps, c_in <-> c_out).
-cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int kc, int nco, int transpose, void* packed,
-                                cudaStream_t st);
+// FP32 [B][C][vox] <-> C32 bf16 [B][vox][32] (channels >= C are zero), C <= 32.
+cudaError_t launch_to_c32(const float* src, int B, int C, long long vox, void* dst, cudaStream_t st);
+cudaError_t launch_from_c32(const void* src, int B, int C, long long vox, float* dst, cudaStream_t st);
+// FP32 [c_out][c_in][27] -> bf16 [27][32][32] (tap, n, k); forward: n = output, k = input
+// channel; transpose = 1 (data gradient): flipped taps, n = input, k = output channel.
+cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed, cudaStream_t st);
 
 }  // namespace rt

@@ -23,8 +23,6 @@ rt_status cuda_err(cudaError_t e, const char* what) {
     return err(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int planes(int c) { return 2 * ((c + 15) / 16); }
-
 std::mutex g_mu;
 int* g_err[64] = {};
 
@@ -53,27 +51,24 @@ rt_status check_shape(int B, int D, int H, int W) {
 
 extern "C" {
 
-int rt_cp8_planes(int channels) { return channels < 1 ? 0 : planes(channels); }
-
-rt_status rt_cp8_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* stream) {
-    if (!src || !dst || B < 1 || C < 1 || D < 1 || H < 1 || W < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_from_f32: bad arguments");
-    cudaError_t e = rt::launch_to_cp8(src, B, C, planes(C), (long long)D * H * W, dst, (cudaStream_t)stream);
-    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_from_f32");
+rt_status rt_c32_from_f32(const float* src, int B, int C, int D, int H, int W, void* dst, void* stream) {
+    if (!src || !dst || B < 1 || C < 1 || C > 32 || D < 1 || H < 1 || W < 1)
+        return err(RT_ERR_INVALID_ARG, "rt_c32_from_f32: bad arguments (1 <= C <= 32)");
+    cudaError_t e = rt::launch_to_c32(src, B, C, (long long)D * H * W, dst, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_c32_from_f32");
 }
 
-rt_status rt_cp8_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* stream) {
-    if (!src || !dst || B < 1 || C < 1 || D < 1 || H < 1 || W < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_to_f32: bad arguments");
-    cudaError_t e = rt::launch_from_cp8(src, B, C, planes(C), (long long)D * H * W, dst, (cudaStream_t)stream);
-    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_to_f32");
+rt_status rt_c32_to_f32(const void* src, int B, int C, int D, int H, int W, float* dst, void* stream) {
+    if (!src || !dst || B < 1 || C < 1 || C > 32 || D < 1 || H < 1 || W < 1)
+        return err(RT_ERR_INVALID_ARG, "rt_c32_to_f32: bad arguments (1 <= C <= 32)");
+    cudaError_t e = rt::launch_from_c32(src, B, C, (long long)D * H * W, dst, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_c32_to_f32");
 }
 
 rt_status rt_conv3d_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed, void* stream) {
     if (!w || !packed || c_in < 1 || c_in > 32 || c_out < 1 || c_out > 32)
         return err(RT_ERR_INVALID_ARG, "rt_conv3d_pack_weights: need 1 <= c_in, c_out <= 32");
-    // forward: K = c_in planes, N = c_out padded; data gradient: K = c_out planes, N = c_in padded
-    const int kc = transpose ? planes(c_out) : planes(c_in);
-    const int nco = ((transpose ? c_in : c_out) + 15) / 16 * 16;
-    cudaError_t e = rt::launch_pack_weights(w, c_in, c_out, kc, nco, transpose ? 1 : 0, packed, (cudaStream_t)stream);
+    cudaError_t e = rt::launch_pack_weights(w, c_in, c_out, transpose ? 1 : 0, packed, (cudaStream_t)stream);
     return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_conv3d_pack_weights");
 }
 
@@ -90,8 +85,6 @@ rt_status rt_conv3d_forward(const void* x, int B, int D, int H, int W, int c_in,
     rt::ConvLaunch c{};
     c.x = x; c.w_packed = w_packed; c.bias = bias; c.mask_src = mask; c.y = y; c.y_f32 = y_f32;
     c.B = B; c.D = D; c.H = H; c.W = W;
-    c.kc_in = planes(c_in);
-    c.nco = (c_out + 15) / 16 * 16;
     c.c_out = c_out; c.dil = dilation; c.act = act; c.slope = slope; c.err = ew;
     cudaError_t e = rt::launch_conv3d_tc(c, (cudaStream_t)stream);
     return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_conv3d_forward launch");
@@ -111,14 +104,12 @@ rt_status rt_conv3d_weight_grad(const void* x, const void* dz, int B, int D, int
         rt::WgradLaunch c{};
         c.x = x; c.dz = dz; c.dw = dw;
         c.B = B; c.D = D; c.H = H; c.W = W;
-        c.kc_in = planes(c_in);
-        c.nco = (c_out + 15) / 16 * 16;
         c.c_in = c_in; c.c_out = c_out; c.dil = dilation; c.err = ew;
         cudaError_t e = rt::launch_conv3d_wgrad(c, st);
         if (e != cudaSuccess) return cuda_err(e, "rt_conv3d_weight_grad launch");
     }
     if (db) {
-        cudaError_t e = rt::launch_bias_grad(dz, B, planes(c_out), (long long)D * H * W, c_out, db, st);
+        cudaError_t e = rt::launch_bias_grad(dz, B, (long long)D * H * W, c_out, db, st);
         if (e != cudaSuccess) return cuda_err(e, "bias gradient launch");
     }
     return RT_OK;
@@ -152,10 +143,11 @@ rt_status rt_field_error(const float* pred, const float* field, int B, long long
     return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_field_error");
 }
 
-rt_status rt_cp8_channel_mean(const void* x, int B, int C, long long vox, float* out, void* stream) {
-    if (!x || !out || B < 1 || C < 1 || vox < 1) return err(RT_ERR_INVALID_ARG, "rt_cp8_channel_mean: bad arguments");
-    cudaError_t e = rt::launch_channel_mean(x, B, C, planes(C), vox, out, (cudaStream_t)stream);
-    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_cp8_channel_mean");
+rt_status rt_c32_channel_mean(const void* x, int B, int C, long long vox, float* out, void* stream) {
+    if (!x || !out || B < 1 || C < 1 || C > 32 || vox < 1)
+        return err(RT_ERR_INVALID_ARG, "rt_c32_channel_mean: bad arguments");
+    cudaError_t e = rt::launch_channel_mean(x, B, C, vox, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? RT_OK : cuda_err(e, "rt_c32_channel_mean");
 }
 
 rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, long long n, float lr, float beta1,

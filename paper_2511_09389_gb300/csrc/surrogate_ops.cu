@@ -1,10 +1,9 @@
 // surrogate_ops.cu -- element-wise and reduction kernels of the convolutional surrogate.
 //
-// Layout changes between plain FP32 NCDHW tensors and the CP8 bf16 layout of the tensor-core
-// convolution ([B][C/8][D][H][W][8]), weight packing ([C_out][C_in][27] FP32 -> [27][C_in/8]
-// [N][8] bf16, also flipped and transposed for the data gradient), the weight / bias gradient
-// of a convolution (a reduction over voxels), the surrogate's input features and loss, and an
-// Adam step.
+// Layout changes between plain FP32 NCDHW tensors and the C32 bf16 layout of the tensor-core
+// convolution ([B][D][H][W][32]), weight packing ([C_out][C_in][27] FP32 -> [27][32][32] bf16,
+// also flipped and transposed for the data gradient), per-channel sums (bias gradient, channel
+// means), the surrogate's input features and loss, and an Adam step.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,25 +20,25 @@ unsigned grid1d(long long n, int block) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
-__global__ void k_to_cp8(const float* __restrict__ src, int C, int kc, long long vox, int B,
-                         __nv_bfloat16* __restrict__ dst) {
-    const long long total = (long long)B * kc * vox;
+// One thread per (sample, 8-channel quarter, voxel), voxel fastest: coalesced FP32 reads.
+__global__ void k_to_c32(const float* __restrict__ src, int C, long long vox, int B, __nv_bfloat16* __restrict__ dst) {
+    const long long total = (long long)B * 4 * vox;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / (kc * vox), r = i - b * kc * vox;
-        const int k = (int)(r / vox);
-        const long long v = r - (long long)k * vox;
+        const long long b = i / (4 * vox), r = i - b * 4 * vox;
+        const int q = (int)(r / vox);
+        const long long v = r - (long long)q * vox;
         __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int c = k * 8 + e;
+            const int c = q * 8 + e;
             o[e] = __float2bfloat16_rn(c < C ? __ldg(src + ((long long)b * C + c) * vox + v) : 0.0f);
         }
-        reinterpret_cast<uint4*>(dst)[i] = *reinterpret_cast<uint4*>(o);
+        reinterpret_cast<uint4*>(dst)[((long long)b * vox + v) * 4 + q] = *reinterpret_cast<uint4*>(o);
     }
 }
 
-__global__ void k_from_cp8(const __nv_bfloat16* __restrict__ src, int C, int kc, long long vox, int B,
+__global__ void k_from_c32(const __nv_bfloat16* __restrict__ src, int C, long long vox, int B,
                            float* __restrict__ dst) {
     const long long total = (long long)B * C * vox;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -47,58 +46,59 @@ __global__ void k_from_cp8(const __nv_bfloat16* __restrict__ src, int C, int kc,
         const long long b = i / (C * vox), r = i - b * C * vox;
         const int c = (int)(r / vox);
         const long long v = r - (long long)c * vox;
-        dst[i] = __bfloat162float(src[(((long long)b * kc + c / 8) * vox + v) * 8 + (c & 7)]);
+        dst[i] = __bfloat162float(src[((long long)b * vox + v) * 32 + c]);
     }
 }
 
-// packed[tap][k][n][e]: forward (transpose = 0): w[n][8k+e][tap];
-// data gradient (transpose = 1): w[8k+e][n][26 - tap] (input = the forward's outputs).
-__global__ void k_pack_weights(const float* __restrict__ w, int c_in, int c_out, int kc, int nco, int transpose,
+// packed[tap][n][k]: forward (transpose = 0): w[n][k][tap];
+// data gradient (transpose = 1): w[k][n][26 - tap] (input = the forward's outputs).
+__global__ void k_pack_weights(const float* __restrict__ w, int c_in, int c_out, int transpose,
                                __nv_bfloat16* __restrict__ packed) {
-    const int total = 27 * kc * nco * 8;
+    const int total = 27 * 32 * 32;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int e = i & 7, n = (i >> 3) % nco, k = (i / (8 * nco)) % kc, tap = i / (8 * nco * kc);
-        const int c = k * 8 + e;
+        const int k = i & 31, n = (i >> 5) & 31, tap = i >> 10;
         float v = 0.0f;
         if (!transpose) {
-            if (n < c_out && c < c_in) v = w[((long long)n * c_in + c) * 27 + tap];
+            if (n < c_out && k < c_in) v = w[((long long)n * c_in + k) * 27 + tap];
         } else {
-            // the transposed convolution maps c_out (its input, index c) to c_in (its output, index n)
-            if (c < c_out && n < c_in) v = w[((long long)c * c_in + n) * 27 + (26 - tap)];
+            // the transposed convolution maps c_out (its input, index k) to c_in (its output, index n)
+            if (k < c_out && n < c_in) v = w[((long long)k * c_in + n) * 27 + (26 - tap)];
         }
         packed[i] = __float2bfloat16_rn(v);
     }
 }
 
-// db[co] += sum_v dz[b][co/8][v][co%8]: one block per (sample, plane) reduces 8 channels.
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dz, int kc, long long vox, int c_out,
-                            float* __restrict__ db) {
-    const int b = blockIdx.y, k = blockIdx.x;
-    const uint4* p = reinterpret_cast<const uint4*>(dz) + ((long long)b * kc + k) * vox;
+// out[b * per_sample][c] += scale * sum over voxels of channel c (c < C) of a C32 tensor. Thread t
+// owns channel quarter t & 3 of voxels t >> 2, t >> 2 + blockDim / 4, ... (coalesced 16-byte
+// loads); lanes with the same quarter are then summed. Grid: (blocks, B).
+__global__ void k_channel_sum(const __nv_bfloat16* __restrict__ x, long long vox, int C, float scale, int per_sample,
+                              float* __restrict__ out) {
+    const int b = blockIdx.y, q = threadIdx.x & 3;
+    const uint4* p = reinterpret_cast<const uint4*>(x) + (long long)b * vox * 4;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long v = threadIdx.x; v < vox; v += blockDim.x) {
-        const uint4 q = __ldg(p + v);
-        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+    const long long step = (long long)gridDim.x * (blockDim.x >> 2);
+    for (long long v = blockIdx.x * (long long)(blockDim.x >> 2) + (threadIdx.x >> 2); v < vox; v += step) {
+        const uint4 u = __ldg(p + v * 4 + q);
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] += __bfloat162float(e[i]);
     }
-    __shared__ float red[8][33];
+    __shared__ float red[32][33];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float x = acc[i];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = x;
+        float t = acc[i];
+        for (int o = 16; o >= 4; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) < 4) red[q * 8 + i][threadIdx.x >> 5] = t;
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
-        float x = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
-        const int co = k * 8 + threadIdx.x;
-        if (co < c_out) atomicAdd(db + co, x);
+    if (threadIdx.x < 32) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        if ((int)threadIdx.x < C) atomicAdd(out + (per_sample ? (long long)b * C : 0) + threadIdx.x, t * scale);
     }
 }
 
-// Surrogate inputs: channel 0 = log(kappa / 0.05), channel 1 = log(1 + j); CP8 with 2 planes.
+// Surrogate inputs: channel 0 = log(kappa / 0.05), channel 1 = log(1 + j); C32, other channels 0.
 __global__ void k_features(const float* __restrict__ kappa, const float* __restrict__ j, long long vox, int B,
                            __nv_bfloat16* __restrict__ x) {
     const long long total = (long long)B * vox;
@@ -111,9 +111,9 @@ __global__ void k_features(const float* __restrict__ kappa, const float* __restr
         o[1] = __float2bfloat16_rn(log1pf(fmaxf(__ldg(j + i), 0.0f)));
 #pragma unroll
         for (int e = 2; e < 8; ++e) o[e] = __float2bfloat16_rn(0.0f);
-        uint4* X = reinterpret_cast<uint4*>(x);
-        X[(b * 2) * vox + v] = *reinterpret_cast<uint4*>(o);
-        X[(b * 2 + 1) * vox + v] = make_uint4(0, 0, 0, 0);
+        uint4* X = reinterpret_cast<uint4*>(x) + (b * vox + v) * 4;
+        X[0] = *reinterpret_cast<uint4*>(o);
+        X[1] = X[2] = X[3] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -139,8 +139,8 @@ __global__ void k_field_max(const float* __restrict__ f, long long vox, float* _
 }
 
 // Loss sum_{b,v} (pred - T)^2 / (B vox) with T = (log(F + eps_b) - mu) / sigma,
-// eps_b = eps_rel * max_b F; its gradient 2 (pred - T) / (B vox) goes to channel 0 of a CP8
-// tensor with 2 planes (the other channels zero).
+// eps_b = eps_rel * max_b F; its gradient 2 (pred - T) / (B vox) goes to channel 0 of a C32
+// tensor (the other channels zero).
 __global__ void k_log_loss(const float* __restrict__ pred, const float* __restrict__ field, long long vox, int B,
                            const float* __restrict__ fmax, float eps_rel, float mu, float inv_sigma,
                            __nv_bfloat16* __restrict__ grad, float* __restrict__ loss) {
@@ -160,9 +160,9 @@ __global__ void k_log_loss(const float* __restrict__ pred, const float* __restri
             o[0] = __float2bfloat16_rn(2.0f * d * norm);
 #pragma unroll
             for (int e = 1; e < 8; ++e) o[e] = __float2bfloat16_rn(0.0f);
-            uint4* G = reinterpret_cast<uint4*>(grad);
-            G[(b * 2) * vox + v] = *reinterpret_cast<uint4*>(o);
-            G[(b * 2 + 1) * vox + v] = make_uint4(0, 0, 0, 0);
+            uint4* G = reinterpret_cast<uint4*>(grad) + (b * vox + v) * 4;
+            G[0] = *reinterpret_cast<uint4*>(o);
+            G[1] = G[2] = G[3] = make_uint4(0, 0, 0, 0);
         }
     }
     const float t = block_sum(acc, red);
@@ -188,27 +188,6 @@ __global__ void k_field_error(const float* __restrict__ pred, const float* __res
     const float a = block_sum(e2, red);
     const float c = block_sum(f2, red);
     if (threadIdx.x == 0) { atomicAdd(out + 2 * b, a); atomicAdd(out + 2 * b + 1, c); }
-}
-
-// out[b][c] = mean over voxels of channel c of a CP8 tensor (kc planes).
-__global__ void k_channel_mean(const __nv_bfloat16* __restrict__ x, int kc, long long vox, int C,
-                               float* __restrict__ out) {
-    const int b = blockIdx.y, k = blockIdx.z;
-    const uint4* p = reinterpret_cast<const uint4*>(x) + ((long long)b * kc + k) * vox;
-    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < vox; v += (long long)gridDim.x * blockDim.x) {
-        const uint4 q = __ldg(p + v);
-        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] += __bfloat162float(e[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float t = acc[i];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        const int c = k * 8 + i;
-        if ((threadIdx.x & 31) == 0 && c < C) atomicAdd(out + (long long)b * C + c, t / (float)vox);
-    }
 }
 
 // Adam (bias-corrected), FP32 master parameters.
@@ -253,10 +232,11 @@ cudaError_t launch_field_error(const float* pred, const float* field, int B, lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_channel_mean(const void* x, int B, int C, int kc, long long vox, float* out, cudaStream_t st) {
+cudaError_t launch_channel_mean(const void* x, int B, int C, long long vox, float* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * B * C, st);
     if (e != cudaSuccess) return e;
-    k_channel_mean<<<dim3(32, B, kc), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(x), kc, vox, C, out);
+    k_channel_sum<<<dim3(32, B), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(x), vox, C, 1.0f / (float)vox, 1,
+                                               out);
     return cudaGetLastError();
 }
 
@@ -267,27 +247,25 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bias_grad(const void* dz, int B, int kc, long long vox, int c_out, float* db, cudaStream_t st) {
-    k_bias_grad<<<dim3(kc, B), 1024, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dz), kc, vox, c_out, db);
+cudaError_t launch_bias_grad(const void* dz, int B, long long vox, int c_out, float* db, cudaStream_t st) {
+    k_channel_sum<<<dim3(32, B), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dz), vox, c_out, 1.0f, 0, db);
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_cp8(const float* src, int B, int C, int kc, long long vox, void* dst, cudaStream_t st) {
-    k_to_cp8<<<grid1d((long long)B * kc * vox, 256), 256, 0, st>>>(src, C, kc, vox, B,
-                                                                    reinterpret_cast<__nv_bfloat16*>(dst));
+cudaError_t launch_to_c32(const float* src, int B, int C, long long vox, void* dst, cudaStream_t st) {
+    k_to_c32<<<grid1d((long long)B * 4 * vox, 256), 256, 0, st>>>(src, C, vox, B, reinterpret_cast<__nv_bfloat16*>(dst));
     return cudaGetLastError();
 }
 
-cudaError_t launch_from_cp8(const void* src, int B, int C, int kc, long long vox, float* dst, cudaStream_t st) {
-    k_from_cp8<<<grid1d((long long)B * C * vox, 256), 256, 0, st>>>(
-        reinterpret_cast<const __nv_bfloat16*>(src), C, kc, vox, B, dst);
+cudaError_t launch_from_c32(const void* src, int B, int C, long long vox, float* dst, cudaStream_t st) {
+    k_from_c32<<<grid1d((long long)B * C * vox, 256), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(src), C, vox,
+                                                                     B, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int kc, int nco, int transpose, void* packed,
-                                cudaStream_t st) {
-    k_pack_weights<<<grid1d(27LL * kc * nco * 8, 256), 256, 0, st>>>(w, c_in, c_out, kc, nco, transpose,
-                                                                      reinterpret_cast<__nv_bfloat16*>(packed));
+cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed, cudaStream_t st) {
+    k_pack_weights<<<grid1d(27LL * 32 * 32, 256), 256, 0, st>>>(w, c_in, c_out, transpose,
+                                                                 reinterpret_cast<__nv_bfloat16*>(packed));
     return cudaGetLastError();
 }
 

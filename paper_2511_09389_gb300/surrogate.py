@@ -73,11 +73,9 @@ class Surrogate:
         lib = self.lib
         st = torch.cuda.current_stream(self.device).cuda_stream
         if not self._packed:
-            for ci, co, _, _ in LAYERS:
-                kf = lib.rt_cp8_planes(ci) * ((co + 15) // 16 * 16) * 8 * 27
-                kt = lib.rt_cp8_planes(co) * ((ci + 15) // 16 * 16) * 8 * 27
-                self._packed.append((torch.empty(kf, dtype=torch.bfloat16, device=self.device),
-                                     torch.empty(kt, dtype=torch.bfloat16, device=self.device)))
+            for _ in LAYERS:
+                self._packed.append((torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device=self.device),
+                                     torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device=self.device)))
         for l, (ci, co, _, _) in enumerate(LAYERS):
             fw, tw = self._packed[l]
             check(lib.rt_conv3d_pack_weights(_p(self.w(l)), ci, co, 0, _p(fw), st))
@@ -103,8 +101,9 @@ class Surrogate:
             self._buf[name] = t
         return t[:n]
 
-    def _act(self, name, B, C, vox):
-        return self._get(name, B * self.lib.rt_cp8_planes(C) * vox * 8, torch.bfloat16)
+    def _act(self, name, B, vox):
+        """An activation buffer in the kernels' layout: bf16 [B][vox][32]."""
+        return self._get(name, B * vox * 32, torch.bfloat16)
 
     # -- forward / backward ---------------------------------------------------------------
     def forward(self, kappa, j, keep=False):
@@ -114,14 +113,14 @@ class Surrogate:
         B, D, H, W = kappa.shape
         vox = D * H * W
         st = torch.cuda.current_stream(self.device).cuda_stream
-        x = self._act("x0", B, 2, vox)
+        x = self._act("x0", B, vox)
         check(lib.rt_surrogate_features(_p(kappa.contiguous()), _p(j.contiguous()), B, D, H, W, _p(x), st))
         acts = [x]
         pred = self._get("pred", B * vox, torch.float32)
         for l, (ci, co, dil, act) in enumerate(LAYERS):
             fw, _ = self._packed[l]
             last = l == len(LAYERS) - 1
-            y = None if last else self._act(f"a{l + 1}", B, co, vox)
+            y = None if last else self._act(f"a{l + 1}", B, vox)
             check(lib.rt_conv3d_forward(_p(acts[-1]), B, D, H, W, ci, _p(fw), _p(self.b(l)), co, dil, act, SLOPE,
                                         None, _p(y), _p(pred) if last else None, st))
             if not last:
@@ -138,7 +137,7 @@ class Surrogate:
         st = torch.cuda.current_stream(self.device).cuda_stream
         loss = self._get("loss", 1, torch.float32)
         loss.zero_()
-        g = self._act("g_out", B, 1, vox)
+        g = self._act("g_out", B, vox)
         check(lib.rt_log_field_loss(_p(pred), _p(field), B, vox, _p(fmax), EPS_REL, self.mu, self.sigma, _p(g),
                                     _p(loss), st))
         self.grads.zero_()
@@ -149,7 +148,7 @@ class Surrogate:
                                             self.grads.data_ptr() + 4 * wo, self.grads.data_ptr() + 4 * bo, st))
             if l > 0:
                 _, tw = self._packed[l]
-                gn = self._act(f"g{l % 2}", B, ci, vox)
+                gn = self._act(f"g{l % 2}", B, vox)
                 # gradient w.r.t. the previous layer's pre-activation: transposed convolution,
                 # times the LeakyReLU derivative (sign of the stored activation)
                 check(lib.rt_conv3d_forward(_p(g), B, D, H, W, co, _p(tw), None, ci, dil, 0, SLOPE, _p(acts[l]),
@@ -176,7 +175,7 @@ class Surrogate:
         acts, *_ = self._acts
         vox = D * H * W
         out = self._get("pool", B * 32, torch.float32)
-        check(self.lib.rt_cp8_channel_mean(_p(acts[-1]), B, 32, vox, _p(out),
+        check(self.lib.rt_c32_channel_mean(_p(acts[-1]), B, 32, vox, _p(out),
                                            torch.cuda.current_stream(self.device).cuda_stream))
         f = out.view(B, 32).cpu().numpy().astype(np.float64)
         return np.concatenate([f, np.ones((B, 1))], axis=1)

@@ -31,18 +31,18 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
 
 
-def to_cp8(torch, lib, x):
+def to_c32(torch, lib, x):
     B, C, D, H, W = x.shape
-    P = lib.rt_cp8_planes(C)
     xt = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
-    out = torch.empty(B * P * D * H * W * 8, dtype=torch.bfloat16, device="cuda")
-    assert lib.rt_cp8_from_f32(xt.data_ptr(), B, C, D, H, W, out.data_ptr(), None) == 0
+    out = torch.empty(B * D * H * W * 32, dtype=torch.bfloat16, device="cuda")
+    assert lib.rt_c32_from_f32(xt.data_ptr(), B, C, D, H, W, out.data_ptr(), None) == 0
+    torch.cuda.synchronize()
     return out
 
 
-def from_cp8(torch, lib, buf, B, C, D, H, W):
+def from_c32(torch, lib, buf, B, C, D, H, W):
     out = torch.empty(B * C * D * H * W, dtype=torch.float32, device="cuda")
-    assert lib.rt_cp8_to_f32(buf.data_ptr(), B, C, D, H, W, out.data_ptr(), None) == 0
+    assert lib.rt_c32_to_f32(buf.data_ptr(), B, C, D, H, W, out.data_ptr(), None) == 0
     torch.cuda.synchronize()
     return out.cpu().numpy().reshape(B, C, D, H, W).astype(np.float64)
 
@@ -50,26 +50,27 @@ def from_cp8(torch, lib, buf, B, C, D, H, W):
 def pack(torch, lib, w, transpose):
     co, ci = w.shape[:2]
     wt = torch.from_numpy(np.ascontiguousarray(w.reshape(co, ci, 27), np.float32)).cuda()
-    kc = lib.rt_cp8_planes(co if transpose else ci)
-    n = ((ci if transpose else co) + 15) // 16 * 16
-    packed = torch.empty(27 * kc * n * 8, dtype=torch.bfloat16, device="cuda")
+    packed = torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device="cuda")
     assert lib.rt_conv3d_pack_weights(wt.data_ptr(), ci, co, int(transpose), packed.data_ptr(), None) == 0
+    torch.cuda.synchronize()
     return packed
 
 
-def conv_gpu(torch, lib, xcp, shape, c_in, packed, bias, c_out, dil, act, slope=0.1, mask=None, f32=False):
+def conv_gpu(torch, lib, xc, shape, c_in, packed, bias, c_out, dil, act, slope=0.1, mask=None, f32=False):
     B, D, H, W = shape
-    P = lib.rt_cp8_planes(c_out)
-    y = torch.zeros(B * P * D * H * W * 8, dtype=torch.bfloat16, device="cuda")
+    y = torch.full((B * D * H * W * 32,), float("nan"), dtype=torch.bfloat16, device="cuda")
     yf = torch.zeros(B * D * H * W, dtype=torch.float32, device="cuda") if f32 else None
     bt = torch.from_numpy(np.asarray(bias, np.float32)).cuda() if bias is not None else None
-    st = lib.rt_conv3d_forward(xcp.data_ptr(), B, D, H, W, c_in, packed.data_ptr(),
+    st = lib.rt_conv3d_forward(xc.data_ptr(), B, D, H, W, c_in, packed.data_ptr(),
                                bt.data_ptr() if bt is not None else None, c_out, dil, act, slope,
                                mask.data_ptr() if mask is not None else None, y.data_ptr(),
                                yf.data_ptr() if yf is not None else None, None)
     assert st == 0, lib.rt_last_error()
     code = ctypes.c_int()
     assert lib.rt_device_status(ctypes.byref(code)) == 0, code.value
+    # every channel is written: the ones beyond c_out as exact zeros
+    pad = y.view(B * D * H * W, 32)[:, c_out:].float().cpu().numpy()
+    assert np.all(pad == 0.0)
     return y, yf
 
 
@@ -85,11 +86,11 @@ def test_conv_forward_matches_oracle(env, c_in, c_out, dil, act):
     ref = oracle.conv3d_fwd(x, w, b, dil)
     if act:
         ref = np.where(ref > 0, ref, 0.1 * ref)
-    y, yf = conv_gpu(torch, lib, to_cp8(torch, lib, x), (B, D, H, W), c_in, pack(torch, lib, w, False), b, c_out,
+    y, yf = conv_gpu(torch, lib, to_c32(torch, lib, x), (B, D, H, W), c_in, pack(torch, lib, w, False), b, c_out,
                      dil, act, f32=True)
     torch.cuda.synchronize()
     assert rel(yf.cpu().numpy().reshape(B, D, H, W), ref[:, 0]) <= 1e-4
-    assert rel(from_cp8(torch, lib, y, B, c_out, D, H, W), ref) <= 1e-2
+    assert rel(from_c32(torch, lib, y, B, c_out, D, H, W), ref) <= 1e-2
 
 
 def test_conv_masked_output(env):
@@ -102,9 +103,9 @@ def test_conv_masked_output(env):
     m = bf16_round(rng.standard_normal((B, c, D, H, W)))
     ref = oracle.conv3d_fwd(x, w, None, 1)
     ref = np.where(m > 0, ref, 0.2 * ref)
-    y, _ = conv_gpu(torch, lib, to_cp8(torch, lib, x), (B, D, H, W), c, pack(torch, lib, w, False), None, c, 1, 0,
-                    slope=0.2, mask=to_cp8(torch, lib, m))
-    assert rel(from_cp8(torch, lib, y, B, c, D, H, W), ref) <= 1e-2
+    y, _ = conv_gpu(torch, lib, to_c32(torch, lib, x), (B, D, H, W), c, pack(torch, lib, w, False), None, c, 1, 0,
+                    slope=0.2, mask=to_c32(torch, lib, m))
+    assert rel(from_c32(torch, lib, y, B, c, D, H, W), ref) <= 1e-2
 
 
 @pytest.mark.parametrize("c_in,c_out,dil", [(32, 32, 1), (32, 32, 2), (32, 1, 1), (2, 32, 1)])
@@ -117,15 +118,20 @@ def test_conv_data_gradient_matches_oracle(env, c_in, c_out, dil):
     w = bf16_round(rng.standard_normal((c_out, c_in, 3, 3, 3)) / np.sqrt(27 * c_in))
     gy = bf16_round(rng.standard_normal((B, c_out, D, H, W)))
     gx, _, _ = oracle.conv3d_bwd(x, w, gy, dil)
-    y, _ = conv_gpu(torch, lib, to_cp8(torch, lib, gy), (B, D, H, W), c_out, pack(torch, lib, w, True), None, c_in,
+    y, _ = conv_gpu(torch, lib, to_c32(torch, lib, gy), (B, D, H, W), c_out, pack(torch, lib, w, True), None, c_in,
                     dil, 0)
-    assert rel(from_cp8(torch, lib, y, B, c_in, D, H, W), gx) <= 1e-2
+    assert rel(from_c32(torch, lib, y, B, c_in, D, H, W), gx) <= 1e-2
 
 
-def test_cp8_round_trip(env):
+def test_c32_round_trip(env):
     torch, lib = env
     x = bf16_round(np.random.default_rng(1).standard_normal((3, 19, 2, 4, 64)))
-    assert np.array_equal(from_cp8(torch, lib, to_cp8(torch, lib, x), 3, 19, 2, 4, 64), x)
+    buf = to_c32(torch, lib, x)
+    assert np.array_equal(from_c32(torch, lib, buf, 3, 19, 2, 4, 64), x)
+    # layout: channel c of voxel v at element v * 32 + c, channels >= 19 zero
+    raw = buf.view(3, 2 * 4 * 64, 32).float().cpu().numpy()
+    assert np.array_equal(raw[:, :, :19], x.reshape(3, 19, -1).transpose(0, 2, 1))
+    assert np.all(raw[:, :, 19:] == 0.0)
 
 
 @pytest.mark.parametrize("c_in,c_out,dil", [(32, 32, 1), (32, 32, 4), (2, 32, 1), (32, 1, 2), (9, 5, 1)])
@@ -140,7 +146,7 @@ def test_conv_weight_and_bias_gradients_match_oracle(env, c_in, c_out, dil):
     _, gw, gb = oracle.conv3d_bwd(x, w, gy, dil)
     dw = torch.zeros(c_out * c_in * 27, dtype=torch.float32, device="cuda")
     db = torch.zeros(c_out, dtype=torch.float32, device="cuda")
-    xc, gc = to_cp8(torch, lib, x), to_cp8(torch, lib, gy)      # keep both alive until the kernel ran
+    xc, gc = to_c32(torch, lib, x), to_c32(torch, lib, gy)      # keep both alive until the kernel ran
     st = lib.rt_conv3d_weight_grad(xc.data_ptr(), gc.data_ptr(), B, D, H, W, c_in, c_out, dil, dw.data_ptr(),
                                    db.data_ptr(), None)
     assert st == 0, lib.rt_last_error()
