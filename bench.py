@@ -272,6 +272,14 @@ def surrogate_leg(args, dev):
     errs, est = S.fit_estimator(model, train, batch=32)
     res = S.evaluate(model, grid, held, batch=32)
     grid.close()
+    # one hidden layer of the network on its own, against the measured bf16 tensor peak
+    conv = S.time_conv_layer(batch=32, edge=64, dilation=2)
+    _, _, peaks = load_peaks()
+    peak_tf = float(peaks.get("bf16_tflops", 1900.0))
+    conv["roofline"] = {"bound": "tensor", "achieved": conv["forward_tflops"], "peak": peak_tf, "unit": "TFLOP/s",
+                        "frac": conv["forward_tflops"] / peak_tf,
+                        "peak_kind": "measured" if "bf16_tflops" in peaks else "fallback"}
+    res["conv_layer"] = conv
     res.update({"train_fields": len(train), "epochs": args.surrogate_epochs, "loss_per_epoch": losses,
                 "train_rel_l2_median": float(np.median(errs)), "estimate_threshold_log10": model.est_threshold,
                 "data_generation_s": t_data, "training_s": t_train,

@@ -352,3 +352,66 @@ def evaluate(model, grid, ds, batch=32, bound=1e-2):
             "gain_vs_plain": t_plain / t_sur, "fallback_fraction": n_fb / n,
             "true_rel_l2_median": float(np.median(e)), "true_rel_l2_min": float(e.min()),
             "fields_within_bound": int(np.sum(e <= bound)), "bound": bound}
+
+
+def time_conv_layer(batch=8, edge=64, dilation=2, reps=5, seed=0):
+    """CUDA-event time of one 32 -> 32 channel tensor-core convolution layer on a batch of
+    edge^3 volumes of random bf16 activations: the forward (bias + LeakyReLU) and the weight +
+    bias gradient, each averaged over `reps` calls after one warm-up call. A call does
+    2 * voxels * 32 * 32 * 27 flops."""
+    lib = _native.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vox = edge ** 3
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.randn(batch * vox * 32, device=dev, generator=g).to(torch.bfloat16)
+    y = torch.empty_like(x)
+    w = torch.randn(32 * 32 * 27, device=dev, generator=g) / math.sqrt(27 * 32)
+    bias = torch.zeros(32, device=dev)
+    packed = torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device=dev)
+    dw = torch.zeros(32 * 32 * 27, device=dev)
+    db = torch.zeros(32, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    check(lib.rt_conv3d_pack_weights(_p(w), 32, 32, 0, _p(packed), st))
+
+    def fwd():
+        check(lib.rt_conv3d_forward(_p(x), batch, edge, edge, edge, 32, _p(packed), _p(bias), 32, dilation, 1, SLOPE,
+                                    None, _p(y), None, st))
+
+    def wgrad():
+        check(lib.rt_conv3d_weight_grad(_p(x), _p(y), batch, edge, edge, edge, 32, 32, dilation, _p(dw), _p(db), st))
+
+    flop = 2.0 * batch * vox * 32 * 32 * 27
+    out = {"batch": batch, "edge": edge, "dilation": dilation, "flop_per_call": flop}
+    for name, fn in (("forward", fwd), ("weight_grad", wgrad)):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name + "_ms"] = ms
+        out[name + "_tflops"] = flop / (ms * 1e-3) / 1e12
+    code = ctypes.c_int()
+    if lib.rt_device_status(ctypes.byref(code)) != 0:
+        raise RuntimeError(f"convolution kernel wait timed out (code {code.value})")
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="time one 32-channel tensor-core convolution layer")
+    ap.add_argument("--time-conv", action="store_true", required=True)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--edge", type=int, default=64)
+    ap.add_argument("--dilation", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=5)
+    a = ap.parse_args()
+    from . import build as _build
+    _build.build()
+    print(json.dumps(time_conv_layer(a.batch, a.edge, a.dilation, a.reps)))
