@@ -59,19 +59,48 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(src_hash):
-    """DRAM bytes per launch of the march kernel from the committed ncu summary, or None when
-    the kernel source changed since it was captured."""
+def profiled_counter(src_hash, key="dram_bytes_per_launch"):
+    """A per-launch counter of the march kernel (DRAM bytes, L2 red sectors) from the committed
+    ncu summary, or None when the kernel source changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "march_fwd_turbulent128.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_tr = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not m_hash or not m_tr or m_hash.group(1) != src_hash:
         return None
     return float(m_tr.group(1))
+
+
+def l2_roofline(plan, U, kms, src_hash):
+    """The march kernel against L2 peaks measured on this GPU by the library's microbenchmarks
+    (stencil kinds: 8 corners of a random cell of a 128^3 cell-major grid, the march's access
+    pattern). Algorithmic operations per (ray, source, bin group) substep: 8 deposits and 9
+    gathers of W-float vectors; merging in registers issues fewer deposits, so the algorithmic
+    fraction can exceed 1. `issued` uses the L2 red sectors ncu counted per launch."""
+    from paper_2511_09389_gb300 import peaks
+    pk = peaks.measure(edge=128, vecs=(4, 1))
+    W = int(plan["width"])
+    vec = 4 if W == 4 else 1
+    t = kms * 1e-3
+    lane_steps = U / W
+    reds, gathers = 8 * lane_steps, 9 * lane_steps
+    red_peak = pk[f"red_stencil_v{vec}"]["ops_per_s"]
+    gather_peak = pk[f"gather_stencil_v{vec}"]["ops_per_s"]
+    issued = profiled_counter(src_hash, "l2_red_sectors_per_launch")
+    return {
+        "bound": "l2_red", "unit": "ops/s", "vector_bytes": 4 * vec,
+        "red": {"algorithmic": reds / t, "peak": red_peak, "frac": reds / t / red_peak,
+                "issued": None if issued is None else issued / t,
+                "issued_frac": None if issued is None else issued / t / red_peak},
+        "gather": {"algorithmic": gathers / t, "peak": gather_peak, "frac": gathers / t / gather_peak},
+        "peaks": {k: v["ops_per_s"] for k, v in pk.items() if isinstance(v, dict)},
+        "peak_kind": "measured here (rt_microbench)",
+        "basis": f"8 deposits and 9 gathers of {W}-float vectors per (ray, source, bin group) substep x "
+                 f"{int(lane_steps)} substeps per launch / march-kernel CUDA-event time",
+    }
 
 
 class ClockSampler:
@@ -374,7 +403,8 @@ def native_arm(args):
 
     peak, peak_kind, _ = load_peaks()
     achieved = ALGO_BYTES_PER_UPDATE * U / (kms * 1e-3) / 1e9
-    traffic = profiled_traffic(kernel_source_hash())
+    src_hash = kernel_source_hash()
+    traffic = profiled_counter(src_hash)
     h2d = p.j.nbytes + p.kappa.nbytes + p.sources.nbytes
     d2h = p.j.nbytes
 
@@ -395,6 +425,8 @@ def native_arm(args):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
     }
+
+    line["l2_roofline"] = l2_roofline(g.last_plan(), U, kms, src_hash)
 
     # the same step with the deterministic (64-bit fixed-point) accumulation
     gd = Grid(p.shape, 8, deterministic=True)

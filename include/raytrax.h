@@ -284,6 +284,25 @@ rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, lo
    weight gradient, 10: shared memory not 1024-byte aligned). */
 rt_status rt_device_status(int* code);
 
+/* ---- Microbenchmarks (no counterpart in the paper) ----------------------------------
+   Peaks of the memory operations the march is built from, measured on the current device so
+   the march's roofline fractions have a denominator from the same GPU. One launch of
+   8 x (SM count) blocks of 256 threads, each thread doing `iters` operations on the device
+   buffer `buf` (buf_bytes bytes, contents overwritten; keep it L2-resident, e.g. 32 MiB):
+     kind 0: red.global.add.f32 (vec 1) / .v4.f32 (vec 4) into uniformly random vectors;
+     kind 1: the same, each warp on 32 consecutive vectors at a random position;
+     kind 2: the same into the 8 corners of a random cell of an edge^3 grid of vectors
+             (cell-major, the march's packed accumulator layout; 8 operations per iteration);
+     kind 3: read-only loads of uniformly random vectors;
+     kind 4: read-only loads of the 8 corners of a random cell of an edge^3 grid.
+   Addresses come from a per-thread linear congruential generator and are in bounds by
+   construction. *ms = device time of the launch (CUDA events on the legacy default stream; the
+   call synchronises), *ops = vector operations performed. Errors: RT_ERR_INVALID_ARG for a bad
+   kind / vec / iters (1 .. 2^20), a NULL pointer, a buffer of fewer than 32 vectors (kinds 0,
+   1, 3) or one that does not hold edge^3 vectors (kinds 2, 4; 2 <= edge <= 2048). */
+rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int edge, int iters, float* ms,
+                        double* ops);
+
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
    group), threads per block, gather mode (0: reuse, 1: ahead, 2: both), lanes per ray, and the march
    time the autotuner measured for it in ms (-1 when rt_options.autotune is 0). Any pointer

@@ -23,7 +23,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
            "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_c32_channel_mean",
-           "rt_adam_step")
+           "rt_adam_step", "rt_microbench")
 
 
 class RTError(RuntimeError):
@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH):
         lib.rt_log_field_loss.restype = i
         lib.rt_field_error.argtypes = [vp, vp, i, ll, vp, f, f, f, vp, vp]
         lib.rt_field_error.restype = i
+        lib.rt_microbench.argtypes = [i, i, vp, ll, i, i, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_double)]
+        lib.rt_microbench.restype = i
         lib.rt_c32_channel_mean.argtypes = [vp, i, i, ll, vp, vp]
         lib.rt_c32_channel_mean.restype = i
         lib.rt_adam_step.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, i, vp]

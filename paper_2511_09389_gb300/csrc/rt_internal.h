@@ -163,4 +163,8 @@ cudaError_t launch_from_c32(const void* src, int B, int C, long long vox, float*
 // channel; transpose = 1 (data gradient): flipped taps, n = input, k = output channel.
 cudaError_t launch_pack_weights(const float* w, int c_in, int c_out, int transpose, void* packed, cudaStream_t st);
 
+// Microbenchmarks of L2 reductions and gathers (microbench.cu): kind 0-4, vec 1 or 4 floats.
+cudaError_t launch_microbench(int kind, int vec, float* buf, long long nvec, int edge, int iters, int grid,
+                              int block, cudaStream_t st);
+
 }  // namespace rt
