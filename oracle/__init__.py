@@ -22,6 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rt_oracle.c")
 _CONV_SRC = os.path.join(_HERE, "conv_oracle.c")
+_THREADS_SRC = os.path.join(_HERE, "rt_oracle_threads.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -33,12 +34,12 @@ _lp = ctypes.POINTER(ctypes.c_long)
 
 def build(force: bool = False) -> str:
     """Compile the oracle C sources into ``oracle/liboracle.so`` (no fast-math, no FMA)."""
-    srcs = [_SRC] + ([_CONV_SRC] if os.path.exists(_CONV_SRC) else [])
+    srcs = [_SRC, _THREADS_SRC] + ([_CONV_SRC] if os.path.exists(_CONV_SRC) else [])
     newest = max(os.path.getmtime(s) for s in srcs)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["cc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["cc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
            "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -61,6 +62,8 @@ def _load():
         common = [_dp, _dp, i, i, i, i, _dp, i, i, d, i, i, i, i, i]
         lib.oracle_advance.argtypes = common + [_dp]
         lib.oracle_advance.restype = i
+        lib.oracle_advance_threads.argtypes = common + [i, i, _dp]
+        lib.oracle_advance_threads.restype = i
         lib.oracle_backward.argtypes = common + [_dp, _dp, _dp]
         lib.oracle_backward.restype = i
         lib.oracle_trace_ray.argtypes = [_dp, _dp, i, i, i, _dp, i, i, d, i, i, i, _lp, _lp, _dp]
@@ -118,22 +121,27 @@ def _grid_args(j, kappa):
 
 
 def advance(j, kappa, source_pos, num_rays: int, step_size: float, num_steps: int,
-            geom_mode: int = 0, kappa_mode: int = 0, ray_range=None) -> np.ndarray:
+            geom_mode: int = 0, kappa_mode: int = 0, ray_range=None, threads: int = 1,
+            ray_block: int = 256) -> np.ndarray:
     """Field after one dt: (4 pi / N_Omega) sum_src sum_rays sum_k W(x_k) I_{k+1} (Sec. 2, Eq. 2).
 
     j, kappa: [n_freq, n0, n1, n2] (or 3-D for one bin); source_pos: [n_src, 3] in grid
     coordinates; num_steps = N_s. geom_mode 0 reproduces FP32 geometry (reading R6), 1 is
-    pure FP64. ray_range=(begin, end) traces a shard of the lattice. Returns FP64
-    [n_freq, n0, n1, n2].
+    pure FP64. ray_range=(begin, end) traces a shard of the lattice. threads > 1 splits the
+    (source, block of ray_block rays) items over host threads, each summing into its own
+    partial field (added in thread order). Returns FP64 [n_freq, n0, n1, n2].
     """
     j, kappa = _grid_args(j, kappa)
     nf, n0, n1, n2 = j.shape
     src = _f64(source_pos).reshape(-1, 3)
     rb, re = (0, num_rays) if ray_range is None else ray_range
     out = np.zeros_like(j)
-    rc = _load().oracle_advance(_ptr(j), _ptr(kappa), nf, n0, n1, n2, _ptr(src), src.shape[0],
-                                int(num_rays), float(step_size), int(num_steps), int(geom_mode),
-                                int(kappa_mode), int(rb), int(re), _ptr(out))
+    args = (_ptr(j), _ptr(kappa), nf, n0, n1, n2, _ptr(src), src.shape[0], int(num_rays), float(step_size),
+            int(num_steps), int(geom_mode), int(kappa_mode), int(rb), int(re))
+    if threads > 1:
+        rc = _load().oracle_advance_threads(*args, int(threads), int(ray_block), _ptr(out))
+    else:
+        rc = _load().oracle_advance(*args, _ptr(out))
     if rc != 0:
         raise ValueError("oracle_advance: invalid arguments")
     return out
