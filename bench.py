@@ -243,6 +243,43 @@ def fwd_adjoint(args, dev, flush, stream):
             "adjoint_updates_per_s": U / (tb * 1e-3)}
 
 
+def paper_workload(args, dev, flush, stream):
+    """The paper's timing run on a synthetic medium (128^3 lognormal kappa, 2097 sources at the
+    0.1 % highest-kappa cells, N_Omega 4096, ds 0.5, one bin; c dt 128 assumed, N_s 256): one
+    rt_advance per step, autotuned during the warm-up, L2 flushed before each timed step. The
+    paper's 4.49 s on one H200 is quoted beside it as context (another machine, N_s unstated)."""
+    import statistics as st
+    import torch
+    from paper_2511_09389_gb300 import inputs
+    from paper_2511_09389_gb300.api import Grid, num_substeps
+    p = inputs.paper_timing()
+    ns = num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    U = len(p.sources) * p.num_rays * ns * p.n_freq
+    g = Grid(p.shape, 1, profile=True, autotune=True)
+    j, k, s = (torch.from_numpy(a).to(dev) for a in (p.j, p.kappa, p.sources))
+    out = torch.empty_like(j)
+    steps, kern = [], []
+    for i in range(3 + max(3, min(args.steps, 10))):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 3:
+            steps.append(e0.elapsed_time(e1))
+            kern.append(g.kernel_ms())
+    plan = g.last_plan()
+    g.close()
+    t = st.mean(steps)
+    return {"value": U / (t * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": t,
+            "kernel_ms": st.mean(kern), "launch_plan": plan,
+            "workload": f"128^3 lognormal kappa, {len(p.sources)} sources at the 0.1 % highest-kappa cells, "
+                        f"N_Omega {p.num_rays}, ds {p.step_size}, N_s {ns} (c dt 128 assumed), 1 bin",
+            "paper": {"seconds": 4.49, "hardware": "1x H200 (JAX)", "speedup_context": 4.49 / (t * 1e-3),
+                      "note": "context only: another machine; the paper does not state N_s or bins"}}
+
+
 def batched(args, dev, stream):
     """64 independent instances (edges from {32,48,64,96,128,160}, lognormal kappa with sigma_g in
     [0.5, 1.5], 1-64 sources, N_Omega from {768, 3072, 12288}, ds 0.5, c dt = edge, 1-8 bins):
@@ -467,6 +504,7 @@ def native_arm(args):
     line["deterministic"] = {"value": U / (statistics.mean(tdet) * 1e-3), "unit": UNIT,
                              "ms_per_step": statistics.mean(tdet), "note": "64-bit fixed-point deposits, bitwise reproducible"}
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
+    line["paper_workload"] = paper_workload(args, dev, flush, stream)
     if not args.no_batch:
         line["batched"] = batched(args, dev, stream)
     if args.surrogate_train > 0:

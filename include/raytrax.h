@@ -72,6 +72,9 @@ typedef struct {
     int plan_prefetch;  /*   of 32), gathers (1: reused while the corner set is unchanged, 2:   */
     int plan_lanes;     /*   one step ahead, 3: both), lanes per ray (1, or 2 / 4 adjacent      */
                         /*   lanes sharing one ray of a 4-bin group, with gathers mode 1)      */
+    int plan_tile;      /*   and source deposit tiles (1: off, 2: on): each block sums the      */
+                        /*   deposits of its rays in the 8^3 cells around its source in shared  */
+                        /*   memory and adds them to the field once (not in deterministic mode) */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
@@ -304,12 +307,12 @@ rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int e
                         double* ops);
 
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
-   group), threads per block, gather mode (0: reuse, 1: ahead, 2: both), lanes per ray, and the march
-   time the autotuner measured for it in ms (-1 when rt_options.autotune is 0). Any pointer
-   may be NULL.
+   group), threads per block, gather mode (0: reuse, 1: ahead, 2: both), lanes per ray, source
+   deposit tiles (0 / 1), and the march time the autotuner measured for it in ms (-1 when
+   rt_options.autotune is 0). Any pointer may be NULL.
    With autotune = 1, the first call of each shape class (n_freq, num_sources, rays, N_s)
    times every candidate plan on its own inputs before running; it synchronises the stream. */
-rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray,
+rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray, int* tile,
                        float* tuned_ms);
 
 /* Text of the last autotuning pass on this handle: one line per candidate plan with its best

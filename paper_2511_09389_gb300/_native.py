@@ -38,7 +38,7 @@ class rt_options(ctypes.Structure):
     _fields_ = [("deterministic", ctypes.c_int), ("kappa_mode", ctypes.c_int), ("ns_cap", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
                 ("profile", ctypes.c_int), ("plan_width", ctypes.c_int), ("plan_block", ctypes.c_int),
-                ("plan_prefetch", ctypes.c_int), ("plan_lanes", ctypes.c_int)]
+                ("plan_prefetch", ctypes.c_int), ("plan_lanes", ctypes.c_int), ("plan_tile", ctypes.c_int)]
 
 
 class rt_instance(ctypes.Structure):
@@ -90,7 +90,7 @@ def load(path: str = LIB_PATH):
         lib.rt_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.rt_kernel_ms.restype = i
         ip = ctypes.POINTER(ctypes.c_int)
-        lib.rt_last_plan.argtypes = [vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_float)]
+        lib.rt_last_plan.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_float)]
         lib.rt_last_plan.restype = i
         lib.rt_tuning_report.argtypes = [vp, ctypes.c_char_p, i]
         lib.rt_tuning_report.restype = i

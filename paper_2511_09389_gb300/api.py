@@ -53,9 +53,10 @@ def direction_table(num_rays: int) -> np.ndarray:
 class Grid:
     """A library handle for one grid shape (owns its scratch on one device).
 
-    plan=(bins_per_group, block, gathers[, lanes_per_ray]) pins the forward launch plan, gathers
-    0 = reused, 1 = one step ahead, 2 = both (ignored
-    when autotune=True, which times the candidates on the first call of each shape class)."""
+    plan=(bins_per_group, block, gathers[, lanes_per_ray[, tile]]) pins the forward launch plan,
+    gathers 0 = reused, 1 = one step ahead, 2 = both, tile 0 / 1 = source deposit tiles off / on
+    (the library's default when not given; ignored when autotune=True, which times the
+    candidates on the first call of each shape class)."""
 
     def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
                  ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
@@ -67,10 +68,11 @@ class Grid:
         self.max_freq = int(max_freq)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
-        pw, pb, pp, pl = (0, 0, 0, 0) if plan is None else (int(plan[0]), int(plan[1]), int(plan[2]) + 1,
-                                                             int(plan[3]) if len(plan) > 3 else 1)
+        pw, pb, pp, pl, pt = (0, 0, 0, 0, 0) if plan is None else (
+            int(plan[0]), int(plan[1]), int(plan[2]) + 1, int(plan[3]) if len(plan) > 3 else 1,
+            int(plan[4]) + 1 if len(plan) > 4 else 0)
         opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
-                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl)
+                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl, pt)
         self.options = opt
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -195,11 +197,13 @@ class Grid:
         return float(ms.value)
 
     def last_plan(self) -> dict:
-        """Launch plan of the last forward call (width, block, prefetch, tuned_ms)."""
-        w, b, p, n, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        """Launch plan of the last forward call (width, block, prefetch, lanes, tile, tuned_ms)."""
+        w, b, p, n, tl, t = (ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(),
+                             ctypes.c_float())
         check(self._lib.rt_last_plan(self._h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(p), ctypes.byref(n),
-                                     ctypes.byref(t)))
-        return {"width": w.value, "block": b.value, "prefetch": p.value, "lanes_per_ray": n.value, "tuned_ms": t.value}
+                                     ctypes.byref(tl), ctypes.byref(t)))
+        return {"width": w.value, "block": b.value, "prefetch": p.value, "lanes_per_ray": n.value, "tile": tl.value,
+                "tuned_ms": t.value}
 
     def tuning_report(self) -> str:
         """Candidates and times of the last autotuning pass ("" if none)."""

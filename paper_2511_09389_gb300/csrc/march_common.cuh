@@ -18,6 +18,7 @@ constexpr float kFourPi = 12.566370614359172f;
 struct Axis {
     int lo, hi;   // clamped floor corner and clamped floor+1 corner
     float t;      // x - floor(x), not clamped
+    int f;        // floor(x), limited to [-1, n-1] (lo = max(f, 0), hi = min(f + 1, n - 1))
 };
 
 __device__ __forceinline__ Axis axis_sample(float x, int n) {
@@ -28,6 +29,7 @@ __device__ __forceinline__ Axis axis_sample(float x, int n) {
     const int fi = __float2int_rz(fminf(fmaxf(f, -1.0f), (float)(n - 1)));
     a.lo = max(fi, 0);
     a.hi = min(fi + 1, n - 1);
+    a.f = fi;
     return a;
 }
 
@@ -42,11 +44,24 @@ struct Sample {
     int cell[8];
     float w[8];
     int nn;
+    int tl;       // with a deposit tile: tile-local index of corner 0, or -1 (see below)
 };
 
+// Edge of the shared-memory deposit tile a block keeps around its source (cells per axis).
+constexpr int kTile = 8;
+
+// TILE: also locate the 8 corners in a kTile^3 tile with origin (o0, o1, o2) lying inside the
+// grid: s.tl = local index of corner 0 when floor(x) - o is in [0, kTile - 2] on every axis
+// (then no corner is clamped and corner c sits at s.tl + tile_offset(c)), else -1.
+template <bool TILE = false>
 __device__ __forceinline__ void make_sample(float x0, float x1, float x2, int n0, int n1, int n2,
-                                            int kappa_mode, Sample& s) {
+                                            int kappa_mode, Sample& s, int o0 = 0, int o1 = 0, int o2 = 0) {
     const Axis a0 = axis_sample(x0, n0), a1 = axis_sample(x1, n1), a2 = axis_sample(x2, n2);
+    if (TILE) {
+        const unsigned u0 = (unsigned)(a0.f - o0), u1 = (unsigned)(a1.f - o1), u2 = (unsigned)(a2.f - o2);
+        const unsigned lim = kTile - 2;
+        s.tl = (u0 <= lim && u1 <= lim && u2 <= lim) ? (int)((u0 * kTile + u1) * kTile + u2) : -1;
+    }
     const int r00 = (a0.lo * n1 + a1.lo) * n2, r01 = (a0.lo * n1 + a1.hi) * n2;
     const int r10 = (a0.hi * n1 + a1.lo) * n2, r11 = (a0.hi * n1 + a1.hi) * n2;
     s.cell[0] = r00 + a2.lo; s.cell[1] = r00 + a2.hi;
@@ -64,6 +79,10 @@ __device__ __forceinline__ void make_sample(float x0, float x1, float x2, int n0
     } else {
         s.nn = (nearest_round(x0, n0) * n1 + nearest_round(x1, n1)) * n2 + nearest_round(x2, n2);
     }
+}
+
+__device__ __forceinline__ constexpr int tile_offset(int c) {
+    return ((c >> 2) & 1) * kTile * kTile + ((c >> 1) & 1) * kTile + (c & 1);
 }
 
 // ---- W-wide bin vectors -----------------------------------------------------------------

@@ -8,20 +8,43 @@
 
 namespace rt {
 
-template <int W, int PF, int DET>
+// Tile origin along one axis: the kTile cells starting kTile/2 - 1 below the source's cell,
+// moved inside [0, n - kTile].
+__device__ __forceinline__ int tile_origin(float src, int n) {
+    const int f = (int)floorf(fminf(fmaxf(src, -4.0e6f), 4.0e6f));
+    return min(max(f - (kTile / 2 - 1), 0), n - kTile);
+}
+
+// TILE: every block (one source, one bin group) keeps the kTile^3 cells around its source in
+// shared memory; its lanes' deposits there are summed with shared-memory atomics and added to
+// the field once per block. The cells next to a source receive a deposit from every ray of it,
+// so this takes the most contended L2 atomics off the march and sums them in shorter chains.
+template <int W, int PF, int DET, bool TILE>
 __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
+    constexpr int TCELLS = kTile * kTile * kTile;
+    __shared__ float tile[TILE ? TCELLS * W : 1];
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
     const int rb = blockIdx.x % rblocks;
     const int sg = blockIdx.x / rblocks;
     const int s = sg % a.nsrc;
     const int g = sg / a.nsrc;
     const int r = rb * blockDim.x + threadIdx.x;
-    if (r >= a.ray_count) return;
     const long long ncell = (long long)a.n0 * a.n1 * a.n2;
+    float* og = a.acc + (size_t)g * ncell * W;
+    int to0 = 0, to1 = 0, to2 = 0;
+    // the launcher uses TILE only when every grid extent is at least kTile
+    if (TILE) {
+        to0 = tile_origin(a.src[3 * s + 0], a.n0);
+        to1 = tile_origin(a.src[3 * s + 1], a.n1);
+        to2 = tile_origin(a.src[3 * s + 2], a.n2);
+        for (int i = threadIdx.x; i < TCELLS * W; i += blockDim.x) tile[i] = 0.0f;
+        __syncthreads();
+    }
+    if (r < a.ray_count) {
     Lane L;
     L.jg = a.jp + (size_t)g * ncell * W;
     L.kg = a.kp + (size_t)g * ncell * W;
-    L.og = a.acc + (size_t)g * ncell * W;
+    L.og = og;
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
@@ -33,7 +56,27 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     L.ncell = ncell;
     L.nbins = min(W, a.n_freq - g * W);
     L.fix = a.fix;
-    march_lane<W, PF, DET>(L);
+    L.tile = TILE ? tile : nullptr;
+    L.to0 = to0; L.to1 = to1; L.to2 = to2;
+    march_lane<W, PF, DET, TILE>(L);
+    }
+    if (TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < TCELLS; i += blockDim.x) {
+            float v[W];
+            bool any = false;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                v[b] = tile[i * W + b];
+                any = any || v[b] != 0.0f;
+            }
+            if (any) {
+                const int u0 = i / (kTile * kTile), u1 = (i / kTile) % kTile, u2 = i % kTile;
+                const int cell = ((to0 + u0) * a.n1 + (to1 + u1)) * a.n2 + (to2 + u2);
+                red_vec<W>(og, cell, v);
+            }
+        }
+    }
 }
 
 // Split lanes over a 4-bin packed group: LPR lanes per (ray, source, group), adjacent in a warp.
@@ -61,6 +104,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_split(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
+    L.tile = nullptr;
     march_lane_split<WL, 4>(L, sub);
 }
 
@@ -89,24 +133,23 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (a.prefetch < 0 || a.prefetch > 2) return cudaErrorInvalidValue;
     if (a.acc64) {
-        switch (W) {   // deterministic mode: gather reuse (PF = 0) only
-            case 1: k_march_fwd<1, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 2: k_march_fwd<2, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd<4, 0, 1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        switch (W) {   // deterministic mode: gather reuse (PF = 0), every deposit quantised on its own
+            case 1: k_march_fwd<1, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 2: k_march_fwd<2, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd<4, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
     }
-    switch (W * 4 + a.prefetch) {
-        case 4: k_march_fwd<1, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 5: k_march_fwd<1, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 6: k_march_fwd<1, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 8: k_march_fwd<2, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 9: k_march_fwd<2, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 10: k_march_fwd<2, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 16: k_march_fwd<4, 0, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 17: k_march_fwd<4, 1, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        case 18: k_march_fwd<4, 2, 0><<<(unsigned)nblk, block, 0, st>>>(a); break;
+    const bool tile = a.tile && a.n0 >= kTile && a.n1 >= kTile && a.n2 >= kTile;
+    switch ((W * 4 + a.prefetch) * 2 + (tile ? 1 : 0)) {
+#define RT_FWD_CASE(W_, PF_)                                                                     \
+        case (W_ * 4 + PF_) * 2: k_march_fwd<W_, PF_, 0, false><<<(unsigned)nblk, block, 0, st>>>(a); break; \
+        case (W_ * 4 + PF_) * 2 + 1: k_march_fwd<W_, PF_, 0, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        RT_FWD_CASE(1, 0) RT_FWD_CASE(1, 1) RT_FWD_CASE(1, 2)
+        RT_FWD_CASE(2, 0) RT_FWD_CASE(2, 1) RT_FWD_CASE(2, 2)
+        RT_FWD_CASE(4, 0) RT_FWD_CASE(4, 1) RT_FWD_CASE(4, 2)
+#undef RT_FWD_CASE
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -47,6 +47,8 @@ struct Lane {
     float ds;
     float scale;              // factor of every deposit
     int kappa_mode;
+    float* tile;              // the block's shared-memory deposit tile ([kTile^3][W]) or NULL
+    int to0, to1, to2;        // its origin cell (a far-away sentinel when tile is NULL)
 };
 
 // A slice of WL bins out of a packed WP-wide cell vector (split lanes: WP / WL adjacent lanes
@@ -89,6 +91,24 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
                 red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * f));
     } else {
         red_vec<W>(L.og, cell, v);
+    }
+}
+
+// Send the merged deposits of one run (8 corners) to memory. Runs whose corners lie in the
+// block's tile (tl >= 0) go to shared memory: the rays of a block all start at its source, so
+// these are the most contended cells of the march; the block adds the tile to the field once.
+template <int W, int DET, bool TILE>
+__device__ __forceinline__ void flush_run(const Lane& L, const int* pc, const float (*pend)[W], int tl) {
+    if (TILE && tl >= 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float* t = L.tile + (tl + tile_offset(c)) * W;
+#pragma unroll
+            for (int b = 0; b < W; ++b) atomicAdd(t + b, pend[c][b]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
     }
 }
 
@@ -172,7 +192,7 @@ __device__ __forceinline__ void march_lane_split(const Lane& L, int sub) {
 // PF = 2: prefetch and reuse combined. The corner set of substep k+1 is computed one step
 // ahead; its gathers are issued (only if it differs from the current set, else the registers
 // are carried over) before the update of substep k, so their latency overlaps that update.
-template <int W, int DET>
+template <int W, int DET, bool TILE = false>
 __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
@@ -190,9 +210,10 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
 #pragma unroll
         for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
     }
+    int ptl = -1;
     Sample sm;
     Gathered<W> gd;
-    make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+    make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm, L.to0, L.to1, L.to2);
     gather<W>(jg, kg, sm, gd);
 #pragma unroll 1
     for (int k = 0; k < L.ns; ++k) {
@@ -200,7 +221,7 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
         y = __fadd_rn(y, dy);
         z = __fadd_rn(z, dz);
         Sample nx;
-        make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx);
+        make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx, L.to0, L.to1, L.to2);
         Gathered<W> ng = gd;
         if (k + 1 < L.ns) {
             if (nx.cell[0] != sm.cell[0] || nx.cell[7] != sm.cell[7]) {
@@ -223,9 +244,10 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
             dep[b] = I[b] * scale;
         }
         if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
+            if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
+            ptl = TILE ? sm.tl : -1;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                if (pc[c] >= 0) flush<W, DET>(L, pc[c], pend[c]);
                 pc[c] = sm.cell[c];
 #pragma unroll
                 for (int b = 0; b < W; ++b) pend[c][b] = sm.w[c] * dep[b];
@@ -240,15 +262,13 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
         sm = nx;
         gd = ng;
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-        if (pc[c] >= 0) flush<W, DET>(L, pc[c], pend[c]);
+    if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
 }
 
-template <int W, int PF, int DET = 0>
+template <int W, int PF, int DET = 0, bool TILE = false>
 __device__ __forceinline__ void march_lane(const Lane& L) {
     if (PF == 2) {
-        march_lane_ahead<W, DET>(L);
+        march_lane_ahead<W, DET, TILE>(L);
         return;
     }
     const float* __restrict__ jg = L.jg;
@@ -271,10 +291,11 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
         for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
     }
 
+    int ptl = -1;   // tile index of the pending run (TILE)
     Sample sm;
     Gathered<W> gd;
     int gnn = -1;   // kappa cell of the gathered values (PF = 0)
-    make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+    make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm, L.to0, L.to1, L.to2);
     if (PF) gather<W>(jg, kg, sm, gd);
 
 #pragma unroll 1
@@ -287,7 +308,7 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
         // same 8 corners as the previous substep: the registers already hold their j values
         const bool same_cells = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
         if (PF) {
-            make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx);
+            make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, nx, L.to0, L.to1, L.to2);
             if (k + 1 < L.ns) gather<W>(jg, kg, nx, ng);
         } else {
             if (!same_cells) {
@@ -314,10 +335,8 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
         }
         // the corner set is fixed by its lowest and highest corner
         if (!same_cells) {
-            if (pc[0] >= 0) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
-            }
+            if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
+            ptl = TILE ? sm.tl : -1;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 pc[c] = sm.cell[c];
@@ -335,13 +354,10 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
             sm = nx;
             gd = ng;
         } else {
-            make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
+            make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm, L.to0, L.to1, L.to2);
         }
     }
-    if (pc[0] >= 0) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
-    }
+    if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
     (void)og;
 }
 

@@ -122,7 +122,7 @@ struct DirTable {
 // Launch plan of the forward march: bin-group width, threads per block, gather prefetch, and
 // lanes per ray (2 or 4 adjacent lanes share the ray of a 4-bin group).
 struct Plan {
-    int W = 1, block = 64, prefetch = 1, lpr = 1;
+    int W = 1, block = 64, prefetch = 1, lpr = 1, tile = 1;
 };
 
 }  // namespace
@@ -307,6 +307,7 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
     m->block = plan.block;
     m->prefetch = plan.prefetch;
     m->lanes_per_ray = plan.lpr;
+    m->tile = plan.lpr == 1 ? plan.tile : 0;
     if (plan.W == 1) {
         float* acc = out;
         if (!acc) {
@@ -363,13 +364,16 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
     if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventCreate");
     for (int W : widths) {
         for (int b : blocks) {
-            for (int pf = 0; pf < (W == 4 ? 5 : 3); ++pf) {
+            for (int cand = 0; cand < (W == 4 ? 8 : 6); ++cand) {
                 if (st != RT_OK) break;
                 Plan p;
                 p.W = W; p.block = b;
-                // prefetch modes 0, 1, 2; W = 4 also tries split lanes (pf 3: 2 lanes, pf 4: 4 lanes)
-                p.prefetch = pf <= 2 ? pf : 0;
-                p.lpr = pf >= 3 ? (pf == 3 ? 2 : 4) : 1;
+                // gather modes 0, 1, 2 with and without source tiles; W = 4 also tries split lanes
+                // (cand 6: 2 lanes, cand 7: 4 lanes per ray)
+                const int pf = cand < 6 ? cand >> 1 : 0;
+                p.prefetch = pf;
+                p.tile = cand < 6 ? (cand & 1) : 0;
+                p.lpr = cand >= 6 ? (cand == 6 ? 2 : 4) : 1;
                 rt::MarchArgs m;
                 if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
                 float cand_ms = 3.0e38f;
@@ -386,9 +390,9 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
                     if (ms < best_ms) { best_ms = ms; bp = p; }
                 }
                 if (st == RT_OK) {
-                    char line[96];
-                    snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d %.4f ms\n", W, b, p.prefetch,
-                             p.lpr, cand_ms);
+                    char line[112];
+                    snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d %.4f ms\n", W, b,
+                             p.prefetch, p.lpr, p.tile, cand_ms);
                     g->tune_report += line;
                 }
             }
@@ -456,15 +460,18 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         return RT_OK;
     }
 
-    // default plan (measured on GB300): 32-thread blocks; gather prefetch only pays for one bin
+    // default plan (measured on GB300): 32-thread blocks; gather prefetch and source deposit
+    // tiles only pay for one bin per thread (a tiled 4-bin deposit is 32 shared-memory atomics)
     Plan plan;
     plan.W = pick_width(a.n_freq);
     plan.block = 32;
     plan.prefetch = plan.W == 1 ? 1 : 0;
     if (g->opt.plan_width) plan.W = g->opt.plan_width;
+    plan.tile = plan.W == 1 ? 1 : 0;
     if (g->opt.plan_block) plan.block = g->opt.plan_block;
     if (g->opt.plan_prefetch) plan.prefetch = g->opt.plan_prefetch - 1;
     if (g->opt.plan_lanes) plan.lpr = g->opt.plan_lanes;
+    if (g->opt.plan_tile) plan.tile = g->opt.plan_tile - 1;
     if (plan.lpr > 1 && (plan.W != 4 || plan.prefetch)) return fail(RT_ERR_INVALID_ARG, "plan_lanes > 1 needs 4 bins per group and no prefetch");
     g->last_plan_ms = -1.0f;
     if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
@@ -513,6 +520,7 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
     if (o.plan_prefetch < 0 || o.plan_prefetch > 3) return fail(RT_ERR_INVALID_ARG, "plan_prefetch must be 0 .. 3");
     if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2 && o.plan_lanes != 4)
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1, 2 or 4");
+    if (o.plan_tile < 0 || o.plan_tile > 2) return fail(RT_ERR_INVALID_ARG, "plan_tile must be 0, 1 or 2");
     rt_grid* g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ERR_OOM, "host allocation failed");
     g->n0 = n0; g->n1 = n1; g->n2 = n2; g->max_freq = max_freq;
@@ -624,12 +632,14 @@ rt_status rt_kernel_ms(rt_grid* g, float* ms) {
     return RT_OK;
 }
 
-rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, int* lanes_per_ray, float* tuned_ms) {
+rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, int* lanes_per_ray, int* tile,
+                       float* tuned_ms) {
     if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
     if (width) *width = g->last_plan.W;
     if (block) *block = g->last_plan.block;
     if (prefetch) *prefetch = g->last_plan.prefetch;
     if (lanes_per_ray) *lanes_per_ray = g->last_plan.lpr;
+    if (tile) *tile = g->last_plan.lpr == 1 ? g->last_plan.tile : 0;
     if (tuned_ms) *tuned_ms = g->last_plan_ms;
     return RT_OK;
 }

@@ -42,6 +42,7 @@ struct MarchArgs {
     int prefetch;           // 0: gathers reused while the corner set is unchanged; 1: the next
                             // substep's gathers issued before the current update; 2: both
     int lanes_per_ray;      // 1, or 2 / 4 adjacent lanes sharing a ray of a 4-bin group
+    int tile;               // 1: source deposit tiles in shared memory (FP32 mode, one lane per ray)
 };
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);

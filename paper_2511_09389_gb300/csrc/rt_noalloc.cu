@@ -155,6 +155,7 @@ extern "C" rt_status rt_advance_noalloc(const float* j_map, const float* kappa_m
     m.kappa_mode = 0;
     m.block = 32;
     m.prefetch = W == 1 ? 1 : 0;
+    m.tile = W == 1 ? 1 : 0;     // source deposit tiles: static shared memory, no allocation
     const float scale = (float)(4.0 * 3.14159265358979323846 / (double)num_rays);
     if (W == 1) {
         // one bin: no packing, the march deposits straight into the (cleared) output

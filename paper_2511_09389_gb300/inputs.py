@@ -106,6 +106,30 @@ def turbulent(n: int = 128, n_src: int = 16, num_rays: int = 3072, step_size: fl
                    extra={"seed": seed, "nu_ratios": tuple(nu_ratios)})
 
 
+def paper_timing(n: int = 128, fraction: float = 0.001, num_rays: int = 4096, step_size: float = 0.5,
+                 horizon: float = 128.0, blob_sigma: float = 1.5, seed: int = 5000) -> Problem:
+    """The paper's timing run (Sec. 3) with a synthetic medium: lognormal kappa on 128^3 (sigma_g
+    1, mean 0.05), sources at the `fraction` = 0.1 % cells of highest kappa (2097), each the
+    centre of a Gaussian j blob (sigma 1.5, amplitude log-uniform in [0.1, 10]), N_Omega 4096,
+    ds 0.5, one bin. The paper does not state its horizon; c dt = 128 (N_s 256) is assumed.
+    Sources are listed by decreasing kappa (ties by cell index)."""
+    kap = lognormal_field((n, n, n), 1.0, 0.05, seed)
+    n_src = int(round(fraction * n ** 3))
+    flat = kap.reshape(-1).astype(np.float64)
+    order = np.lexsort((np.arange(flat.size), -flat))[:n_src]
+    src = np.stack(np.unravel_index(order, (n, n, n)), axis=1).astype(np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    amps = 10.0 ** rng.uniform(-1.0, 1.0, size=n_src)
+    # j = sum_i A_i g(x - c_i0) g(y - c_i1) g(z - c_i2): a sum of separable terms, as contractions
+    ax = np.arange(n, dtype=np.float64)
+    g = [np.exp(-(ax[None, :] - src[:, a, None]) ** 2 / (2 * blob_sigma ** 2)) for a in range(3)]
+    j = np.empty((n, n, n))
+    for x in range(n):
+        j[x] = (g[1] * (amps * g[0][:, x])[:, None]).T @ g[2]
+    return Problem("paper_timing", j.astype(np.float32)[None], kap[None], src.astype(np.float32), num_rays,
+                   step_size, 1.0, horizon, extra={"seed": seed, "fraction": fraction})
+
+
 def inverse_problem(n: int = 64, n_blobs: int = 8, num_rays: int = 3072, step_size: float = 0.5,
                     horizon: float = 64.0, seed: int = 4000) -> Problem:
     """Differentiable inverse problem: lognormal kappa (sigma_g 1, mean 0.05); target j made of

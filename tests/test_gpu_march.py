@@ -219,11 +219,33 @@ def test_deterministic_mode_full_size(torch_cuda):
 
 
 @pytest.mark.parametrize("plan", [(4, 64, 0, 2), (4, 128, 0, 4), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
-                                  (1, 32, 0, 1)])
+                                  (1, 32, 0, 1), (4, 32, 0, 1, 1), (2, 128, 1, 1, 1), (1, 64, 1, 1, 1),
+                                  (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0)])
 def test_every_launch_plan_meets_parity(torch_cuda, plan):
-    """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray)
-    on a ragged multi-bin problem."""
+    """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray,
+    source deposit tiles) on a ragged multi-bin problem."""
     p = inputs.random_small(60, shape=(18, 14, 22), n_freq=6, n_src=3, num_rays=257, horizon=16.0)
     from paper_2511_09389_gb300.api import Grid
     g = Grid(p.shape, 8, plan=plan)
     assert_parity(run_gpu(torch_cuda, p, grid=g), run_oracle(p))
+
+
+@pytest.mark.parametrize("plan", [(1, 32, 1, 1, 1), (1, 128, 0, 1, 1), (4, 64, 0, 1, 1), (2, 32, 2, 1, 1)])
+def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
+    """Source deposit tiles: many sources packed into a few cells (the tiles overlap and take
+    most deposits), plus sources on and outside the faces and corners (the tile origin is moved
+    inside the grid; rays that start outside it never use it). Every bin against the oracle."""
+    from paper_2511_09389_gb300.api import Grid
+    rng = np.random.Generator(np.random.PCG64(77))
+    shape = (16, 12, 20)
+    nf = plan[0] + 1 if plan[0] > 1 else 1
+    j = rng.uniform(0.0, 1.0, size=(nf,) + shape).astype(np.float32)
+    kap = rng.uniform(0.0, 0.3, size=(nf,) + shape).astype(np.float32)
+    cluster = np.array([7.0, 5.0, 9.0]) + rng.uniform(-1.2, 1.2, size=(10, 3))
+    faces = np.array([[0.0, 0.0, 0.0], [15.0, 11.0, 19.0], [-2.0, 5.5, 9.0], [16.5, -0.7, 21.0], [3.0, 11.0, 0.25]])
+    src = np.concatenate([cluster, faces]).astype(np.float32)
+    p = inputs.Problem("tiles", j, kap, src, 300, 0.5, 1.0, 10.0)
+    g = Grid(p.shape, 8, plan=plan)
+    F = run_gpu(torch_cuda, p, grid=g)
+    assert g.last_plan()["tile"] == 1
+    assert_parity(F, run_oracle(p))
