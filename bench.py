@@ -504,7 +504,8 @@ def native_arm(args):
     line["deterministic"] = {"value": U / (statistics.mean(tdet) * 1e-3), "unit": UNIT,
                              "ms_per_step": statistics.mean(tdet), "note": "64-bit fixed-point deposits, bitwise reproducible"}
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
-    line["paper_workload"] = paper_workload(args, dev, flush, stream)
+    if not args.no_paper:
+        line["paper_workload"] = paper_workload(args, dev, flush, stream)
     if not args.no_batch:
         line["batched"] = batched(args, dev, stream)
     if args.surrogate_train > 0:
@@ -542,6 +543,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (faster)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched measurement")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's 2097-source timing workload")
     ap.add_argument("--surrogate-train", type=int, default=4096, help="surrogate training fields (0: skip)")
     ap.add_argument("--surrogate-heldout", type=int, default=512)
     ap.add_argument("--surrogate-epochs", type=int, default=3)
