@@ -19,8 +19,8 @@
  *     t = x - f (unclamped); a ray that leaves the box keeps marching and deposits on the
  *     nearest boundary voxels.
  *   - kappa cell: kappa_mode 0 = the clamped floor corner of x_k (default); kappa_mode 1 =
- *     clamped floor(x_k + 1/2). The paper says only "nearest-neighbour at the cell index
- *     used for the previous position".
+ *     clamped floor(x_k + 1/2). The paper fixes only a nearest-neighbour read at the cell of
+ *     the previous position, not which cell that is.
  *   - Lattice: z_i = 1 - (2i+1)/N, phi_i = i pi (3 - sqrt 5) mod 2 pi, n_i = (sqrt(1-z^2)
  *     cos phi, sqrt(1-z^2) sin phi, z), computed in FP64 and rounded once to FP32.
  *   - Geometry in IEEE FP32 without contraction: d = fl(n ds) once per ray,
@@ -62,7 +62,7 @@ typedef struct {
                            bitwise identical for every launch plan and deposit order.
                            rt_advance / rt_advance_rays only (no autotuning, no batch) */
     int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
-    int ns_cap;         /* 0: none; > 0: cap on the substep count (Sec. 2 "user cap") */
+    int ns_cap;         /* 0: none; > 0: cap on the substep count (the optional cap of Sec. 2) */
     int autotune;       /* 1: time the launch shapes once per shape class and keep the best */
     int ckpt_stride;    /* adjoint checkpoint stride K in substeps; 0: automatic */
     int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
@@ -118,14 +118,33 @@ rt_status rt_advance(rt_grid* grid, const float* j_map, const float* kappa_map,
                      float* out_field, int accumulate, void* cuda_stream);
 
 /* rt_advance restricted to the lattice directions ray_begin .. ray_end-1 (each still
-   weighted 4 pi / num_rays): the direction shard of Sec. 2 ("shard directions across
-   devices ... sum per shard before reducing across shards"). Shards that tile
+   weighted 4 pi / num_rays): the direction shard of Sec. 2 (each device marches a subset
+   of the directions; the partial fields are summed). Shards that tile
    [0, num_rays) sum to the rt_advance field. 0 <= ray_begin <= ray_end <= num_rays. */
 rt_status rt_advance_rays(rt_grid* grid, const float* j_map, const float* kappa_map,
                           const float* source_pos, int num_sources, int num_rays,
                           int ray_begin, int ray_end, float step_size, float radiation_velocity,
                           float time_step, int n_freq, float* out_field, int accumulate,
                           void* cuda_stream);
+
+/* Stateful advance: the march continued across calls, for time integration with a fixed dt
+   (Sec. 3: a fixed dt, advanced call after call; the light-travel horizon of Sec. 2 then grows
+   by c dt per call). Same arguments and field as rt_advance, except that each ray starts where this
+   handle's previous rt_advance_continue call left it -- at its position, with the intensity I
+   and optical depth tau it had -- marches N_s = ceil(c dt / ds) further substeps through THIS
+   call's j and kappa (which may change between calls), and deposits only those. The handle
+   keeps the state: positions [num_sources][num_rays][3] and I, tau [n_freq][num_sources]
+   [num_rays] in FP32 (20 bytes per lane and bin). The rays restart at their sources with
+   I = tau = 0 when restart != 0, on the first call, and whenever num_sources, num_rays, n_freq
+   or step_size differ from the previous call's (source positions must not change between
+   continued calls). For the same j and kappa, n consecutive calls add up to one call over the
+   summed substeps; the positions repeat the uninterrupted march's FP32 additions exactly.
+   RT_ERR_UNSUPPORTED in deterministic mode. Not stream-safe across handles sharing state: one
+   handle, one sequence of calls. */
+rt_status rt_advance_continue(rt_grid* grid, const float* j_map, const float* kappa_map,
+                              const float* source_pos, int num_sources, int num_rays, float step_size,
+                              float radiation_velocity, float time_step, int n_freq, float* out_field,
+                              int accumulate, int restart, void* cuda_stream);
 
 /* rt_advance with HOST buffers (same shapes): copies the inputs to handle-owned device
    scratch, runs the march on the given stream, copies the field back and synchronises

@@ -64,6 +64,8 @@ def _load():
         lib.oracle_advance.restype = i
         lib.oracle_advance_threads.argtypes = common + [i, i, _dp]
         lib.oracle_advance_threads.restype = i
+        lib.oracle_advance_state.argtypes = [_dp, _dp, i, i, i, i, _dp, i, i, d, i, i, i, i, _dp, _dp, _dp, _dp]
+        lib.oracle_advance_state.restype = i
         lib.oracle_backward.argtypes = common + [_dp, _dp, _dp]
         lib.oracle_backward.restype = i
         lib.oracle_trace_ray.argtypes = [_dp, _dp, i, i, i, _dp, i, i, d, i, i, i, _lp, _lp, _dp]
@@ -144,6 +146,37 @@ def advance(j, kappa, source_pos, num_rays: int, step_size: float, num_steps: in
         rc = _load().oracle_advance(*args, _ptr(out))
     if rc != 0:
         raise ValueError("oracle_advance: invalid arguments")
+    return out
+
+
+class MarchState:
+    """Per-ray state carried between stateful advances: positions [n_src, num_rays, 3] and
+    I, tau [n_freq, n_src, num_rays] (FP64)."""
+
+    def __init__(self, n_freq: int, n_src: int, num_rays: int):
+        self.pos = np.zeros((n_src, num_rays, 3))
+        self.I = np.zeros((n_freq, n_src, num_rays))
+        self.tau = np.zeros((n_freq, n_src, num_rays))
+
+
+def advance_state(j, kappa, source_pos, num_rays: int, step_size: float, num_steps: int, state: MarchState,
+                  restart: bool, geom_mode: int = 0, kappa_mode: int = 0) -> np.ndarray:
+    """One advance of the march continued across calls (Sec. 3: time integration with a fixed dt): rays start
+    from `state` (or, with restart, at their sources with I = tau = 0), march num_steps
+    substeps of Eq. 2 through this call's j and kappa, deposit them, and leave their new state
+    in `state`. Returns the call's field, FP64 [n_freq, n0, n1, n2]."""
+    j, kappa = _grid_args(j, kappa)
+    nf, n0, n1, n2 = j.shape
+    src = _f64(source_pos).reshape(-1, 3)
+    if state.pos.shape != (src.shape[0], num_rays, 3) or state.I.shape != (nf, src.shape[0], num_rays):
+        raise ValueError("advance_state: state shape does not match the call")
+    out = np.zeros_like(j)
+    rc = _load().oracle_advance_state(_ptr(j), _ptr(kappa), nf, n0, n1, n2, _ptr(src), src.shape[0],
+                                      int(num_rays), float(step_size), int(num_steps), int(geom_mode),
+                                      int(kappa_mode), int(bool(restart)), _ptr(state.pos), _ptr(state.I),
+                                      _ptr(state.tau), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_advance_state: invalid arguments")
     return out
 
 

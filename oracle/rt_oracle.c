@@ -10,7 +10,7 @@
  *         x_{k+1}   = x_k + n * ds
  *         tau_{k+1} = tau_k + kappa(x_k) ds
  *         I_{k+1}   = I_k exp(-kappa(x_k) ds) + j(x_k) exp(-tau_k) ds
- *   - N_s = ceil(c dt / ds) substeps, or a user cap (Sec. 2, text after Eq. 2; App. A).
+ *   - N_s = ceil(c dt / ds) substeps, or an optional cap (Sec. 2, text after Eq. 2; App. A).
  *   - N_Omega directions on a Fibonacci (golden-angle) lattice; per-ray deposits are summed and
  *     scaled by 4 pi / N_Omega (Sec. 2).
  *   - j read by trilinear interpolation, kappa by nearest neighbour at the cell index of the
@@ -317,6 +317,82 @@ int oracle_trace_ray(const double *j, const double *kappa, int n0, int n1, int n
             I = I * exp(-kk * dsr) + jk * exp(-tau) * dsr;
             tau += kk * dsr;
             I_out[k] = I;
+        }
+    }
+    free(dirs);
+    free(smp);
+    return 0;
+}
+
+/* ---- Stateful advance: the march continued across calls (time integration with a fixed dt, Sec. 3) ----
+ * Same march as oracle_advance, but each ray starts where the previous call left it: from the
+ * position pos, with the intensity I and optical depth tau it had, and after ns substeps its new
+ * position, I and tau are written back. With restart != 0 the input state is ignored and every
+ * ray starts at its source with I = tau = 0 (oracle_advance exactly). j and kappa may change
+ * between calls; each call deposits its own substeps. Consecutive calls therefore add up to one
+ * call over the summed substeps.
+ *   pos: [nsrc][num_rays][3] (in / out; with geom_mode 0 the positions are FP32 values)
+ *   I, tau: [nf][nsrc][num_rays] (in / out)
+ *   out: [nf][n0][n1][n2], ACCUMULATED.
+ * Returns 0, or -1 on invalid arguments / allocation failure. */
+int oracle_advance_state(const double *j, const double *kappa, int nf, int n0, int n1, int n2,
+                         const double *src, int nsrc, int num_rays, double ds, int ns,
+                         int geom_mode, int kappa_mode, int restart,
+                         double *pos, double *I_state, double *tau_state, double *out)
+{
+    if (check_args(nf, n0, n1, n2, nsrc, num_rays, ds, ns, 0, num_rays)) return -1;
+    if (!pos || !I_state || !tau_state) return -1;
+    const long ncell = (long)n0 * n1 * n2;
+    const long lanes = (long)nsrc * num_rays;
+    const double scale = 4.0 * ORACLE_PI / (double)num_rays;
+    const double dsr = geom_mode == 0 ? (double)(float)ds : ds;
+    double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)num_rays);
+    sample_t *smp = (sample_t *)malloc(sizeof(sample_t) * (size_t)(ns > 0 ? ns : 1));
+    if (!dirs || !smp) { free(dirs); free(smp); return -1; }
+    oracle_fibonacci_dirs(num_rays, dirs);
+
+    for (int s = 0; s < nsrc; ++s) {
+        for (int r = 0; r < num_rays; ++r) {
+            const long lane = (long)s * num_rays + r;
+            double *p = &pos[3 * lane];
+            if (restart)
+                for (int a = 0; a < 3; ++a) p[a] = src[3 * s + a];
+            ray_samples(p, &dirs[3 * r], ds, ns, geom_mode, kappa_mode, n0, n1, n2, smp);
+            for (int b = 0; b < nf; ++b) {
+                const double *jb = j + (long)b * ncell;
+                const double *kb = kappa + (long)b * ncell;
+                double *ob = out + (long)b * ncell;
+                double I = restart ? 0.0 : I_state[(long)b * lanes + lane];
+                double tau = restart ? 0.0 : tau_state[(long)b * lanes + lane];
+                for (int k = 0; k < ns; ++k) {
+                    const sample_t *q = &smp[k];
+                    double jk = 0.0;
+                    for (int c = 0; c < 8; ++c) jk += q->w[c] * jb[q->cell[c]];
+                    double kk = kb[q->nn];
+                    I = I * exp(-kk * dsr) + jk * exp(-tau) * dsr;   /* Eq. 2, I update   */
+                    tau = tau + kk * dsr;                             /* Eq. 2, tau update */
+                    for (int c = 0; c < 8; ++c) ob[q->cell[c]] += scale * q->w[c] * I;
+                }
+                I_state[(long)b * lanes + lane] = I;
+                tau_state[(long)b * lanes + lane] = tau;
+            }
+            /* the position after ns substeps, by the same additions ray_samples makes */
+            if (geom_mode == 0) {
+                const float ds32 = (float)ds;
+                for (int a = 0; a < 3; ++a) {
+                    const float d = (float)dirs[3 * r + a] * ds32;
+                    float x = (float)p[a];
+                    for (int k = 0; k < ns; ++k) x = x + d;
+                    p[a] = (double)x;
+                }
+            } else {
+                for (int a = 0; a < 3; ++a) {
+                    const double d = dirs[3 * r + a] * ds;
+                    double x = p[a];
+                    for (int k = 0; k < ns; ++k) x = x + d;
+                    p[a] = x;
+                }
+            }
         }
     }
     free(dirs);

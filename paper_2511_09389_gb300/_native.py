@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ER
 
 # every symbol include/raytrax.h declares
 EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
-           "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_host", "rt_backward",
+           "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_continue", "rt_advance_host", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
         lib.rt_advance.restype = i
         lib.rt_advance_rays.argtypes = [vp, fp, fp, fp, i, i, i, i, f, f, f, i, fp, i, vp]
         lib.rt_advance_rays.restype = i
+        lib.rt_advance_continue.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, i, i, vp]
+        lib.rt_advance_continue.restype = i
         lib.rt_advance_host.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, vp]
         lib.rt_advance_host.restype = i
         lib.rt_backward.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, vp]

@@ -139,6 +139,29 @@ class Grid:
         check(st)
         return out
 
+    def advance_continue(self, j, kappa, sources, num_rays: int, step_size: float,
+                         radiation_velocity: float = 1.0, time_step: float = 1.0, *, out=None,
+                         accumulate: bool = False, restart: bool = False, stream=None) -> torch.Tensor:
+        """rt_advance_continue: one more dt of a march that continues across calls (each ray resumes
+        where the previous call on this handle left it; restart=True, or a change of sources /
+        rays / bins / step size, starts the rays at their sources again)."""
+        j, kappa, src = self._inputs(j, kappa, sources)
+        nf = j.shape[0]
+        if out is None:
+            out = torch.empty_like(j)
+            accumulate = False
+        elif out.shape != j.shape or out.dtype != torch.float32 or not out.is_contiguous() \
+                or out.device != self.device:
+            raise ValueError("out must be a contiguous float32 tensor shaped like j on the handle's device")
+        sp = _stream_ptr(stream, self.device)
+        with torch.cuda.device(self.device):
+            st = self._lib.rt_advance_continue(self._h, j.data_ptr(), kappa.data_ptr(), src.data_ptr(), src.shape[0],
+                                               int(num_rays), float(step_size), float(radiation_velocity),
+                                               float(time_step), nf, out.data_ptr(), int(bool(accumulate)),
+                                               int(bool(restart)), sp)
+        check(st)
+        return out
+
     def advance_host(self, j: np.ndarray, kappa: np.ndarray, sources: np.ndarray, num_rays: int,
                      step_size: float, radiation_velocity: float = 1.0, time_step: float = 1.0, *,
                      out: np.ndarray | None = None, stream=None) -> np.ndarray:

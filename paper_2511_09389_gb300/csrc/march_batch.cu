@@ -43,7 +43,11 @@ __global__ void __launch_bounds__(256, 2) k_march_batch(const BatchInst* __restr
             L.ds = B.ds;
             L.scale = 1.0f;
             L.kappa_mode = B.kappa_mode;
-            march_lane<W, 0>(L);
+            RayState<W> rs;
+            rs.x = L.sx; rs.y = L.sy; rs.z = L.sz;
+#pragma unroll
+            for (int b = 0; b < W; ++b) { rs.I[b] = 0.0f; rs.tau[b] = 0.0f; }
+            march_lane<W, 0>(L, rs);
         }
         __syncwarp();
     }

@@ -58,7 +58,35 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     L.fix = a.fix;
     L.tile = TILE ? tile : nullptr;
     L.to0 = to0; L.to1 = to1; L.to2 = to2;
-    march_lane<W, PF, DET, TILE>(L);
+    // start at the source with I = tau = 0, or (stateful advance) where the previous call left
+    // the ray: per-(source, ray) position, per-(bin, source, ray) I and tau
+    RayState<W> rs;
+    rs.x = L.sx; rs.y = L.sy; rs.z = L.sz;
+#pragma unroll
+    for (int b = 0; b < W; ++b) { rs.I[b] = 0.0f; rs.tau[b] = 0.0f; }
+    const long long lanes = (long long)a.nsrc * a.ray_count;
+    const long long lane = (long long)s * a.ray_count + r;
+    if (a.st_I && a.st_read) {
+        rs.x = a.st_pos_in[3 * lane + 0]; rs.y = a.st_pos_in[3 * lane + 1]; rs.z = a.st_pos_in[3 * lane + 2];
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            if (b < L.nbins) {
+                rs.I[b] = a.st_I[(long long)(g * W + b) * lanes + lane];
+                rs.tau[b] = a.st_tau[(long long)(g * W + b) * lanes + lane];
+            }
+    }
+    march_lane<W, PF, DET, TILE>(L, rs);
+    if (a.st_I) {
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            if (b < L.nbins) {
+                a.st_I[(long long)(g * W + b) * lanes + lane] = rs.I[b];
+                a.st_tau[(long long)(g * W + b) * lanes + lane] = rs.tau[b];
+            }
+        if (g == 0) {   // every bin group of the ray reads the old position: written to the other buffer
+            a.st_pos_out[3 * lane + 0] = rs.x; a.st_pos_out[3 * lane + 1] = rs.y; a.st_pos_out[3 * lane + 2] = rs.z;
+        }
+    }
     }
     if (TILE) {
         __syncthreads();

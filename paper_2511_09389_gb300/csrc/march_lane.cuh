@@ -47,8 +47,17 @@ struct Lane {
     float ds;
     float scale;              // factor of every deposit
     int kappa_mode;
-    float* tile;              // the block's shared-memory deposit tile ([kTile^3][W]) or NULL
-    int to0, to1, to2;        // its origin cell (a far-away sentinel when tile is NULL)
+    float* tile = nullptr;    // the block's shared-memory deposit tile ([kTile^3][W]) or NULL
+    int to0 = 0, to1 = 0, to2 = 0;   // its origin cell
+};
+
+// The state a lane carries through its march, in and out: position, and I and tau of its bins.
+// A fresh lane starts at its source with I = tau = 0; a continued lane (stateful advance) with
+// the values its previous call left.
+template <int W>
+struct RayState {
+    float x, y, z;
+    float I[W], tau[W];
 };
 
 // A slice of WL bins out of a packed WP-wide cell vector (split lanes: WP / WL adjacent lanes
@@ -193,14 +202,14 @@ __device__ __forceinline__ void march_lane_split(const Lane& L, int sub) {
 // ahead; its gathers are issued (only if it differs from the current set, else the registers
 // are carried over) before the update of substep k, so their latency overlaps that update.
 template <int W, int DET, bool TILE = false>
-__device__ __forceinline__ void march_lane_ahead(const Lane& L) {
+__device__ __forceinline__ void march_lane_ahead(const Lane& L, RayState<W>& R) {
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
     const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
-    float x = L.sx, y = L.sy, z = L.sz;
+    float x = R.x, y = R.y, z = R.z;
     float I[W], tau[W];
 #pragma unroll
-    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    for (int b = 0; b < W; ++b) { I[b] = R.I[b]; tau[b] = R.tau[b]; }
     const float ds = L.ds, scale = L.scale;
     int pc[8];
     float pend[8][W];
@@ -263,23 +272,26 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L) {
         gd = ng;
     }
     if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
+    R.x = x; R.y = y; R.z = z;
+#pragma unroll
+    for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
 }
 
 template <int W, int PF, int DET = 0, bool TILE = false>
-__device__ __forceinline__ void march_lane(const Lane& L) {
+__device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
     if (PF == 2) {
-        march_lane_ahead<W, DET, TILE>(L);
+        march_lane_ahead<W, DET, TILE>(L, R);
         return;
     }
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
     float* __restrict__ og = L.og;
     const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
-    float x = L.sx, y = L.sy, z = L.sz;
+    float x = R.x, y = R.y, z = R.z;
 
     float I[W], tau[W];
 #pragma unroll
-    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    for (int b = 0; b < W; ++b) { I[b] = R.I[b]; tau[b] = R.tau[b]; }
     const float ds = L.ds, scale = L.scale;
     // pending deposit of the current run of substeps with an unchanged corner set
     int pc[8];
@@ -358,6 +370,9 @@ __device__ __forceinline__ void march_lane(const Lane& L) {
         }
     }
     if (pc[0] >= 0) flush_run<W, DET, TILE>(L, pc, pend, ptl);
+    R.x = x; R.y = y; R.z = z;
+#pragma unroll
+    for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
     (void)og;
 }
 

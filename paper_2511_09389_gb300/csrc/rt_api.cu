@@ -133,7 +133,7 @@ struct rt_grid {
     int device = 0;
     std::vector<DirTable> dirs;
     // scratch slots
-    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, NSLOT };
+    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -150,6 +150,14 @@ struct rt_grid {
     Plan last_plan;
     float last_plan_ms = -1.0f;
     std::string tune_report;   // candidates timed by the last autotuning pass
+    // state of the stateful advance (rt_advance_continue): which problem it belongs to, which of
+    // the two position buffers holds the current positions, substeps marched since the restart
+    struct ContinueState {
+        bool valid = false;
+        int nsrc = 0, rays = 0, n_freq = 0, parity = 0;
+        float ds = 0.0f;
+        long long steps = 0;
+    } cont;
 
     rt_status mark(int which, cudaStream_t st) {
         if (!opt.profile) return RT_OK;
@@ -253,6 +261,12 @@ struct Call {
     float* out;
     int accumulate;
     cudaStream_t st;
+    // stateful advance (rt_advance_continue); see MarchArgs
+    const float* st_pos_in = nullptr;
+    float* st_pos_out = nullptr;
+    float* st_I = nullptr;
+    float* st_tau = nullptr;
+    int st_read = 0;
 };
 
 rt_status validate(rt_grid* g, const Call& a, int* ns_out) {
@@ -475,10 +489,19 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (plan.lpr > 1 && (plan.W != 4 || plan.prefetch)) return fail(RT_ERR_INVALID_ARG, "plan_lanes > 1 needs 4 bins per group and no prefetch");
     g->last_plan_ms = -1.0f;
     if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
+    if (a.st_I && plan.lpr > 1) {   // the stateful march runs one lane per (ray, source, bin group)
+        plan.lpr = 1;
+        plan.prefetch = 0;
+    }
     g->last_plan = plan;
 
     rt::MarchArgs m;
     if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
+    m.st_pos_in = a.st_pos_in;
+    m.st_pos_out = a.st_pos_out;
+    m.st_I = a.st_I;
+    m.st_tau = a.st_tau;
+    m.st_read = a.st_read;
     if (plan.W > 1 || !a.accumulate)
         RT_CUDA(cudaMemsetAsync(m.acc, 0, plan.W == 1 ? field_bytes : acc_bytes(g, a, plan), a.st),
                 "cudaMemsetAsync(accumulator)");
@@ -558,6 +581,52 @@ rt_status rt_advance(rt_grid* grid, const float* j_map, const float* kappa_map, 
     Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size,
            radiation_velocity, time_step, n_freq, out_field, accumulate ? 1 : 0, (cudaStream_t)cuda_stream};
     return advance_impl(grid, a);
+}
+
+rt_status rt_advance_continue(rt_grid* g, const float* j_map, const float* kappa_map, const float* source_pos,
+                              int num_sources, int num_rays, float step_size, float radiation_velocity,
+                              float time_step, int n_freq, float* out_field, int accumulate, int restart,
+                              void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (g->opt.deterministic)
+        return fail(RT_ERR_UNSUPPORTED, "rt_advance_continue: not available in deterministic mode");
+    Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size,
+           radiation_velocity, time_step, n_freq, out_field, accumulate ? 1 : 0, (cudaStream_t)cuda_stream};
+    int ns = 0;
+    rt_status st = validate(g, a, &ns);
+    if (st != RT_OK) return st;
+    if ((st = check_device(g)) != RT_OK) return st;
+    auto& c = g->cont;
+    const bool fresh = restart || !c.valid || c.nsrc != num_sources || c.rays != num_rays || c.n_freq != n_freq ||
+                       c.ds != step_size;
+    const size_t lanes = (size_t)std::max(num_sources, 1) * (size_t)num_rays;
+    void *pos, *I, *tau;
+    if ((st = g->ensure(rt_grid::STPOS, 2 * 3 * sizeof(float) * lanes, &pos)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::STI, sizeof(float) * (size_t)n_freq * lanes, &I)) != RT_OK) return st;
+    if ((st = g->ensure(rt_grid::STTAU, sizeof(float) * (size_t)n_freq * lanes, &tau)) != RT_OK) return st;
+    if (fresh) {
+        c.valid = false;
+        c.parity = 0;
+        c.steps = 0;
+    }
+    float* p0 = (float*)pos + (size_t)c.parity * 3 * lanes;
+    float* p1 = (float*)pos + (size_t)(c.parity ^ 1) * 3 * lanes;
+    a.st_pos_in = p0;
+    a.st_pos_out = p1;
+    a.st_I = (float*)I;
+    a.st_tau = (float*)tau;
+    a.st_read = fresh ? 0 : 1;
+    if (ns == 0 || num_sources == 0)   // nothing marches: zero (or unchanged) field, state as it was
+        return advance_impl(g, a);
+    if ((st = advance_impl(g, a)) != RT_OK) {
+        c.valid = false;
+        return st;
+    }
+    c.valid = true;
+    c.nsrc = num_sources; c.rays = num_rays; c.n_freq = n_freq; c.ds = step_size;
+    c.parity ^= 1;
+    c.steps += ns;
+    return RT_OK;
 }
 
 rt_status rt_advance_rays(rt_grid* grid, const float* j_map, const float* kappa_map, const float* source_pos,

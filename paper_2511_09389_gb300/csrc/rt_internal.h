@@ -43,6 +43,14 @@ struct MarchArgs {
                             // substep's gathers issued before the current update; 2: both
     int lanes_per_ray;      // 1, or 2 / 4 adjacent lanes sharing a ray of a 4-bin group
     int tile;               // 1: source deposit tiles in shared memory (FP32 mode, one lane per ray)
+    // stateful advance (NULL st_I: none): st_I / st_tau [n_freq][nsrc][ray_count], positions
+    // [nsrc][ray_count][3] read from st_pos_in when st_read and written to st_pos_out (a
+    // different buffer: every bin group of a ray reads the position)
+    const float* st_pos_in;
+    float* st_pos_out;
+    float* st_I;
+    float* st_tau;
+    int st_read;
 };
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);

@@ -1,6 +1,6 @@
 """The paper's timing workload generator (sources at the highest-kappa cells, Gaussian j
 blobs), checked on a small grid against its definition; the GPU march on the full-size
-workload against the oracle (a source subset) and against loop-and-sum over sources."""
+workload against the oracle (a source subset) and against the sum over sources of separate runs."""
 import os
 
 import numpy as np
@@ -40,7 +40,7 @@ def test_generator_small():
 @pytest.mark.gpu
 def test_full_size_march(torch_cuda):
     """All 2097 sources: the 64-bit fixed-point mode (exact integer sums of the deposits) against
-    the oracle at the parity bar, and loop-and-sum over sources; the FP32-atomic field against it.
+    the oracle at the parity bar, and the sum over sources of separate runs; the FP32-atomic field against it.
     The sources sit in a few clusters of high-kappa cells, so the cells around a cluster take
     ~1e5 FP32 atomic additions from the rays of its neighbouring sources (each block's deposit
     tile covers only its own source), every addition rounding to 2^-24 of the running sum: that
