@@ -64,6 +64,8 @@ def _load():
         lib.oracle_advance.restype = i
         lib.oracle_advance_threads.argtypes = common + [i, i, _dp]
         lib.oracle_advance_threads.restype = i
+        lib.oracle_source_gradient.argtypes = [_dp, _dp, i, i, i, i, _dp, i, i, d, i, i, i, _dp, _dp]
+        lib.oracle_source_gradient.restype = i
         lib.oracle_advance_state.argtypes = [_dp, _dp, i, i, i, i, _dp, i, i, d, i, i, i, i, _dp, _dp, _dp, _dp]
         lib.oracle_advance_state.restype = i
         lib.oracle_backward.argtypes = common + [_dp, _dp, _dp]
@@ -196,6 +198,24 @@ def backward(j, kappa, source_pos, num_rays: int, step_size: float, num_steps: i
     if rc != 0:
         raise ValueError("oracle_backward: invalid arguments")
     return dj, dk
+
+
+def source_gradient(j, kappa, source_pos, num_rays: int, step_size: float, num_steps: int, grad_out,
+                    geom_mode: int = 0, kappa_mode: int = 0) -> np.ndarray:
+    """dL/d(source positions) [n_src, 3] for G = dL/d(out): each ray's positions are the source
+    plus multiples of n ds, so the gradient sums dL/dx_k over the source's rays and substeps
+    (trilinear deposit and gather weights; the kappa cell is piecewise constant)."""
+    j, kappa = _grid_args(j, kappa)
+    nf, n0, n1, n2 = j.shape
+    G = _f64(grad_out).reshape(j.shape)
+    src = _f64(source_pos).reshape(-1, 3)
+    out = np.zeros_like(src)
+    rc = _load().oracle_source_gradient(_ptr(j), _ptr(kappa), nf, n0, n1, n2, _ptr(src), src.shape[0],
+                                        int(num_rays), float(step_size), int(num_steps), int(geom_mode),
+                                        int(kappa_mode), _ptr(G), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_source_gradient: invalid arguments")
+    return out
 
 
 def trace_ray(j, kappa, source, num_rays: int, ray: int, step_size: float, num_steps: int,

@@ -85,6 +85,7 @@ typedef struct {
     long cell[8];   /* flat indices of the 8 trilinear corners */
     double w[8];    /* their weights */
     long nn;        /* flat index of the kappa cell */
+    double t[3];    /* fractions x - floor(x) per axis (the weights are products of t, 1 - t) */
 } sample_t;
 
 static long clamp_index(double f, int n)
@@ -114,6 +115,7 @@ static void make_sample(const double f[3], const double t[3], const double fnn[3
     }
     long m0 = clamp_index(fnn[0], n0), m1 = clamp_index(fnn[1], n1), m2 = clamp_index(fnn[2], n2);
     s->nn = (m0 * n1 + m1) * n2 + m2;
+    for (int a = 0; a < 3; ++a) s->t[a] = t[a];
 }
 
 /* Geometry of one ray: positions x_0 .. x_{ns-1} turned into samples (R2, R3, R6). */
@@ -397,5 +399,83 @@ int oracle_advance_state(const double *j, const double *kappa, int nf, int n0, i
     }
     free(dirs);
     free(smp);
+    return 0;
+}
+
+/* ---- Gradient with respect to the source positions ------------------------------------
+ * Every position of a ray from source s is x_k = src_s + k n ds, so dL/dsrc_s is the sum over
+ * the source's rays and substeps of dL/dx_k with everything else held fixed. x_k enters twice,
+ * through trilinear weights: the deposit of I_{k+1} (scale w_c G[c] I_{k+1}) and the gather of
+ * j (dL/dj_k = lam_{k+1} E_k ds, as in oracle_backward). With V_c = scale I_{k+1} G[c] +
+ * lam_{k+1} E_k ds j[c] at the 8 corners,
+ *     dL/dx_k,a = sum_c (dw_c / dt_a) V_c,   dw_c/dt_a = +-prod_{a' != a} (t or 1 - t),
+ * + for the corners on the floor+1 side of axis a. The kappa cell is piecewise constant in x
+ * and contributes nothing; on a clamped axis both corners are the same cell, so its terms
+ * cancel. dsrc: [nsrc][3], ACCUMULATED. Returns 0, or -1 on invalid arguments. */
+int oracle_source_gradient(const double *j, const double *kappa, int nf, int n0, int n1, int n2,
+                           const double *src, int nsrc, int num_rays, double ds, int ns,
+                           int geom_mode, int kappa_mode, const double *G, double *dsrc)
+{
+    if (check_args(nf, n0, n1, n2, nsrc, num_rays, ds, ns, 0, num_rays)) return -1;
+    if (ns == 0 || nsrc == 0) return 0;
+    const long ncell = (long)n0 * n1 * n2;
+    const double scale = 4.0 * ORACLE_PI / (double)num_rays;
+    const double dsr = geom_mode == 0 ? (double)(float)ds : ds;
+    double *dirs = (double *)malloc(sizeof(double) * 3 * (size_t)num_rays);
+    sample_t *smp = (sample_t *)malloc(sizeof(sample_t) * (size_t)ns);
+    double *Ik = (double *)malloc(sizeof(double) * (size_t)(ns + 1));   /* I_0 .. I_ns */
+    double *Ek = (double *)malloc(sizeof(double) * (size_t)ns);
+    double *ak = (double *)malloc(sizeof(double) * (size_t)ns);
+    if (!dirs || !smp || !Ik || !Ek || !ak) {
+        free(dirs); free(smp); free(Ik); free(Ek); free(ak);
+        return -1;
+    }
+    oracle_fibonacci_dirs(num_rays, dirs);
+    for (int s = 0; s < nsrc; ++s) {
+        for (int r = 0; r < num_rays; ++r) {
+            ray_samples(&src[3 * s], &dirs[3 * r], ds, ns, geom_mode, kappa_mode, n0, n1, n2, smp);
+            for (int b = 0; b < nf; ++b) {
+                const double *jb = j + (long)b * ncell;
+                const double *kb = kappa + (long)b * ncell;
+                const double *Gb = G + (long)b * ncell;
+                double tau = 0.0;
+                Ik[0] = 0.0;
+                for (int k = 0; k < ns; ++k) {
+                    const sample_t *q = &smp[k];
+                    double jk = 0.0;
+                    for (int c = 0; c < 8; ++c) jk += q->w[c] * jb[q->cell[c]];
+                    double kk = kb[q->nn];
+                    ak[k] = exp(-kk * dsr);
+                    Ek[k] = exp(-tau);
+                    Ik[k + 1] = Ik[k] * ak[k] + jk * Ek[k] * dsr;      /* Eq. 2 */
+                    tau = tau + kk * dsr;
+                }
+                double lam_next = 0.0, a_next = 0.0;
+                for (int k = ns - 1; k >= 0; --k) {
+                    const sample_t *q = &smp[k];
+                    double g = 0.0;
+                    for (int c = 0; c < 8; ++c) g += q->w[c] * Gb[q->cell[c]];
+                    const double lam = scale * g + a_next * lam_next;   /* lam_{k+1} */
+                    for (int a = 0; a < 3; ++a) {
+                        double d = 0.0;
+                        for (int c = 0; c < 8; ++c) {
+                            double dw = 1.0;
+                            for (int e = 0; e < 3; ++e) {
+                                const int bit = (c >> (2 - e)) & 1;
+                                if (e == a) dw *= bit ? 1.0 : -1.0;
+                                else dw *= bit ? q->t[e] : 1.0 - q->t[e];
+                            }
+                            const double V = scale * Ik[k + 1] * Gb[q->cell[c]] + lam * Ek[k] * dsr * jb[q->cell[c]];
+                            d += dw * V;
+                        }
+                        dsrc[3 * s + a] += d;
+                    }
+                    lam_next = lam;
+                    a_next = ak[k];
+                }
+            }
+        }
+    }
+    free(dirs); free(smp); free(Ik); free(Ek); free(ak);
     return 0;
 }
