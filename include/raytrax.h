@@ -164,11 +164,28 @@ rt_status rt_advance_host(rt_grid* grid, const float* j_map, const float* kappa_
      dj[c_{k,c}] += lam_{k+1} E_k ds w_{k,c},
      dkappa[cell_k] += -ds (lam_{k+1} I_k a_k + mu_{k+1}).
    The forward state is recomputed from per-ray checkpoints every ckpt_stride substeps
-   (never by dividing out exp(-kappa ds)). Not differentiable in source_pos, ds, c, dt. */
+   (never by dividing out exp(-kappa ds)). For source positions see rt_backward_sources; not
+   differentiable in ds, c, dt. */
 rt_status rt_backward(rt_grid* grid, const float* grad_out, const float* j_map,
                       const float* kappa_map, const float* source_pos, int num_sources,
                       int num_rays, float step_size, float radiation_velocity, float time_step,
                       int n_freq, float* grad_j, float* grad_kappa, void* cuda_stream);
+
+/* rt_backward plus the gradient with respect to the source positions: grad_src (device
+   [num_sources][3], overwritten, or NULL). Sec. 4 notes that the march is built from smooth
+   interpolation and deposition primitives; source positions enter only through them. Every position of a ray is x_k = src + k n ds, so dL/dsrc sums dL/dx_k over the
+   source's rays and substeps with everything else fixed, where x_k enters the deposit of
+   I_{k+1} and the gather of j:
+     dL/dx_k = grad_x [ sum_c w_c(x) (s I_{k+1} G[c] + lam_{k+1} E_k ds j[c]) ] at x = x_k,
+   the corner values held fixed. The nearest-cell kappa read is piecewise constant and adds
+   nothing (the gradient is that of the almost-everywhere derivative); a clamped axis adds
+   nothing. Any of grad_j, grad_kappa, grad_src may be NULL; they must not alias each other or
+   an input. Summed with FP32 atomics (one per warp and component). */
+rt_status rt_backward_sources(rt_grid* grid, const float* grad_out, const float* j_map,
+                              const float* kappa_map, const float* source_pos, int num_sources,
+                              int num_rays, float step_size, float radiation_velocity, float time_step,
+                              int n_freq, float* grad_j, float* grad_kappa, float* grad_src,
+                              void* cuda_stream);
 
 /* Duration in ms of the march kernel(s) of the last rt_advance / rt_backward call on this
    handle (forward: the march kernel only, without packing or zeroing; backward: the adjoint

@@ -87,6 +87,8 @@ def load(path: str = LIB_PATH):
         lib.rt_advance_host.restype = i
         lib.rt_backward.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, vp]
         lib.rt_backward.restype = i
+        lib.rt_backward_sources.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, fp, vp]
+        lib.rt_backward_sources.restype = i
         lib.rt_trace_cells.argtypes = [vp, fp, i, i, f, i, llp, llp]
         lib.rt_trace_cells.restype = i
         lib.rt_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]

@@ -196,22 +196,30 @@ class Grid:
     # -- adjoint --------------------------------------------------------------------------
     def backward(self, grad_out, j, kappa, sources, num_rays: int, step_size: float,
                  radiation_velocity: float = 1.0, time_step: float = 1.0, *, need_j: bool = True,
-                 need_kappa: bool = True, stream=None):
-        """(dL/dj, dL/dkappa) for G = dL/d(out) of :meth:`advance` (either may be None if not needed)."""
+                 need_kappa: bool = True, need_sources: bool = False, stream=None):
+        """(dL/dj, dL/dkappa) for G = dL/d(out) of :meth:`advance` (either may be None if not
+        needed); with need_sources=True also dL/d(source positions) [n_src, 3] as a third entry."""
         j, kappa, src = self._inputs(j, kappa, sources)
         g = _grid_tensor(grad_out, "grad_out")
         if g.shape != j.shape or g.device != self.device:
             raise ValueError("grad_out must be shaped like j on the handle's device")
         gj = torch.empty_like(j) if need_j else None
         gk = torch.empty_like(j) if need_kappa else None
+        gs = torch.empty_like(src) if need_sources else None
+        ptr = lambda t: t.data_ptr() if t is not None else None
         with torch.cuda.device(self.device):
-            st = self._lib.rt_backward(self._h, g.data_ptr(), j.data_ptr(), kappa.data_ptr(), src.data_ptr(),
-                                       src.shape[0], int(num_rays), float(step_size), float(radiation_velocity),
-                                       float(time_step), j.shape[0], gj.data_ptr() if gj is not None else None,
-                                       gk.data_ptr() if gk is not None else None,
-                                       _stream_ptr(stream, self.device))
+            if need_sources:
+                st = self._lib.rt_backward_sources(self._h, g.data_ptr(), j.data_ptr(), kappa.data_ptr(),
+                                                   src.data_ptr(), src.shape[0], int(num_rays), float(step_size),
+                                                   float(radiation_velocity), float(time_step), j.shape[0], ptr(gj),
+                                                   ptr(gk), ptr(gs), _stream_ptr(stream, self.device))
+            else:
+                st = self._lib.rt_backward(self._h, g.data_ptr(), j.data_ptr(), kappa.data_ptr(), src.data_ptr(),
+                                           src.shape[0], int(num_rays), float(step_size), float(radiation_velocity),
+                                           float(time_step), j.shape[0], ptr(gj), ptr(gk),
+                                           _stream_ptr(stream, self.device))
         check(st)
-        return gj, gk
+        return (gj, gk, gs) if need_sources else (gj, gk)
 
     def kernel_ms(self) -> float:
         """Duration of the last call's march kernel (needs profile=True)."""

@@ -18,7 +18,15 @@
 
 namespace rt {
 
-template <int W, int K>
+// SG: also dL/d(source position). Each position of the ray is x_k = src + k n ds, so the source
+// gradient sums dL/dx_k over substeps with everything else fixed. x_k enters through trilinear
+// weights twice: the deposit of I_{k+1} and the gather of j (adjoint lam_{k+1} E_k ds). With the
+// corner values V_c = s I_{k+1} G[c] + lam_{k+1} E_k ds j[c] (summed over the lane's bins),
+// dL/dx_k is the gradient of the trilinear interpolant of V at x_k; the nearest-cell kappa is
+// piecewise constant and contributes nothing, and on a clamped axis the two corners are one
+// cell, so that component vanishes. The lanes of a block share the source: a warp reduction,
+// then one atomic per warp and axis.
+template <int W, int K, bool SG>
 __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
     const int rb = blockIdx.x % rblocks;
@@ -26,7 +34,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     const int s = sg % a.nsrc;
     const int g = sg / a.nsrc;
     const int r = rb * blockDim.x + threadIdx.x;
-    if (r >= a.ray_count) return;
+    float gsx = 0.0f, gsy = 0.0f, gsz = 0.0f;   // SG: this lane's dL/d(source position)
+    if (!SG && r >= a.ray_count) return;
+    if (r < a.ray_count) {
     const long long lanes = (long long)a.ray_count * a.nsrc * ((a.n_freq + W - 1) / W);
     const long long lane = ((long long)g * a.nsrc + s) * a.ray_count + r;
 
@@ -102,6 +112,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 
     Vec<W> gc[8];                     // G at the corners of pc (the pending dj corner set)
     int g0 = -1, g7 = -1;
+    Vec<W> jr[8];                     // SG: j at the corners of the current substep
+    int jr0 = -1, jr7 = -1;
     // per-thread segment record (local memory): x, I_k, E_k, a_k, e_k
     float rx[K], ry[K], rz[K], rI[K][W], rE[K][W], ra[K][W], re[K][W];
     const int nseg = (a.ns + K - 1) / K;
@@ -166,6 +178,36 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
                 lam_next[b] = lam;
                 a_next[b] = ra[q][b];
             }
+            if (SG) {
+                if (sm.cell[0] != jr0 || sm.cell[7] != jr7) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) jr[c] = ldg_vec<W>(jg, sm.cell[c]);
+                    jr0 = sm.cell[0]; jr7 = sm.cell[7];
+                }
+                float V[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float In = fmaf(rI[q][b], ra[q][b], re[q][b]);     // I_{k+1}
+                        v = fmaf(a.scale * In, gc[c].v[b], v);
+                        v = fmaf(ddj[b], jr[c].v[b], v);
+                    }
+                    V[c] = v;
+                }
+                const float t0 = __fsub_rn(rx[q], floorf(rx[q]));
+                const float t1 = __fsub_rn(ry[q], floorf(ry[q]));
+                const float t2 = __fsub_rn(rz[q], floorf(rz[q]));
+                const float u0 = 1.0f - t0, u1 = 1.0f - t1, u2 = 1.0f - t2;
+                // corner c = (bit axis 0, bit axis 1, bit axis 2) = (c >> 2, c >> 1, c) & 1
+                gsx += ((V[4] - V[0]) * u1 * u2 + (V[5] - V[1]) * u1 * t2 + (V[6] - V[2]) * t1 * u2 +
+                        (V[7] - V[3]) * t1 * t2);
+                gsy += ((V[2] - V[0]) * u0 * u2 + (V[3] - V[1]) * u0 * t2 + (V[6] - V[4]) * t0 * u2 +
+                        (V[7] - V[5]) * t0 * t2);
+                gsz += ((V[1] - V[0]) * u0 * u1 + (V[3] - V[2]) * u0 * t1 + (V[5] - V[4]) * t0 * u1 +
+                        (V[7] - V[6]) * t0 * t1);
+            }
             if (djg) {
                 if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
                     if (pc[0] >= 0) {
@@ -204,6 +246,21 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
         for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c]);
     }
     if (dkg && pnn >= 0) red_vec<W>(dkg, pnn, pdk);
+    }   // r < ray_count
+    if (SG) {
+        // every thread of the block reaches here (blocks are whole warps; lanes past the last ray
+        // contribute zero)
+        for (int o = 16; o > 0; o >>= 1) {
+            gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
+            gsy += __shfl_xor_sync(0xffffffffu, gsy, o);
+            gsz += __shfl_xor_sync(0xffffffffu, gsz, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(a.dsrc + 3 * s + 0, gsx);
+            atomicAdd(a.dsrc + 3 * s + 1, gsy);
+            atomicAdd(a.dsrc + 3 * s + 2, gsz);
+        }
+    }
 }
 
 size_t backward_ckpt_floats(const BackArgs& a, int W) {
@@ -221,17 +278,16 @@ cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st) {
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)nblk;
-    const int key = W * 100 + a.stride;
+    if (block % 32) return cudaErrorInvalidValue;
+    const int key = (W * 100 + a.stride) * 2 + (a.dsrc ? 1 : 0);
     switch (key) {
-        case 108: k_march_bwd<1, 8><<<grid, block, 0, st>>>(a); break;
-        case 116: k_march_bwd<1, 16><<<grid, block, 0, st>>>(a); break;
-        case 132: k_march_bwd<1, 32><<<grid, block, 0, st>>>(a); break;
-        case 208: k_march_bwd<2, 8><<<grid, block, 0, st>>>(a); break;
-        case 216: k_march_bwd<2, 16><<<grid, block, 0, st>>>(a); break;
-        case 232: k_march_bwd<2, 32><<<grid, block, 0, st>>>(a); break;
-        case 408: k_march_bwd<4, 8><<<grid, block, 0, st>>>(a); break;
-        case 416: k_march_bwd<4, 16><<<grid, block, 0, st>>>(a); break;
-        case 432: k_march_bwd<4, 32><<<grid, block, 0, st>>>(a); break;
+#define RT_BWD_CASE(W_, K_)                                                                        \
+        case (W_ * 100 + K_) * 2: k_march_bwd<W_, K_, false><<<grid, block, 0, st>>>(a); break;    \
+        case (W_ * 100 + K_) * 2 + 1: k_march_bwd<W_, K_, true><<<grid, block, 0, st>>>(a); break;
+        RT_BWD_CASE(1, 8) RT_BWD_CASE(1, 16) RT_BWD_CASE(1, 32)
+        RT_BWD_CASE(2, 8) RT_BWD_CASE(2, 16) RT_BWD_CASE(2, 32)
+        RT_BWD_CASE(4, 8) RT_BWD_CASE(4, 16) RT_BWD_CASE(4, 32)
+#undef RT_BWD_CASE
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -722,26 +722,35 @@ rt_status rt_tuning_report(rt_grid* g, char* buf, int len) {
     return RT_OK;
 }
 
-rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,
-                      const float* source_pos, int num_sources, int num_rays, float step_size,
-                      float radiation_velocity, float time_step, int n_freq, float* grad_j, float* grad_kappa,
-                      void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,
+                        const float* source_pos, int num_sources, int num_rays, float step_size,
+                        float radiation_velocity, float time_step, int n_freq, float* grad_j, float* grad_kappa,
+                        float* grad_src, void* cuda_stream) {
+    // the Call's output pointer only carries validation (non-NULL, no aliasing with the inputs)
+    float* any_out = grad_j ? grad_j : (grad_kappa ? grad_kappa : grad_src);
     Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size, radiation_velocity,
-           time_step, n_freq, grad_j ? grad_j : grad_kappa, 0, (cudaStream_t)cuda_stream};
+           time_step, n_freq, any_out, 0, (cudaStream_t)cuda_stream};
     int ns = 0;
     if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
     if (!grad_out) return fail(RT_ERR_INVALID_ARG, "grad_out is NULL");
-    if (!grad_j && !grad_kappa) return RT_OK;   // nothing requested
-    if (a.out == nullptr) return fail(RT_ERR_INVALID_ARG, "no gradient output");
+    if (!grad_j && !grad_kappa && !grad_src) return RT_OK;   // nothing requested
     rt_status st = validate(g, a, &ns);
     if (st != RT_OK) return st;
-    for (const float* o : {(const float*)grad_j, (const float*)grad_kappa})
-        if (o && (o == grad_out || o == j_map || o == kappa_map))
+    for (const float* o : {(const float*)grad_j, (const float*)grad_kappa, (const float*)grad_src})
+        if (o && (o == grad_out || o == j_map || o == kappa_map || o == source_pos))
             return fail(RT_ERR_INVALID_ARG, "a gradient output aliases an input");
     if (grad_j && grad_j == grad_kappa) return fail(RT_ERR_INVALID_ARG, "grad_j and grad_kappa alias");
+    if (grad_src && (grad_src == grad_j || grad_src == grad_kappa))
+        return fail(RT_ERR_INVALID_ARG, "grad_src aliases another gradient");
     if ((st = check_device(g)) != RT_OK) return st;
     const long long ncell = g->ncell();
     const size_t field_bytes = sizeof(float) * (size_t)n_freq * ncell;
+    if (grad_src && num_sources > 0)
+        RT_CUDA(cudaMemsetAsync(grad_src, 0, sizeof(float) * 3 * (size_t)num_sources, a.st), "cudaMemsetAsync(grad_src)");
     if (ns == 0 || num_sources == 0) {
         if (grad_j) RT_CUDA(cudaMemsetAsync(grad_j, 0, field_bytes, a.st), "cudaMemsetAsync(grad_j)");
         if (grad_kappa) RT_CUDA(cudaMemsetAsync(grad_kappa, 0, field_bytes, a.st), "cudaMemsetAsync(grad_kappa)");
@@ -762,6 +771,7 @@ rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, con
     b.n_freq = n_freq;
     b.kappa_mode = g->opt.kappa_mode;
     b.block = 32;
+    b.dsrc = grad_src;
     // checkpoint stride: the option, rounded to a supported value; automatic = 16
     const int want = g->opt.ckpt_stride > 0 ? g->opt.ckpt_stride : 16;
     b.stride = want <= 11 ? 8 : (want <= 23 ? 16 : 32);
@@ -802,6 +812,26 @@ rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, con
         RT_CUDA(rt::launch_unpack((const float*)dkp, grad_kappa, n_freq, W, ncell, 1.0f, 0, a.st),
                 "unpack(dkappa) launch");
     return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,
+                      const float* source_pos, int num_sources, int num_rays, float step_size,
+                      float radiation_velocity, float time_step, int n_freq, float* grad_j, float* grad_kappa,
+                      void* cuda_stream) {
+    return backward_impl(g, grad_out, j_map, kappa_map, source_pos, num_sources, num_rays, step_size,
+                         radiation_velocity, time_step, n_freq, grad_j, grad_kappa, nullptr, cuda_stream);
+}
+
+rt_status rt_backward_sources(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,
+                              const float* source_pos, int num_sources, int num_rays, float step_size,
+                              float radiation_velocity, float time_step, int n_freq, float* grad_j,
+                              float* grad_kappa, float* grad_src, void* cuda_stream) {
+    return backward_impl(g, grad_out, j_map, kappa_map, source_pos, num_sources, num_rays, step_size,
+                         radiation_velocity, time_step, n_freq, grad_j, grad_kappa, grad_src, cuda_stream);
 }
 
 }  // extern "C"

@@ -79,6 +79,7 @@ struct BackArgs {
     const float* kappa;     // packed like j
     float* dj;              // accumulator packed like j, or NULL (not wanted)
     float* dk;              // accumulator packed like j, or NULL (not wanted)
+    float* dsrc;            // dL/d(source positions) [nsrc][3], accumulated, or NULL (not wanted)
     float* ckpt;            // checkpoint scratch
     const float4* dirs;
     const float* src;

@@ -152,3 +152,81 @@ def test_amplitude_inversion_on_gpu(torch_cuda):
         with torch.no_grad():
             A -= (0.8 * A.grad.double() / curv).float()
     assert abs(A.item() - A_star.item()) <= 1e-4 * abs(A_star.item()), (A.item(), A_star.item())
+
+
+# ---- gradients with respect to the source positions and parameters built into j / kappa ----
+
+def gpu_backward_sources(torch, p, G, **opts):
+    from paper_2511_09389_gb300.api import Grid
+    g = Grid(p.shape, 8, **opts)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    gj, gk, gs = g.backward(t(G), t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size,
+                            p.radiation_velocity, p.time_step, need_sources=True)
+    torch.cuda.synchronize()
+    return gj.cpu().numpy(), gk.cpu().numpy(), gs.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_freq,stride", [(1, 16), (2, 8), (3, 32), (5, 16)])
+def test_source_gradient_matches_oracle(torch_cuda, n_freq, stride):
+    p = inputs.random_small(200 + n_freq, shape=(14, 11, 17), n_freq=n_freq, n_src=4, num_rays=97,
+                            step_size=0.6, horizon=15.0)
+    G = np.random.default_rng(7 + n_freq).standard_normal(p.j.shape)
+    gj, gk, gs = gpu_backward_sources(torch_cuda, p, G, ckpt_stride=stride)
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    rs = oracle.source_gradient(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G)
+    assert rel(gs, rs) <= GRAD_REL, rel(gs, rs)
+    # the field gradients of the same call are those of rt_backward
+    rj, rk = oracle_backward(p, G)
+    for b in range(n_freq):
+        assert rel(gj[b], rj[b]) <= GRAD_REL and rel(gk[b], rk[b]) <= GRAD_REL
+
+
+def test_source_gradient_full_size_inverse_workload(torch_cuda):
+    """64^3 lognormal kappa, 8 sources, N_Omega 3072, N_s 128, G = the log-field loss gradient
+    shape (a random field), against the oracle."""
+    p = inputs.inverse_problem()
+    G = np.random.default_rng(11).standard_normal(p.j.shape)
+    _, _, gs = gpu_backward_sources(torch_cuda, p, G)
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    rs = oracle.source_gradient(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G)
+    assert rel(gs, rs) <= GRAD_REL, rel(gs, rs)
+
+
+def test_autograd_sources_kappa_scale_and_amplitudes(torch_cuda):
+    """Parameters of the kind Sec. 4 names: a global kappa scale, per-source amplitudes (j as a
+    sum of per-source templates), and the source positions; gradients through RTFunction
+    against the oracle's adjoint composed by hand."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.autograd import render
+    rng = np.random.default_rng(3)
+    shape = (16, 14, 18)
+    centres = np.array([[5.2, 6.7, 8.1], [10.4, 7.3, 9.9], [7.7, 4.2, 12.5]])
+    templ = np.stack([inputs.gaussian_blobs(shape, c[None], 1.5, 1.0) for c in centres]).astype(np.float64)
+    kap0 = (0.03 + 0.05 * rng.random(shape))
+    amps = np.array([1.0, 0.6, 1.7])
+    alpha = 1.3
+    G = rng.standard_normal((2,) + shape)
+    num_rays, ds, dt = 256, 0.5, 9.0
+    nus = np.array([1.0, 1.5])
+
+    A = torch.tensor(amps, dtype=torch.float32, device="cuda", requires_grad=True)
+    al = torch.tensor(alpha, dtype=torch.float32, device="cuda", requires_grad=True)
+    S = torch.tensor(centres, dtype=torch.float32, device="cuda", requires_grad=True)
+    T = torch.from_numpy(templ.astype(np.float32)).cuda()
+    K0 = torch.from_numpy(kap0.astype(np.float32)).cuda()
+    nu = torch.from_numpy(nus.astype(np.float32)).cuda()
+    j = torch.einsum("i,ixyz->xyz", A, T)[None].expand(2, *shape).contiguous()
+    kappa = al * K0[None] * nu[:, None, None, None] ** -3.0
+    F = render(j, kappa, S, num_rays, ds, 1.0, dt)
+    (F * torch.from_numpy(G.astype(np.float32)).cuda()).sum().backward()
+
+    jn = np.einsum("i,ixyz->xyz", amps, templ)[None].repeat(2, axis=0)
+    kn = alpha * kap0[None] * nus[:, None, None, None] ** -3.0
+    ns = oracle.num_substeps(ds, 1.0, dt)
+    rj, rk = oracle.backward(jn, kn, centres, num_rays, ds, ns, G)
+    dA = np.einsum("bxyz,ixyz->i", rj, templ)
+    dal = float((rk * kn / alpha).sum())
+    dS = oracle.source_gradient(jn, kn, centres, num_rays, ds, ns, G)
+    assert rel(A.grad.cpu().numpy(), dA) <= GRAD_REL
+    assert abs(al.grad.item() - dal) <= GRAD_REL * abs(dal)
+    assert rel(S.grad.cpu().numpy(), dS) <= GRAD_REL
