@@ -280,16 +280,12 @@ def paper_workload(args, dev, flush, stream):
                       "note": "context only: another machine; the paper does not state N_s or bins"}}
 
 
-def batched(args, dev, stream):
-    """64 independent instances (edges from {32,48,64,96,128,160}, lognormal kappa with sigma_g in
-    [0.5, 1.5], 1-64 sources, N_Omega from {768, 3072, 12288}, ds 0.5, c dt = edge, 1-8 bins):
-    one autotuned persistent launch replayed from a CUDA graph, against the same instances
-    advanced one rt_advance call at a time. The inputs (2.6 GB) exceed L2, so no flush."""
+def _batch_vs_one_by_one(probs, args, dev, stream):
+    """One autotuned persistent launch of all instances replayed from a CUDA graph, against the
+    same instances advanced one autotuned rt_advance call at a time (mean ms of each)."""
     import statistics as st
     import torch
-    from paper_2511_09389_gb300 import inputs
     from paper_2511_09389_gb300.api import Batch, Grid
-    probs = inputs.batch_instances(64)
     dev_in = []
     for p in probs:
         d = {k: torch.from_numpy(v).to(dev) for k, v in (("j", p.j), ("kappa", p.kappa), ("sources", p.sources))}
@@ -332,9 +328,26 @@ def batched(args, dev, stream):
         g.close()
     return {"value": U / (mb * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": mb,
             "one_by_one": {"value": U / (m1 * 1e-3), "ms_per_step": m1}, "speedup_vs_one_by_one": m1 / mb,
-            "max_rel_l2_batched_vs_one_by_one": rel,
-            "workload": "64 instances: edges {32..160}, 1-64 sources, N_Omega {768,3072,12288}, 1-8 bins, c*dt = edge",
-            "l2": "inputs (2.6 GB) larger than L2"}
+            "max_rel_l2_batched_vs_one_by_one": rel}
+
+
+def batched(args, dev, stream):
+    """64 independent instances (edges from {32,48,64,96,128,160}, lognormal kappa with sigma_g in
+    [0.5, 1.5], 1-64 sources, N_Omega from {768, 3072, 12288}, ds 0.5, c dt = edge, 1-8 bins):
+    one autotuned persistent launch replayed from a CUDA graph, against the same instances
+    advanced one rt_advance call at a time. The inputs (2.6 GB) exceed L2, so no flush. Beside
+    it, 256 small instances (edges {16, 24, 32}, 1-4 sources, N_Omega {192, 768}, 1-2 bins), where
+    one call per instance is bound by launch and host overheads."""
+    from paper_2511_09389_gb300 import inputs
+    res = _batch_vs_one_by_one(inputs.batch_instances(64), args, dev, stream)
+    res.update({"workload": "64 instances: edges {32..160}, 1-64 sources, N_Omega {768,3072,12288}, 1-8 bins, "
+                            "c*dt = edge",
+                "l2": "inputs (2.6 GB) larger than L2"})
+    small = _batch_vs_one_by_one(inputs.batch_instances(256, seed=3100, edges=(16, 24, 32), ray_choices=(192, 768),
+                                                        max_src=4, max_freq=2), args, dev, stream)
+    small["workload"] = "256 instances: edges {16, 24, 32}, 1-4 sources, N_Omega {192, 768}, 1-2 bins, c*dt = edge"
+    res["small_instances"] = small
+    return res
 
 
 def surrogate_leg(args, dev):
