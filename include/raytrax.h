@@ -75,6 +75,11 @@ typedef struct {
     int plan_tile;      /*   and source deposit tiles (1: off, 2: on): each block sums the      */
                         /*   deposits of its rays in the 8^3 cells around its source in shared  */
                         /*   memory and adds them to the field once (not in deterministic mode) */
+    int check_inputs;   /* 1: checked mode. rt_advance* and rt_backward* first scan j, kappa,
+                           the sources (and grad_out) on the device and return
+                           RT_ERR_INVALID_ARG, naming the array, if a value is not finite, a
+                           kappa is negative or a source coordinate has |x| >= 2^24. The scan
+                           synchronises the stream (one pass over the inputs). 0: no scan. */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
@@ -245,6 +250,12 @@ rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, c
    every call then launches that graph on `cuda_stream` (NULL: legacy default stream). */
 rt_status rt_batch_run(rt_batch* batch, void* cuda_stream);
 
+/* One-shot batch: rt_batch_create with the handle's options (deterministic mode is not
+   supported), one rt_batch_run on the stream, a synchronisation of the stream, and
+   rt_batch_destroy. The instances need not match the handle's grid shape. For repeated runs
+   keep an rt_batch: its CUDA graph is captured once. */
+rt_status rt_advance_batch(rt_grid* grid, const rt_instance* inst, int n_inst, void* cuda_stream);
+
 /* Total updates (substeps x rays x sources x bins over all instances) of one run. */
 long long rt_batch_updates(const rt_batch* batch);
 
@@ -322,6 +333,11 @@ rt_status rt_adam_step(float* params, const float* grads, float* m, float* v, lo
    with *code = which wait gave up (1-4, 11: convolution ring / accumulator / completion, 5-9:
    weight gradient, 10: shared memory not 1024-byte aligned). */
 rt_status rt_device_status(int* code);
+
+/* Synchronise the stream (NULL: legacy default stream) and report what the device left:
+   RT_ERR_CUDA with the CUDA error's text if one is pending, RT_ERR_TIMEOUT if a kernel with
+   bounded waits gave up (as rt_device_status, whose word it clears), else RT_OK. */
+rt_status rt_sync_status(void* cuda_stream);
 
 /* ---- Microbenchmarks (no counterpart in the paper) ----------------------------------
    Peaks of the memory operations the march is built from, measured on the current device so

@@ -23,7 +23,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
            "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_c32_channel_mean",
-           "rt_adam_step", "rt_microbench")
+           "rt_adam_step", "rt_microbench", "rt_advance_batch", "rt_sync_status")
 
 
 class RTError(RuntimeError):
@@ -38,7 +38,8 @@ class rt_options(ctypes.Structure):
     _fields_ = [("deterministic", ctypes.c_int), ("kappa_mode", ctypes.c_int), ("ns_cap", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
                 ("profile", ctypes.c_int), ("plan_width", ctypes.c_int), ("plan_block", ctypes.c_int),
-                ("plan_prefetch", ctypes.c_int), ("plan_lanes", ctypes.c_int), ("plan_tile", ctypes.c_int)]
+                ("plan_prefetch", ctypes.c_int), ("plan_lanes", ctypes.c_int), ("plan_tile", ctypes.c_int),
+                ("check_inputs", ctypes.c_int)]
 
 
 class rt_instance(ctypes.Structure):
@@ -130,6 +131,10 @@ def load(path: str = LIB_PATH):
         lib.rt_microbench.argtypes = [i, i, vp, ll, i, i, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_double)]
         lib.rt_microbench.restype = i
+        lib.rt_advance_batch.argtypes = [vp, vp, i, vp]
+        lib.rt_advance_batch.restype = i
+        lib.rt_sync_status.argtypes = [vp]
+        lib.rt_sync_status.restype = i
         lib.rt_c32_channel_mean.argtypes = [vp, i, i, ll, vp, vp]
         lib.rt_c32_channel_mean.restype = i
         lib.rt_adam_step.argtypes = [vp, vp, vp, vp, ll, f, f, f, f, i, vp]

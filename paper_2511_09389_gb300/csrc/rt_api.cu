@@ -133,7 +133,7 @@ struct rt_grid {
     int device = 0;
     std::vector<DirTable> dirs;
     // scratch slots
-    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, NSLOT };
+    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, CHK, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -422,11 +422,31 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
     return RT_OK;
 }
 
+// Checked mode (rt_options.check_inputs): scan the call's inputs on the device, synchronise,
+// and name the first offending array.
+rt_status check_inputs(rt_grid* g, const Call& a, const float* grad) {
+    if (!g->opt.check_inputs) return RT_OK;
+    void* f;
+    rt_status st = g->ensure(rt_grid::CHK, 4 * sizeof(int), &f);
+    if (st != RT_OK) return st;
+    const long long n = (long long)a.n_freq * g->ncell();
+    RT_CUDA(rt::launch_check_inputs(a.j, a.kappa, n, a.src, a.nsrc, grad, (int*)f, a.st), "input check launch");
+    int h[4] = {0, 0, 0, 0};
+    RT_CUDA(cudaMemcpyAsync(h, f, sizeof h, cudaMemcpyDeviceToHost, a.st), "input check copy");
+    RT_CUDA(cudaStreamSynchronize(a.st), "input check synchronise");
+    if (h[0]) return fail(RT_ERR_INVALID_ARG, "checked mode: j_map holds a value that is not finite");
+    if (h[1]) return fail(RT_ERR_INVALID_ARG, "checked mode: kappa_map holds a negative or non-finite value");
+    if (h[2]) return fail(RT_ERR_INVALID_ARG, "checked mode: source_pos holds a non-finite coordinate or |x| >= 2^24");
+    if (h[3]) return fail(RT_ERR_INVALID_ARG, "checked mode: grad_out holds a value that is not finite");
+    return RT_OK;
+}
+
 rt_status advance_impl(rt_grid* g, const Call& a) {
     int ns = 0;
     rt_status st = validate(g, a, &ns);
     if (st != RT_OK) return st;
     if ((st = check_device(g)) != RT_OK) return st;
+    if ((st = check_inputs(g, a, nullptr)) != RT_OK) return st;
     const long long ncell = g->ncell();
     const size_t field_bytes = sizeof(float) * (size_t)a.n_freq * ncell;
     const int count = a.ray_end - a.ray_begin;
@@ -581,6 +601,29 @@ rt_status rt_advance(rt_grid* grid, const float* j_map, const float* kappa_map, 
     Call a{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size,
            radiation_velocity, time_step, n_freq, out_field, accumulate ? 1 : 0, (cudaStream_t)cuda_stream};
     return advance_impl(grid, a);
+}
+
+rt_status rt_sync_status(void* cuda_stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(RT_ERR_CUDA, "device error: %s", cudaGetErrorString(e));
+    int code = 0;
+    return rt_device_status(&code);
+}
+
+rt_status rt_advance_batch(rt_grid* g, const rt_instance* inst, int n_inst, void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    rt_status st = check_device(g);
+    if (st != RT_OK) return st;
+    rt_batch* b = nullptr;
+    if ((st = rt_batch_create(&b, inst, n_inst, &g->opt)) != RT_OK) return st;
+    st = rt_batch_run(b, cuda_stream);
+    if (st == RT_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "rt_advance_batch synchronise");
+    }
+    rt_batch_destroy(b);
+    return st;
 }
 
 rt_status rt_advance_continue(rt_grid* g, const float* j_map, const float* kappa_map, const float* source_pos,
@@ -747,6 +790,7 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
     if (grad_src && (grad_src == grad_j || grad_src == grad_kappa))
         return fail(RT_ERR_INVALID_ARG, "grad_src aliases another gradient");
     if ((st = check_device(g)) != RT_OK) return st;
+    if ((st = check_inputs(g, a, grad_out)) != RT_OK) return st;
     const long long ncell = g->ncell();
     const size_t field_bytes = sizeof(float) * (size_t)n_freq * ncell;
     if (grad_src && num_sources > 0)

@@ -64,6 +64,10 @@ cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long 
 // Deterministic mode: *fix = largest power of two with fix * per_jmax * max|j| <= 2^62
 // (jmax_tmp: device float scratch), and out[b][c] (+)= acc[b / W][c][b % W] / *fix.
 cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, float* fix, cudaStream_t st);
+// Checked mode: flags (4 device ints, cleared first) mark non-finite j / negative or non-finite
+// kappa / non-finite or too large source coordinates / non-finite extra (a loss gradient, may be NULL).
+cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n, const float* src, int nsrc,
+                                const float* extra, int* flags, cudaStream_t st);
 cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
                                   float* out, int accumulate, cudaStream_t st);
 
