@@ -215,7 +215,7 @@ def fwd_adjoint(args, dev, flush, stream):
     from paper_2511_09389_gb300.api import Grid, num_substeps
     p = inputs.inverse_problem()
     U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
-    g = Grid(p.shape, 1, profile=True)
+    g = Grid(p.shape, 1, profile=True, record_checkpoints=True)
     j, k, s = (torch.from_numpy(a).to(dev) for a in (p.j, p.kappa, p.sources))
     G = torch.randn(p.j.shape, device=dev)
     out = torch.empty_like(j)
@@ -239,6 +239,7 @@ def fwd_adjoint(args, dev, flush, stream):
     tf, tb = st.mean(fwd), st.mean(bwd)
     return {"value": U / ((tf + tb) * 1e-3), "unit": "updates/s", "updates_per_step": U,
             "workload": "inverse problem: lognormal kappa 64^3, 8 sources, N_Omega 3072, ds 0.5, N_s 128, 1 bin",
+            "checkpoints": "recorded by the forward march, reused by the reverse march (record_checkpoints)",
             "ms_fwd": tf, "ms_bwd": tb, "fwd_kernel_ms": st.mean(kf), "adjoint_kernel_ms": st.mean(kb),
             "adjoint_updates_per_s": U / (tb * 1e-3)}
 

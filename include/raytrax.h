@@ -80,6 +80,13 @@ typedef struct {
                            RT_ERR_INVALID_ARG, naming the array, if a value is not finite, a
                            kappa is negative or a source coordinate has |x| >= 2^24. The scan
                            synchronises the stream (one pass over the inputs). 0: no scan. */
+    int record_checkpoints; /* 1: every full-range rt_advance also stores the reverse march's
+                           checkpoints (every ckpt_stride substeps) in the handle, marching
+                           with the adjoint's bin grouping and gathers mode 0; a following
+                           rt_backward / rt_backward_sources with the same j_map, kappa_map and
+                           source_pos pointers and the same scalars uses them instead of
+                           repeating the forward sweep. The caller must not change the contents
+                           of those buffers in between (autograd guarantees it). 0: off. */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,

@@ -39,7 +39,7 @@ class rt_options(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("ckpt_stride", ctypes.c_int),
                 ("profile", ctypes.c_int), ("plan_width", ctypes.c_int), ("plan_block", ctypes.c_int),
                 ("plan_prefetch", ctypes.c_int), ("plan_lanes", ctypes.c_int), ("plan_tile", ctypes.c_int),
-                ("check_inputs", ctypes.c_int)]
+                ("check_inputs", ctypes.c_int), ("record_checkpoints", ctypes.c_int)]
 
 
 class rt_instance(ctypes.Structure):

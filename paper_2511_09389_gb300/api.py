@@ -60,7 +60,7 @@ class Grid:
 
     def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
                  ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
-                 plan=None, check_inputs: bool = False, device=None):
+                 plan=None, check_inputs: bool = False, record_checkpoints: bool = False, device=None):
         self._lib = _native.load()
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) != 3:
@@ -72,7 +72,8 @@ class Grid:
             int(plan[0]), int(plan[1]), int(plan[2]) + 1, int(plan[3]) if len(plan) > 3 else 1,
             int(plan[4]) + 1 if len(plan) > 4 else 0)
         opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
-                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl, pt, int(bool(check_inputs)))
+                                 int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl, pt, int(bool(check_inputs)),
+                                 int(bool(record_checkpoints)))
         self.options = opt
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -24,9 +24,14 @@ class RTFunction(torch.autograd.Function):
         j4 = _grid_tensor(j, "j")
         k4 = _grid_tensor(kappa, "kappa")
         if grid is None:
-            grid = _cached_grid(j4.shape[1:], j4.shape[0], j4.device)
-        out = grid.advance(j4, k4, sources, num_rays, step_size, radiation_velocity, time_step)
-        ctx.save_for_backward(j4, k4, torch.as_tensor(sources, dtype=torch.float32, device=j4.device).detach())
+            # the forward records the reverse march's checkpoints; backward reuses them
+            grid = _cached_grid(j4.shape[1:], j4.shape[0], j4.device, record_checkpoints=True)
+        # one device copy of the sources, used by both passes (the recorded checkpoints are
+        # matched by buffer address)
+        src = torch.as_tensor(sources, dtype=torch.float32, device=j4.device).detach().reshape(-1, 3).contiguous()
+        out = grid.advance(j4, k4, src, num_rays, step_size, radiation_velocity, time_step)
+        ctx.save_for_backward(j4, k4, src)
+        ctx.src_shape = tuple(torch.as_tensor(sources).shape)
         ctx.args = (num_rays, step_size, radiation_velocity, time_step, grid, squeeze)
         return out[0] if squeeze else out
 
@@ -39,7 +44,7 @@ class RTFunction(torch.autograd.Function):
         res = grid.backward(g.contiguous().float(), j4, k4, src, num_rays, step_size, c, dt,
                             need_j=need_j, need_kappa=need_k, need_sources=need_s)
         gj, gk = res[0], res[1]
-        gs = res[2].reshape(src.shape) if need_s else None
+        gs = res[2].reshape(ctx.src_shape) if need_s else None
         if squeeze:
             gj = gj[0] if gj is not None else None
             gk = gk[0] if gk is not None else None

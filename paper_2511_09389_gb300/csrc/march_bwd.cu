@@ -54,8 +54,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     float* __restrict__ ck = a.ckpt;
     auto ck_at = [&](int c, int f) -> float& { return ck[((size_t)c * F + f) * lanes + lane]; };
 
-    // ---- forward sweep: Eq. 2, checkpoint every K substeps ----
-    {
+    // ---- forward sweep: Eq. 2, checkpoint every K substeps (skipped when the forward march
+    // recorded them) ----
+    if (!a.have_ckpt) {
         float x = a.src[3 * s + 0], y = a.src[3 * s + 1], z = a.src[3 * s + 2];
         float I[W], tau[W];
 #pragma unroll

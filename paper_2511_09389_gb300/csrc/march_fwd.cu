@@ -19,7 +19,8 @@ __device__ __forceinline__ int tile_origin(float src, int n) {
 // shared memory; its lanes' deposits there are summed with shared-memory atomics and added to
 // the field once per block. The cells next to a source receive a deposit from every ray of it,
 // so this takes the most contended L2 atomics off the march and sums them in shorter chains.
-template <int W, int PF, int DET, bool TILE>
+// REC: also write the reverse march's checkpoints (march_lane).
+template <int W, int PF, int DET, bool TILE, bool REC = false>
 __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     constexpr int TCELLS = kTile * kTile * kTile;
     __shared__ float tile[TILE ? TCELLS * W : 1];
@@ -75,7 +76,12 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
                 rs.tau[b] = a.st_tau[(long long)(g * W + b) * lanes + lane];
             }
     }
-    march_lane<W, PF, DET, TILE>(L, rs);
+    if (REC) {
+        L.ck_lanes = (long long)a.ray_count * a.nsrc * a.groups;
+        L.ck = a.ckpt + ((long long)g * a.nsrc + s) * a.ray_count + r;
+        L.ck_stride = a.ck_stride;
+    }
+    march_lane<W, PF, DET, TILE, REC>(L, rs);
     if (a.st_I) {
 #pragma unroll
         for (int b = 0; b < W; ++b)
@@ -170,6 +176,19 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
         return cudaGetLastError();
     }
     const bool tile = a.tile && a.n0 >= kTile && a.n1 >= kTile && a.n2 >= kTile;
+    if (a.ckpt) {   // recording the adjoint's checkpoints: gather mode 0
+        if (a.prefetch != 0 || a.ck_stride < 1) return cudaErrorInvalidValue;
+        switch (W * 2 + (tile ? 1 : 0)) {
+            case 2: k_march_fwd<1, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 3: k_march_fwd<1, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd<2, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 5: k_march_fwd<2, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 8: k_march_fwd<4, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 9: k_march_fwd<4, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch ((W * 4 + a.prefetch) * 2 + (tile ? 1 : 0)) {
 #define RT_FWD_CASE(W_, PF_)                                                                     \
         case (W_ * 4 + PF_) * 2: k_march_fwd<W_, PF_, 0, false><<<(unsigned)nblk, block, 0, st>>>(a); break; \

@@ -49,6 +49,11 @@ struct Lane {
     int kappa_mode;
     float* tile = nullptr;    // the block's shared-memory deposit tile ([kTile^3][W]) or NULL
     int to0 = 0, to1 = 0, to2 = 0;   // its origin cell
+    // REC: adjoint checkpoints written during the march, in the reverse march's layout: the
+    // lane's fields f of checkpoint c at ck[(c * (3 + 2W) + f) * ck_lanes]
+    float* ck = nullptr;
+    long long ck_lanes = 0;
+    int ck_stride = 0;
 };
 
 // The state a lane carries through its march, in and out: position, and I and tau of its bins.
@@ -277,7 +282,9 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L, RayState<W>& R) 
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
 }
 
-template <int W, int PF, int DET = 0, bool TILE = false>
+// REC (gather mode 0 only): store (x_k, I_k, tau_k) every ck_stride substeps, the forward sweep
+// the reverse march would otherwise repeat.
+template <int W, int PF, int DET = 0, bool TILE = false, bool REC = false>
 __device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
     if (PF == 2) {
         march_lane_ahead<W, DET, TILE>(L, R);
@@ -310,8 +317,23 @@ __device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
     make_sample<TILE>(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm, L.to0, L.to1, L.to2);
     if (PF) gather<W>(jg, kg, sm, gd);
 
+    int ck_left = 0;     // REC: substeps until the next checkpoint
+    float* ckp = L.ck;   // REC: this lane's next checkpoint
 #pragma unroll 1
     for (int k = 0; k < L.ns; ++k) {
+        if (REC) {
+            if (ck_left == 0) {
+                ckp[0] = x; ckp[L.ck_lanes] = y; ckp[2 * L.ck_lanes] = z;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    ckp[(3 + b) * L.ck_lanes] = I[b];
+                    ckp[(3 + W + b) * L.ck_lanes] = tau[b];
+                }
+                ckp += (3 + 2 * W) * L.ck_lanes;
+                ck_left = L.ck_stride;
+            }
+            --ck_left;
+        }
         x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
         y = __fadd_rn(y, dy);
         z = __fadd_rn(z, dz);

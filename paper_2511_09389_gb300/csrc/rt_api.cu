@@ -152,6 +152,14 @@ struct rt_grid {
     std::string tune_report;   // candidates timed by the last autotuning pass
     // state of the stateful advance (rt_advance_continue): which problem it belongs to, which of
     // the two position buffers holds the current positions, substeps marched since the restart
+    // checkpoints recorded by the last recording rt_advance (record_checkpoints): the call they
+    // belong to; valid until a reverse march or another recording overwrites the CKPT slot
+    struct Recording {
+        bool valid = false;
+        const float *j = nullptr, *kappa = nullptr, *src = nullptr;
+        int nsrc = 0, rays = 0, ns = 0, n_freq = 0, stride = 0, W = 0, kappa_mode = 0;
+        float ds = 0.0f;
+    } rec;
     struct ContinueState {
         bool valid = false;
         int nsrc = 0, rays = 0, n_freq = 0, parity = 0;
@@ -348,6 +356,12 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
     return RT_OK;
 }
 
+// Adjoint checkpoint stride: the option, rounded to a supported value; automatic = 16.
+int ckpt_stride(const rt_grid* g) {
+    const int want = g->opt.ckpt_stride > 0 ? g->opt.ckpt_stride : 16;
+    return want <= 11 ? 8 : (want <= 23 ? 16 : 32);
+}
+
 size_t acc_bytes(const rt_grid* g, const Call& a, const Plan& plan) {
     const int groups = (a.n_freq + plan.W - 1) / plan.W;
     return sizeof(float) * (size_t)groups * g->ncell() * plan.W;
@@ -513,6 +527,14 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         plan.lpr = 1;
         plan.prefetch = 0;
     }
+    // record the reverse march's checkpoints: its bin grouping, one lane per ray, gathers mode 0
+    const bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
+    if (record) {
+        if (plan.W != pick_width(a.n_freq)) plan.block = 32;   // the tuned block was for another width
+        plan.W = pick_width(a.n_freq);
+        plan.lpr = 1;
+        plan.prefetch = 0;
+    }
     g->last_plan = plan;
 
     rt::MarchArgs m;
@@ -522,6 +544,19 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     m.st_I = a.st_I;
     m.st_tau = a.st_tau;
     m.st_read = a.st_read;
+    if (record) {
+        rt::BackArgs sz{};
+        sz.ray_count = a.num_rays; sz.nsrc = a.nsrc; sz.n_freq = a.n_freq; sz.ns = ns;
+        sz.stride = ckpt_stride(g);
+        void* ck;
+        g->rec.valid = false;
+        if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(sz, plan.W), &ck)) != RT_OK)
+            return st;
+        m.ckpt = (float*)ck;
+        m.ck_stride = sz.stride;
+        g->rec = rt_grid::Recording{true, a.j, a.kappa, a.src, a.nsrc, a.num_rays, ns, a.n_freq, sz.stride,
+                                    plan.W, g->opt.kappa_mode, a.ds};
+    }
     if (plan.W > 1 || !a.accumulate)
         RT_CUDA(cudaMemsetAsync(m.acc, 0, plan.W == 1 ? field_bytes : acc_bytes(g, a, plan), a.st),
                 "cudaMemsetAsync(accumulator)");
@@ -816,11 +851,15 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
     b.kappa_mode = g->opt.kappa_mode;
     b.block = 32;
     b.dsrc = grad_src;
-    // checkpoint stride: the option, rounded to a supported value; automatic = 16
-    const int want = g->opt.ckpt_stride > 0 ? g->opt.ckpt_stride : 16;
-    b.stride = want <= 11 ? 8 : (want <= 23 ? 16 : 32);
+    b.stride = ckpt_stride(g);
     const int W = pick_width(n_freq);
     const int groups = (n_freq + W - 1) / W;
+    // checkpoints recorded by the forward march of exactly this problem: skip the forward sweep
+    const auto& r = g->rec;
+    b.have_ckpt = r.valid && r.j == j_map && r.kappa == kappa_map && r.src == source_pos &&
+                  r.nsrc == num_sources && r.rays == num_rays && r.ns == ns && r.n_freq == n_freq &&
+                  r.stride == b.stride && r.W == W && r.kappa_mode == g->opt.kappa_mode && r.ds == step_size;
+    if (!b.have_ckpt) g->rec.valid = false;   // this reverse march rewrites the checkpoint slot
     void* ck;
     if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(b, W), &ck)) != RT_OK) return st;
     b.ckpt = (float*)ck;

@@ -51,6 +51,9 @@ struct MarchArgs {
     float* st_I;
     float* st_tau;
     int st_read;
+    // adjoint checkpoints recorded during the march (NULL: none), layout of BackArgs::ckpt
+    float* ckpt;
+    int ck_stride;
 };
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);
@@ -84,6 +87,7 @@ struct BackArgs {
     float* dj;              // accumulator packed like j, or NULL (not wanted)
     float* dk;              // accumulator packed like j, or NULL (not wanted)
     float* dsrc;            // dL/d(source positions) [nsrc][3], accumulated, or NULL (not wanted)
+    int have_ckpt;          // 1: ckpt already holds this problem's checkpoints (skip the forward sweep)
     float* ckpt;            // checkpoint scratch
     const float4* dirs;
     const float* src;
