@@ -432,12 +432,15 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
 
     const int half_h = a.H >> 1;
     const int tiles_per_b = a.D * half_h;
-    const int t_begin = (int)((long long)a.n_tiles * blockIdx.x / gridDim.x);
-    const int t_end = (int)((long long)a.n_tiles * (blockIdx.x + 1) / gridDim.x);
+    // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: at any time the blocks work on one window of
+    // neighbouring tiles, whose shifted boxes overlap and stay in L2 (a contiguous range per
+    // block re-read its halos from DRAM: 3.5x the input)
+    const int t_begin = blockIdx.x;
+    const int t_step = gridDim.x;
     int done_tiles = 0;
     if (warp == 0 && lane == 0) {
         int gq = 0, zq = 0;
-        for (int tile = t_begin; tile < t_end && !*abort_flag; ++tile, ++done_tiles) {
+        for (int tile = t_begin; tile < a.n_tiles && !*abort_flag; tile += t_step, ++done_tiles) {
             const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
             const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
             if (!mbar_wait(zempty, ((uint32_t)done_tiles & 1u) ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 5); break; }
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
         for (int p = gq > 2 ? gq - 2 : 0; p < gq; ++p) mbar_wait(&gfull[p & 1], (uint32_t)(p >> 1) & 1u);
     } else if (warp == 1 && lane == 0) {
         int gq = 0;
-        for (int tile = t_begin; tile < t_end && !*abort_flag; ++tile, ++done_tiles) {
+        for (int tile = t_begin; tile < a.n_tiles && !*abort_flag; tile += t_step, ++done_tiles) {
             if (!mbar_wait(zfull, (uint32_t)done_tiles & 1u)) { *abort_flag = 1; atomicExch(a.err, 7); break; }
             const uint32_t zb = smem_u32(sz);
             for (int g = 0; g < kWgGroups; ++g, ++gq) {
@@ -484,7 +487,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
         mma_commit(mma_done);   // arrives once every MMA issued above has completed
     }
     __syncthreads();
-    const int ntile = t_end - t_begin;
+    const int ntile = t_begin < a.n_tiles ? (a.n_tiles - 1 - t_begin) / t_step + 1 : 0;
     const bool mma_ok = mbar_wait(mma_done, 0);
     bool ok = mma_ok && !*abort_flag;
     if (!mma_ok && tid == 0) atomicExch(a.err, 9);
