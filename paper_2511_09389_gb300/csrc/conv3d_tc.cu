@@ -9,7 +9,8 @@
 // swizzle lays the box out as the canonical SW64 K-major operand (8-row atoms of 512 bytes): the
 // tensor core reads A straight from the TMA destination, K = 32 channels = two MMAs of K = 16.
 // B (weights) sits in shared memory for the whole kernel as [tap][32 out][32 in] in the same
-// swizzled layout. The weight gradient reads the same boxes MN-major.
+// swizzled layout. The forward kernel walks chains of output slices along z so that each box
+// serves the three outputs that need it; the weight gradient reads the same boxes MN-major.
 //
 // Every wait is bounded (about one second of global time): on timeout the kernel records an
 // error word, stops issuing work, frees its tensor memory and returns.
@@ -133,28 +134,6 @@ constexpr int kTmemCols = 32;
 constexpr int kBox = 128 * 64;             // one tap box: 128 voxels x 32 channels x 2 bytes
 constexpr int kWBytes = 27 * 32 * 64;      // weights: 27 taps x 32 outputs x 64-byte rows
 constexpr int kConvThreads = 192;          // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
-// Each ring stage costs a fixed few hundred cycles of barrier round trip on top of its MMAs,
-// so a stage carries several taps and two blocks share an SM to overlap those latencies
-// (measured on GB300: 1 block x 1 tap per stage 184 TFLOP/s, 2 blocks x 3 taps 433 TFLOP/s).
-#ifndef RT_CONV_CTAS
-#define RT_CONV_CTAS 2
-#endif
-constexpr int kConvCtas = RT_CONV_CTAS;    // resident blocks per SM
-#ifndef RT_CONV_TPS
-#define RT_CONV_TPS 3
-#endif
-constexpr int kTps = RT_CONV_TPS;          // taps per ring stage (1, 3 or 9)
-constexpr int kStageBytes = kTps * kBox;
-#ifdef RT_CONV_STAGES
-constexpr int kStages = RT_CONV_STAGES;
-#else
-// ring as deep as each block's share of the SM's 228 KB of shared memory allows
-constexpr int kStages = ((228 * 1024) / kConvCtas - 1024 - kWBytes - 512) / kStageBytes;
-#endif
-static_assert(27 % kTps == 0 && kStages >= 2, "ring layout");
-constexpr int kConvBarOff = kWBytes + kStages * kStageBytes;
-constexpr int kConvBytes = kConvBarOff + (2 * kStages + 5) * 8 + 16;
-
 struct ConvArgs {
     const uint4* w_packed;            // [27][32][32] bf16 (tap, out, in) in 16-byte units
     const float* bias;                // [c_out] or NULL
@@ -163,7 +142,6 @@ struct ConvArgs {
     float* y_f32;                     // [B][D][H][W] (channel 0) or NULL
     int B, D, H, W, c_out, dil, act;
     float slope;
-    int n_tiles;
     int* err;
 };
 
@@ -179,30 +157,74 @@ __device__ __forceinline__ int sw64(int r, int c) { return r * 64 + ((c ^ ((r >>
 
 }  // namespace
 
-// Persistent and warp-specialised: warp 0 streams the 27 tap boxes of every tile through a
-// ring of multi-tap stages, warp 1 issues the MMAs into one of two TMEM accumulators, warps 2-5 drain the other
-// (epilogue), so loads, MMAs and stores of consecutive tiles overlap.
-__global__ void __launch_bounds__(kConvThreads, kConvCtas) k_conv3d_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
-    constexpr int S = kStages;
+// ---- forward, chained along z ------------------------------------------------------------
+// An output slice z takes the input slices z - d, z, z + d. Along a chain of outputs r, r + d,
+// r + 2d, ... (fixed batch, y-pair and residue r = z mod d) consecutive outputs share input
+// slices, so each input box (slice z', dy, dx) is loaded once and feeds the three outputs it
+// belongs to (dz = -1, 0, +1, with the weights of tap (dz, dy, dx)). A work item is a chain
+// segment of at most kChainMax outputs; its inputs are the segment's slices plus one on each
+// side (those outside the volume are zero padding and skipped). A ring stage carries the three
+// dx boxes of one (input slice, dy); up to 18 MMAs per stage into a ring of kChainSlots TMEM
+// accumulators, drained by the epilogue warps in output order. Per output tile ~11 boxes are
+// loaded instead of 27, and each stage's fixed round trip is shared by six times more MMAs.
+namespace {
+#ifndef RT_CHAIN_MAX
+#define RT_CHAIN_MAX 8
+#endif
+constexpr int kChainMax = RT_CHAIN_MAX;   // outputs per work item
+constexpr int kChainSlots = 4;
+#ifndef RT_CHAIN_CTAS
+#define RT_CHAIN_CTAS 2
+#endif
+constexpr int kChainCtas = RT_CHAIN_CTAS;
+constexpr int kChainStageBytes = 3 * kBox;
+constexpr int kChainStages = ((228 * 1024) / kChainCtas - 1024 - kWBytes - 512) / kChainStageBytes;
+static_assert(kChainStages >= 2, "chain ring");
+constexpr int kChainBarOff = kWBytes + kChainStages * kChainStageBytes;
+constexpr int kChainBytes = kChainBarOff + (2 * kChainStages + 2 * kChainSlots + 1) * 8 + 16;
+
+struct ChainItem {
+    int b, y0, r, n0, n1;   // outputs z = r + n * dil for n in [n0, n1)
+};
+
+// Items ordered (batch, segment, residue, y-pair), y-pair fastest: neighbouring items share halo rows.
+__device__ __forceinline__ bool chain_item(const ConvArgs& a, int item, int Q, ChainItem& it) {
+    const int half_h = a.H >> 1;
+    int t = item;
+    const int p = t % half_h;
+    t /= half_h;
+    const int r = t % a.dil;
+    t /= a.dil;
+    const int q = t % Q;
+    it.b = t / Q;
+    it.y0 = 2 * p;
+    it.r = r;
+    const int lc = (a.D - r + a.dil - 1) / a.dil;   // outputs of residue r (0 when r >= D)
+    it.n0 = q * kChainMax;
+    it.n1 = min(lc, it.n0 + kChainMax);
+    return it.n0 < it.n1;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const __grid_constant__ CUtensorMap tmap,
+                                                                           ConvArgs a, int n_items, int Q) {
+    constexpr int S = kChainStages;
+    constexpr int NS = kChainSlots;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sw = smem;
     unsigned char* sa = smem + kWBytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kConvBarOff);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kChainBarOff);
     uint64_t* empty = full + S;
     uint64_t* acc_full = empty + S;
-    uint64_t* acc_empty = acc_full + 2;
-    uint64_t* mma_done = acc_empty + 2;
+    uint64_t* acc_empty = acc_full + NS;
+    uint64_t* mma_done = acc_empty + NS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the 64-byte swizzle is a function of address bits: every operand block must sit on a
-    // 1024-byte boundary (uniform exit, before any barrier or allocation)
     if (smem_u32(smem) & 1023u) {
         if (tid == 0) atomicExch(a.err, 10);
         return;
     }
-
-    // weights -> shared memory in the swizzled layout (ordinary stores, fenced below)
     for (int i = tid; i < kWBytes / 16; i += kConvThreads) {
         const int c = i & 3, r = (i >> 2) & 31, tap = i >> 7;
         *reinterpret_cast<uint4*>(sw + tap * 2048 + sw64(r, c)) = __ldg(a.w_packed + i);
@@ -212,7 +234,7 @@ __global__ void __launch_bounds__(kConvThreads, kConvCtas) k_conv3d_tc(const __g
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
         }
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < NS; ++q) {
             mbar_init(&acc_full[q], 1);
             mbar_init(&acc_empty[q], 128);
         }
@@ -222,7 +244,7 @@ __global__ void __launch_bounds__(kConvThreads, kConvCtas) k_conv3d_tc(const __g
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * kTmemCols)
+                     "r"(NS * kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -231,138 +253,166 @@ __global__ void __launch_bounds__(kConvThreads, kConvCtas) k_conv3d_tc(const __g
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
     constexpr uint32_t idesc = idesc_bf16(128, 32);
-    const int half_h = a.H >> 1;
-    const int tiles_per_b = a.D * half_h;
 
     if (warp == 0) {
         if (lane == 0) {
             int q = 0;
-            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x) {
-                const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
-                const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
-                for (int t0 = 0; t0 < 27; t0 += kTps, ++q) {
-                    const int st = q % S;
-                    if (!mbar_wait(&empty[st], ((uint32_t)(q / S) & 1u) ^ 1u)) {
-                        *abort_flag = 1;
-                        atomicExch(a.err, 1);
-                        break;
-                    }
-                    mbar_expect_tx(&full[st], kStageBytes);
+            for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+                ChainItem it;
+                if (!chain_item(a, item, Q, it)) continue;
+                for (int i = it.n0 - 1; i <= it.n1 && !*abort_flag; ++i) {
+                    const int zi = it.r + i * a.dil;
+                    if (zi < 0 || zi >= a.D) continue;
+                    for (int dy = -1; dy <= 1; ++dy, ++q) {
+                        const int st = q % S;
+                        if (!mbar_wait(&empty[st], ((uint32_t)(q / S) & 1u) ^ 1u)) {
+                            *abort_flag = 1;
+                            atomicExch(a.err, 1);
+                            break;
+                        }
+                        mbar_expect_tx(&full[st], kChainStageBytes);
 #pragma unroll
-                    for (int u = 0; u < kTps; ++u) {
-                        const int tap = t0 + u;
-                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                        tma_load_5d(sa + st * kStageBytes + u * kBox, &tmap, &full[st], 0, dx * a.dil,
-                                    y0 + dy * a.dil, z + dz * a.dil, b);
+                        for (int u = 0; u < 3; ++u)
+                            tma_load_5d(sa + st * kChainStageBytes + u * kBox, &tmap, &full[st], 0, (u - 1) * a.dil,
+                                        it.y0 + dy * a.dil, zi, it.b);
                     }
                 }
             }
-            // let the last loads land before the block can exit (returns at once after normal use)
             for (int p = q > S ? q - S : 0; p < q; ++p) mbar_wait(&full[p % S], (uint32_t)(p / S) & 1u);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int q = 0, t = 0;
-            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x, ++t) {
-                const int acc = t & 1;
-                if (!mbar_wait(&acc_empty[acc], ((uint32_t)(t >> 1) & 1u) ^ 1u)) {
-                    *abort_flag = 1;
-                    atomicExch(a.err, 3);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * kTmemCols);
-                bool ok = true;
-                for (int t0 = 0; t0 < 27; t0 += kTps, ++q) {
-                    const int st = q % S;
-                    if (!mbar_wait(&full[st], (uint32_t)(q / S) & 1u)) {
-                        *abort_flag = 1;
-                        atomicExch(a.err, 2);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+            int q = 0, seq = 0;
+            bool first[NS];
 #pragma unroll
-                    for (int u = 0; u < kTps; ++u) {
-                        const int tap = t0 + u;
-                        const uint32_t abase = smem_u32(sa + st * kStageBytes + u * kBox);
-                        const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * 2048);
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            // K-major SW64: K half k starts 32 bytes into each 64-byte row
-                            const uint64_t ad = sdesc_sw64(abase + (uint32_t)(k * 32), 16, 512);
-                            const uint64_t bd = sdesc_sw64(bbase + (uint32_t)(k * 32), 16, 512);
-                            mma_bf16(d, ad, bd, idesc, (tap | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < NS; ++k) first[k] = false;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok && !*abort_flag; item += gridDim.x) {
+                ChainItem it;
+                if (!chain_item(a, item, Q, it)) continue;
+                const int base = seq;
+                int started = it.n0;   // outputs [n0, started) have their accumulators
+                for (int i = it.n0 - 1; i <= it.n1 && ok; ++i) {
+                    const int zi = it.r + i * a.dil;
+                    if (zi >= 0 && zi < a.D) {
+                        // outputs fed by this input: i + 1 (dz = -1), i (dz = 0), i - 1 (dz = +1)
+                        const int last = min(i + 1, it.n1 - 1);
+                        for (; started <= last && ok; ++started) {
+                            const int sq = base + (started - it.n0);
+                            if (!mbar_wait(&acc_empty[sq % NS], ((uint32_t)(sq / NS) & 1u) ^ 1u)) {
+                                *abort_flag = 1;
+                                atomicExch(a.err, 3);
+                                ok = false;
+                            }
+                            first[sq % NS] = true;
                         }
+                        if (!ok) break;
+                        tc_fence_after();
+                        for (int dy = -1; dy <= 1; ++dy, ++q) {
+                            const int st = q % S;
+                            if (!mbar_wait(&full[st], (uint32_t)(q / S) & 1u)) {
+                                *abort_flag = 1;
+                                atomicExch(a.err, 2);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t sbase = smem_u32(sa + st * kChainStageBytes);
+#pragma unroll
+                            for (int dz = -1; dz <= 1; ++dz) {
+                                const int n = i - dz;
+                                if (n < it.n0 || n >= it.n1) continue;
+                                const int slot = (base + (n - it.n0)) % NS;
+                                const uint32_t d = tmem + (uint32_t)(slot * kTmemCols);
+#pragma unroll
+                                for (int u = 0; u < 3; ++u) {
+                                    const int tap = (dz + 1) * 9 + (dy + 1) * 3 + u;
+                                    const uint32_t abase = sbase + (uint32_t)(u * kBox);
+                                    const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * 2048);
+#pragma unroll
+                                    for (int k = 0; k < 2; ++k) {
+                                        const uint64_t ad = sdesc_sw64(abase + (uint32_t)(k * 32), 16, 512);
+                                        const uint64_t bd = sdesc_sw64(bbase + (uint32_t)(k * 32), 16, 512);
+                                        mma_bf16(d, ad, bd, idesc, (first[slot] && k == 0) ? 0u : 1u);
+                                        first[slot] = false;
+                                    }
+                                }
+                            }
+                            mma_commit(&empty[st]);
+                        }
+                        if (!ok) break;
                     }
-                    mma_commit(&empty[st]);
+                    // after input i, output i - 1 has all its contributions
+                    if (i - 1 >= it.n0 && i - 1 < it.n1) mma_commit(&acc_full[(base + (i - 1 - it.n0)) % NS]);
                 }
-                if (!ok) break;
-                mma_commit(&acc_full[acc]);
+                seq = base + (it.n1 - it.n0);
             }
-            mma_commit(mma_done);   // arrives once every MMA issued above has completed
+            mma_commit(mma_done);
         }
     } else {
-        // epilogue warps 2-5: warp w reads TMEM lanes 32 (w % 4) .. +31 = accumulator rows
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        int t = 0;
-        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++t) {
-            const int acc = t & 1;
-            const bool ready = mbar_wait(&acc_full[acc], (uint32_t)(t >> 1) & 1u);
-            if (!ready || *abort_flag) {
-                if (!ready) { *abort_flag = 1; atomicExch(a.err, 4); }
-                break;
-            }
-            __syncwarp();
-            tc_fence_after();
-            float v[32];
-            tmem_load<32>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * kTmemCols), v);
-            tc_fence_before();
-            mbar_arrive(&acc_empty[acc]);
-            const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
-            const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
-            const int yy = y0 + (row >> 6), xx = row & 63;
-            const size_t vox = (((size_t)b * a.D + z) * a.H + yy) * a.W + xx;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                float x = v[c];
-                if (c < a.c_out) {
-                    if (a.bias) x += __ldg(a.bias + c);
-                } else {
-                    x = 0.0f;
+        int seq = 0;
+        bool live = true;
+        for (int item = blockIdx.x; item < n_items && live; item += gridDim.x) {
+            ChainItem it;
+            if (!chain_item(a, item, Q, it)) continue;
+            for (int n = it.n0; n < it.n1; ++n, ++seq) {
+                const int slot = seq % NS;
+                const bool ready = mbar_wait(&acc_full[slot], (uint32_t)(seq / NS) & 1u);
+                if (!ready || *abort_flag) {
+                    if (!ready) { *abort_flag = 1; atomicExch(a.err, 4); }
+                    live = false;
+                    break;
                 }
-                v[c] = x;
-            }
-            if (a.mask_src) {
-                const uint4* mp = reinterpret_cast<const uint4*>(a.mask_src) + vox * 4;
+                __syncwarp();
+                tc_fence_after();
+                float v[32];
+                tmem_load<32>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * kTmemCols), v);
+                tc_fence_before();
+                mbar_arrive(&acc_empty[slot]);
+                const int z = it.r + n * a.dil;
+                const int yy = it.y0 + (row >> 6), xx = row & 63;
+                const size_t vox = (((size_t)it.b * a.D + z) * a.H + yy) * a.W + xx;
 #pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    const uint4 m = __ldg(mp + q4);
-                    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (!(__bfloat162float(mb[e]) > 0.0f)) v[q4 * 8 + e] *= a.slope;
+                for (int c = 0; c < 32; ++c) {
+                    float x = v[c];
+                    if (c < a.c_out) {
+                        if (a.bias) x += __ldg(a.bias + c);
+                    } else {
+                        x = 0.0f;
+                    }
+                    v[c] = x;
                 }
-            }
-            if (a.act == 1) {
+                if (a.mask_src) {
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask_src) + vox * 4;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) v[c] = v[c] > 0.0f ? v[c] : a.slope * v[c];
-            }
-            if (a.y) {
-                uint4* yp = reinterpret_cast<uint4*>(a.y) + vox * 4;
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const uint4 m = __ldg(mp + q4);
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
 #pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    uint4 o;
-                    __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) ob[e] = __floats2bfloat162_rn(v[q4 * 8 + 2 * e], v[q4 * 8 + 2 * e + 1]);
-                    yp[q4] = o;
+                        for (int e = 0; e < 8; ++e)
+                            if (!(__bfloat162float(mb[e]) > 0.0f)) v[q4 * 8 + e] *= a.slope;
+                    }
                 }
+                if (a.act == 1) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = v[c] > 0.0f ? v[c] : a.slope * v[c];
+                }
+                if (a.y) {
+                    uint4* yp = reinterpret_cast<uint4*>(a.y) + vox * 4;
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        uint4 o;
+                        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) ob[e] = __floats2bfloat162_rn(v[q4 * 8 + 2 * e], v[q4 * 8 + 2 * e + 1]);
+                        yp[q4] = o;
+                    }
+                }
+                if (a.y_f32) a.y_f32[vox] = v[0];
             }
-            if (a.y_f32) a.y_f32[vox] = v[0];
         }
     }
     tc_fence_before();
@@ -371,7 +421,7 @@ __global__ void __launch_bounds__(kConvThreads, kConvCtas) k_conv3d_tc(const __g
         if (!mbar_wait(mma_done, 0) && lane == 0) atomicExch(a.err, 11);
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NS * kTmemCols)
                      : "memory");
     }
 }
@@ -560,7 +610,7 @@ cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
     if (!make_map(&map, c.x, c.B, c.D, c.H, c.W)) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvBytes);
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, kChainBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -575,12 +625,14 @@ cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
     a.dil = c.dil;
     a.act = c.act;
     a.slope = c.slope;
-    a.n_tiles = c.B * c.D * (c.H / 2);
     a.err = c.err;
-    int grid = kConvCtas * sm_count();
-    if (grid > a.n_tiles) grid = a.n_tiles;
+    const int Q = ((c.D + c.dil - 1) / c.dil + kChainMax - 1) / kChainMax;
+    const long long items = (long long)c.B * Q * c.dil * (c.H / 2);
+    if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int grid = kChainCtas * sm_count();
+    if (grid > items) grid = (int)items;
     if (grid < 1) return cudaSuccess;
-    k_conv3d_tc<<<grid, kConvThreads, kConvBytes, st>>>(map, a);
+    k_conv3d_chain<<<grid, kConvThreads, kChainBytes, st>>>(map, a, (int)items, Q);
     return cudaGetLastError();
 }
 
