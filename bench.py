@@ -465,15 +465,35 @@ def native_arm(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+    # the same calls pipelined (rt_advance_host_async): step i+1's inputs move in and step i-1's
+    # field moves out while step i marches; two alternating host output buffers, K steps
+    # between one pair of events (pipeline fill and drain included)
+    houts = [hout, torch.empty(p.j.shape, dtype=torch.float32).pin_memory()]
+    for i in range(max(1, args.warmup)):
+        g.advance_host_async(hj, hk, hs, p.num_rays, p.step_size, p.radiation_velocity, p.time_step,
+                             out=houts[i & 1], stream=stream)
+    g.host_wait()
+    flush.fill_(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        g.advance_host_async(hj, hk, hs, p.num_rays, p.step_size, p.radiation_velocity, p.time_step,
+                             out=houts[i & 1], stream=stream)
+    g.host_join(stream)
+    e1.record(stream)
+    e1.synchronize()
+    g.host_wait()
+    pipe_ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
 
     ms = statistics.mean(step_ms)
     kms = statistics.mean(kern_ms)
     ems = statistics.mean(e2e_ms)
     if world > 1:
-        t = torch.tensor([ms, kms, ems], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, kms, ems, pipe_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, kms, ems = t.tolist()
+        ms, kms, ems, pipe_ms = t.tolist()
 
     peak, peak_kind, _ = load_peaks()
     achieved = ALGO_BYTES_PER_UPDATE * U / (kms * 1e-3) / 1e9
@@ -493,8 +513,14 @@ def native_arm(args):
                      "traffic": traffic, "peak_kind": peak_kind,
                      "basis": f"{ALGO_BYTES_PER_UPDATE} algorithmic bytes per update x {U} updates per launch / "
                               "march-kernel CUDA-event time"},
-        "e2e": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": ems},
+        "e2e": {"value": world * U / (pipe_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": pipe_ms,
+                "api": "rt_advance_host_async x K steps, one event pair around all K (fill and drain included)",
+                "l2": "not flushed inside the pipeline; each step copies its 67 MB of inputs in and 34 MB out, "
+                      "alternating two device buffer sets (per-step footprint with packing ~200 MB > L2)"},
+        "e2e_serial": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": ems,
+                       "api": "rt_advance_host (copy in, march, copy out, synchronise) per step, L2 flushed before each"},
         "gpu_launches": 4 * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},

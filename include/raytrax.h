@@ -166,6 +166,31 @@ rt_status rt_advance_host(rt_grid* grid, const float* j_map, const float* kappa_
                           float step_size, float radiation_velocity, float time_step, int n_freq,
                           float* out_field, void* cuda_stream);
 
+/* Pipelined rt_advance_host: same arguments and field, but the call only ENQUEUES the work and
+   returns. Three streams overlap consecutive calls: the inputs are copied in on a copy stream of
+   the handle, the march runs on cuda_stream, the field is copied out on a second copy stream of
+   the handle; two sets of device buffers alternate, so call i+1's inputs move in and call i-1's
+   field moves out while call i marches. Calls complete in order. The host buffers must stay
+   valid, and the inputs unmodified, until rt_host_wait returns (or until a stream joined with
+   rt_host_join has passed the join); the field is in out_field only then. Consecutive calls may
+   pass the same out_field (its copies land in call order). Pinned (page-locked) host buffers are
+   needed for the copies to overlap anything; pageable ones work but serialise. The handle's
+   other entry points share its march scratch: on the same cuda_stream they are ordered after
+   the enqueued marches; on another stream, call rt_host_wait first. Errors of the enqueued work
+   surface in rt_host_wait. */
+rt_status rt_advance_host_async(rt_grid* grid, const float* j_map, const float* kappa_map,
+                                const float* source_pos, int num_sources, int num_rays,
+                                float step_size, float radiation_velocity, float time_step,
+                                int n_freq, float* out_field, void* cuda_stream);
+
+/* Block until every rt_advance_host_async call of this handle has finished, including its
+   copy to the host; RT_ERR_CUDA if any of that work failed. */
+rt_status rt_host_wait(rt_grid* grid);
+
+/* Make cuda_stream (NULL: legacy default stream) wait, on the device, for every
+   rt_advance_host_async call enqueued so far; the host does not block. */
+rt_status rt_host_join(rt_grid* grid, void* cuda_stream);
+
 /* Reverse-mode adjoint of rt_advance (the Jacobians w.r.t. (j, kappa) of Sec. 4,
    "Coupling to differentiable hydro"). Given grad_out = dL/d(out_field) (device,
    [n_freq][n0][n1][n2]) and the forward's inputs, writes dL/dj to grad_j and dL/dkappa

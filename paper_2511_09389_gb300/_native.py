@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ER
 
 # every symbol include/raytrax.h declares
 EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
-           "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_continue", "rt_advance_host", "rt_backward",
+           "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_continue", "rt_advance_host",
+           "rt_advance_host_async", "rt_host_wait", "rt_host_join", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
@@ -86,6 +87,12 @@ def load(path: str = LIB_PATH):
         lib.rt_advance_continue.restype = i
         lib.rt_advance_host.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, vp]
         lib.rt_advance_host.restype = i
+        lib.rt_advance_host_async.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, fp, vp]
+        lib.rt_advance_host_async.restype = i
+        lib.rt_host_wait.argtypes = [vp]
+        lib.rt_host_wait.restype = i
+        lib.rt_host_join.argtypes = [vp, vp]
+        lib.rt_host_join.restype = i
         lib.rt_backward.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, vp]
         lib.rt_backward.restype = i
         lib.rt_backward_sources.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, fp, vp]

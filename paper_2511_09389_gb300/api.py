@@ -79,6 +79,7 @@ class Grid:
         with torch.cuda.device(self.device):
             check(self._lib.rt_create_grid(ctypes.byref(h), *self.shape, self.max_freq, ctypes.byref(opt)))
         self._h = h
+        self._inflight = []   # host buffers of enqueued advance_host_async calls
 
     # -- lifetime -------------------------------------------------------------------------
     def close(self):
@@ -163,10 +164,8 @@ class Grid:
         check(st)
         return out
 
-    def advance_host(self, j: np.ndarray, kappa: np.ndarray, sources: np.ndarray, num_rays: int,
-                     step_size: float, radiation_velocity: float = 1.0, time_step: float = 1.0, *,
-                     out: np.ndarray | None = None, stream=None) -> np.ndarray:
-        """rt_advance_host: host (numpy / pinned torch CPU) buffers in, host field out, synchronous."""
+    def _host_call(self, fn, j, kappa, sources, num_rays, step_size, radiation_velocity, time_step, out,
+                   stream):
         def host(a, name):
             if isinstance(a, torch.Tensor):
                 if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
@@ -188,11 +187,41 @@ class Grid:
         if tuple(oshape) != tuple(jshape):
             raise ValueError("out has the wrong shape")
         with torch.cuda.device(self.device):
-            st = self._lib.rt_advance_host(self._h, jp, kp, spp, nsrc, int(num_rays), float(step_size),
-                                           float(radiation_velocity), float(time_step), jshape[0], op,
-                                           _stream_ptr(stream, self.device))
+            st = fn(self._h, jp, kp, spp, nsrc, int(num_rays), float(step_size), float(radiation_velocity),
+                    float(time_step), jshape[0], op, _stream_ptr(stream, self.device))
         check(st)
+        return oh, (jh, kh, sh, oh)
+
+    def advance_host(self, j: np.ndarray, kappa: np.ndarray, sources: np.ndarray, num_rays: int,
+                     step_size: float, radiation_velocity: float = 1.0, time_step: float = 1.0, *,
+                     out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """rt_advance_host: host (numpy / pinned torch CPU) buffers in, host field out, synchronous."""
+        oh, _ = self._host_call(self._lib.rt_advance_host, j, kappa, sources, num_rays, step_size,
+                                radiation_velocity, time_step, out, stream)
         return oh
+
+    def advance_host_async(self, j, kappa, sources, num_rays: int, step_size: float,
+                           radiation_velocity: float = 1.0, time_step: float = 1.0, *, out=None, stream=None):
+        """rt_advance_host_async: enqueue one host-buffer advance and return at once; the field is
+        in the returned buffer (``out`` if given) after :meth:`host_wait`. Consecutive calls overlap
+        their copies with the march of their neighbours when the host buffers are pinned. The
+        handle keeps references to the buffers until :meth:`host_wait`."""
+        oh, keep = self._host_call(self._lib.rt_advance_host_async, j, kappa, sources, num_rays, step_size,
+                                   radiation_velocity, time_step, out, stream)
+        self._inflight.append(keep)
+        return oh
+
+    def host_wait(self) -> None:
+        """rt_host_wait: block until every :meth:`advance_host_async` call has landed on the host."""
+        with torch.cuda.device(self.device):
+            st = self._lib.rt_host_wait(self._h)
+        self._inflight.clear()
+        check(st)
+
+    def host_join(self, stream=None) -> None:
+        """rt_host_join: make ``stream`` wait on the device for the enqueued host calls."""
+        with torch.cuda.device(self.device):
+            check(self._lib.rt_host_join(self._h, _stream_ptr(stream, self.device)))
 
     # -- adjoint --------------------------------------------------------------------------
     def backward(self, grad_out, j, kappa, sources, num_rays: int, step_size: float,

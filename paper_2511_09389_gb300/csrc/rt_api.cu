@@ -133,7 +133,8 @@ struct rt_grid {
     int device = 0;
     std::vector<DirTable> dirs;
     // scratch slots
-    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, CHK, NSLOT };
+    enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, CHK,
+                AJ0, AK0, AOUT0, ASRC0, AJ1, AK1, AOUT1, ASRC1, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -160,6 +161,13 @@ struct rt_grid {
         int nsrc = 0, rays = 0, ns = 0, n_freq = 0, stride = 0, W = 0, kappa_mode = 0;
         float ds = 0.0f;
     } rec;
+    // pipelined host calls (rt_advance_host_async): a copy-in and a copy-out stream, and per
+    // buffer set the events that order its reuse
+    struct HostPipe {
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t in_ready[2] = {}, done[2] = {}, out_done[2] = {};
+        long long calls = 0;
+    } pipe;
     struct ContinueState {
         bool valid = false;
         int nsrc = 0, rays = 0, n_freq = 0, parity = 0;
@@ -224,6 +232,14 @@ struct rt_grid {
         cudaDeviceSynchronize();
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        for (int i = 0; i < 2; ++i) {
+            if (pipe.in_ready[i]) cudaEventDestroy(pipe.in_ready[i]);
+            if (pipe.done[i]) cudaEventDestroy(pipe.done[i]);
+            if (pipe.out_done[i]) cudaEventDestroy(pipe.out_done[i]);
+        }
+        if (pipe.h2d) cudaStreamDestroy(pipe.h2d);
+        if (pipe.d2h) cudaStreamDestroy(pipe.d2h);
+        pipe = HostPipe{};
         for (auto& t : dirs) cudaFree(t.d);
         dirs.clear();
         for (int s = 0; s < NSLOT; ++s) {
@@ -745,6 +761,80 @@ rt_status rt_advance_host(rt_grid* g, const float* j_map, const float* kappa_map
     if ((st = advance_impl(g, a)) != RT_OK) return st;
     RT_CUDA(cudaMemcpyAsync(out_field, dout, field, cudaMemcpyDeviceToHost, s), "copy field to host");
     RT_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return RT_OK;
+}
+
+rt_status rt_advance_host_async(rt_grid* g, const float* j_map, const float* kappa_map, const float* source_pos,
+                                int num_sources, int num_rays, float step_size, float radiation_velocity,
+                                float time_step, int n_freq, float* out_field, void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (n_freq < 1 || n_freq > g->max_freq)
+        return fail(RT_ERR_INVALID_ARG, "n_freq = %d outside [1, max_freq = %d]", n_freq, g->max_freq);
+    if (num_sources < 0) return fail(RT_ERR_INVALID_ARG, "num_sources must be >= 0");
+    if (!j_map || !kappa_map || !out_field || (num_sources > 0 && !source_pos))
+        return fail(RT_ERR_INVALID_ARG, "host buffers must be non-NULL");
+    rt_status st = check_device(g);
+    if (st != RT_OK) return st;
+    auto& P = g->pipe;
+    if (!P.h2d) {
+        RT_CUDA(cudaStreamCreateWithFlags(&P.h2d, cudaStreamNonBlocking), "cudaStreamCreate(copy in)");
+        RT_CUDA(cudaStreamCreateWithFlags(&P.d2h, cudaStreamNonBlocking), "cudaStreamCreate(copy out)");
+        for (int i = 0; i < 2; ++i) {
+            RT_CUDA(cudaEventCreateWithFlags(&P.in_ready[i], cudaEventDisableTiming), "cudaEventCreate");
+            RT_CUDA(cudaEventCreateWithFlags(&P.done[i], cudaEventDisableTiming), "cudaEventCreate");
+            RT_CUDA(cudaEventCreateWithFlags(&P.out_done[i], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int b = (int)(P.calls & 1);
+    const rt_grid::Slot sj = b ? rt_grid::AJ1 : rt_grid::AJ0, sk = b ? rt_grid::AK1 : rt_grid::AK0;
+    const rt_grid::Slot so = b ? rt_grid::AOUT1 : rt_grid::AOUT0, ss = b ? rt_grid::ASRC1 : rt_grid::ASRC0;
+    const size_t field = sizeof(float) * (size_t)n_freq * g->ncell();
+    const size_t srcb = sizeof(float) * 3 * (size_t)std::max(num_sources, 1);
+    // growing a buffer set frees memory that enqueued copies may still use: drain the pipeline
+    if (g->cap[sj] < field || g->cap[sk] < field || g->cap[so] < field || g->cap[ss] < srcb)
+        if ((st = rt_host_wait(g)) != RT_OK) return st;
+    void *dj, *dk, *dout, *dsrc;
+    if ((st = g->ensure(sj, field, &dj)) != RT_OK) return st;
+    if ((st = g->ensure(sk, field, &dk)) != RT_OK) return st;
+    if ((st = g->ensure(so, field, &dout)) != RT_OK) return st;
+    if ((st = g->ensure(ss, srcb, &dsrc)) != RT_OK) return st;
+    // copy in once the march two calls back has read this set (an unrecorded event is complete)
+    RT_CUDA(cudaStreamWaitEvent(P.h2d, P.done[b], 0), "cudaStreamWaitEvent");
+    RT_CUDA(cudaMemcpyAsync(dj, j_map, field, cudaMemcpyHostToDevice, P.h2d), "copy j to device");
+    RT_CUDA(cudaMemcpyAsync(dk, kappa_map, field, cudaMemcpyHostToDevice, P.h2d), "copy kappa to device");
+    if (num_sources > 0)
+        RT_CUDA(cudaMemcpyAsync(dsrc, source_pos, sizeof(float) * 3 * (size_t)num_sources,
+                                cudaMemcpyHostToDevice, P.h2d), "copy sources to device");
+    RT_CUDA(cudaEventRecord(P.in_ready[b], P.h2d), "cudaEventRecord");
+    // march once the inputs are in and the field of two calls back has left this set
+    RT_CUDA(cudaStreamWaitEvent(s, P.in_ready[b], 0), "cudaStreamWaitEvent");
+    RT_CUDA(cudaStreamWaitEvent(s, P.out_done[b], 0), "cudaStreamWaitEvent");
+    Call a{(const float*)dj, (const float*)dk, (const float*)dsrc, num_sources, num_rays, 0, num_rays,
+           step_size, radiation_velocity, time_step, n_freq, (float*)dout, 0, s};
+    if ((st = advance_impl(g, a)) != RT_OK) return st;
+    RT_CUDA(cudaEventRecord(P.done[b], s), "cudaEventRecord");
+    RT_CUDA(cudaStreamWaitEvent(P.d2h, P.done[b], 0), "cudaStreamWaitEvent");
+    RT_CUDA(cudaMemcpyAsync(out_field, dout, field, cudaMemcpyDeviceToHost, P.d2h), "copy field to host");
+    RT_CUDA(cudaEventRecord(P.out_done[b], P.d2h), "cudaEventRecord");
+    ++P.calls;
+    return RT_OK;
+}
+
+rt_status rt_host_wait(rt_grid* g) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (!g->pipe.d2h) return RT_OK;
+    // the last copy out waits for every march and copy in before it
+    RT_CUDA(cudaStreamSynchronize(g->pipe.h2d), "cudaStreamSynchronize(copy in)");
+    RT_CUDA(cudaStreamSynchronize(g->pipe.d2h), "cudaStreamSynchronize(copy out)");
+    return RT_OK;
+}
+
+rt_status rt_host_join(rt_grid* g, void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (!g->pipe.d2h || g->pipe.calls == 0) return RT_OK;
+    const int last = (int)((g->pipe.calls - 1) & 1);
+    RT_CUDA(cudaStreamWaitEvent((cudaStream_t)cuda_stream, g->pipe.out_done[last], 0), "cudaStreamWaitEvent");
     return RT_OK;
 }
 
