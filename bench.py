@@ -282,8 +282,9 @@ def paper_workload(args, dev, flush, stream):
 
 
 def _batch_vs_one_by_one(probs, args, dev, stream):
-    """One autotuned persistent launch of all instances replayed from a CUDA graph, against the
-    same instances advanced one autotuned rt_advance call at a time (mean ms of each)."""
+    """One autotuned batch (dedicated launches for instances that fill the GPU, persistent
+    kernels for the rest) replayed from a CUDA graph, against the same instances advanced one
+    autotuned rt_advance call at a time (mean ms of each)."""
     import statistics as st
     import torch
     from paper_2511_09389_gb300.api import Batch, Grid
@@ -335,7 +336,7 @@ def _batch_vs_one_by_one(probs, args, dev, stream):
 def batched(args, dev, stream):
     """64 independent instances (edges from {32,48,64,96,128,160}, lognormal kappa with sigma_g in
     [0.5, 1.5], 1-64 sources, N_Omega from {768, 3072, 12288}, ds 0.5, c dt = edge, 1-8 bins):
-    one autotuned persistent launch replayed from a CUDA graph, against the same instances
+    one autotuned batch replayed from a CUDA graph, against the same instances
     advanced one rt_advance call at a time. The inputs (2.6 GB) exceed L2, so no flush. Beside
     it, 256 small instances (edges {16, 24, 32}, 1-4 sources, N_Omega {192, 768}, 1-2 bins), where
     one call per instance is bound by launch and host overheads."""

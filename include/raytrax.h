@@ -271,10 +271,15 @@ typedef struct {
 } rt_instance;
 
 /* Validate the instances, allocate the batch's scratch (packed copies, accumulators, lattice
-   tables, work queue) and build the work queue of 32-ray items (longest first). The buffers
-   named in inst[] are bound to the batch: each rt_batch_run reads and writes them in place.
-   opt: kappa_mode is honoured; autotune = 1 times the persistent block sizes on the first run.
-   Same results as one rt_advance per instance. */
+   tables, work queue) and split the instances in two. An instance with at least
+   RT_BATCH_DEDICATED_LANES (source, ray, bin group) lanes fills the GPU alone: it gets its own
+   pack / march / unpack launches with a single-call launch plan. The others share persistent
+   march kernels fed by work queues of 32-ray items (longest first), in waves whose packed
+   inputs and accumulators fit in half the L2 cache. The buffers named in inst[] are bound to
+   the batch: each rt_batch_run reads and writes them in place. opt: kappa_mode is honoured;
+   autotune = 1 times, on the first run, the launch plans of the dedicated instances and the
+   persistent block sizes. Same results as one rt_advance per instance. */
+#define RT_BATCH_DEDICATED_LANES 19456
 rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, const rt_options* opt);
 
 /* Advance every instance by its dt on the stream. The first call (optionally autotunes and)
@@ -290,6 +295,14 @@ rt_status rt_advance_batch(rt_grid* grid, const rt_instance* inst, int n_inst, v
 
 /* Total updates (substeps x rays x sources x bins over all instances) of one run. */
 long long rt_batch_updates(const rt_batch* batch);
+
+/* How instance `instance` (its index in rt_batch_create's array) is marched: *dedicated = 1
+   for its own launches, then *width, *block, *prefetch, *tile give its plan (as rt_last_plan;
+   final after the first rt_batch_run when autotuning); *dedicated = 0 for the persistent
+   kernels, then *width = its bin-group width, *block = the persistent block size, *prefetch =
+   *tile = 0. Any output may be NULL. RT_ERR_INVALID_ARG for a bad batch or index. */
+rt_status rt_batch_info(const rt_batch* batch, int instance, int* dedicated, int* width, int* block,
+                        int* prefetch, int* tile);
 
 /* Free the batch (synchronises the device). NULL is accepted. */
 rt_status rt_batch_destroy(rt_batch* batch);

@@ -21,6 +21,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_advance_host_async", "rt_host_wait", "rt_host_join", "rt_backward",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
+           "rt_batch_info",
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
            "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_c32_channel_mean",
@@ -114,6 +115,9 @@ def load(path: str = LIB_PATH):
         lib.rt_batch_run.restype = i
         lib.rt_batch_updates.argtypes = [vp]
         lib.rt_batch_updates.restype = ctypes.c_longlong
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.rt_batch_info.argtypes = [vp, i, ip, ip, ip, ip, ip]
+        lib.rt_batch_info.restype = i
         lib.rt_batch_destroy.argtypes = [vp]
         lib.rt_batch_destroy.restype = i
         lib.rt_c32_from_f32.argtypes = [vp, i, i, i, i, i, vp, vp]

@@ -325,6 +325,14 @@ class Batch:
     def updates(self) -> int:
         return int(self._lib.rt_batch_updates(self._h))
 
+    def info(self, instance: int) -> dict:
+        """rt_batch_info: how an instance is marched (its own launches or the persistent kernels)
+        and with which plan."""
+        vals = [ctypes.c_int() for _ in range(5)]
+        check(self._lib.rt_batch_info(self._h, int(instance), *[ctypes.byref(v) for v in vals]))
+        keys = ("dedicated", "bins_per_thread", "block", "gathers", "tile")
+        return {k: v.value for k, v in zip(keys, vals)}
+
     def run(self, stream=None):
         check(self._lib.rt_batch_run(self._h, _stream_ptr(stream, self.device)))
         return self.outputs

@@ -256,6 +256,28 @@ int num_substeps(float ds, float c, float dt, int cap) { return rt::substeps(ds,
 
 }  // namespace
 
+// Widths W in {the default, 2, 1} that fit n_freq; 32, 64, 128, 256 threads per block; gather
+// modes 0, 1, 2 with and without source tiles; for W = 4 also 2 and 4 lanes per ray.
+int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
+    int widths[3], nw = 0;
+    widths[nw++] = n_freq == 1 ? 1 : (n_freq == 2 ? 2 : 4);
+    if (n_freq >= 3) widths[nw++] = 2;
+    if (n_freq >= 2) widths[nw++] = 1;
+    int n = 0;
+    for (int wi = 0; wi < nw; ++wi)
+        for (int b : {32, 64, 128, 256})
+            for (int cand = 0; cand < (widths[wi] == 4 ? 8 : 6); ++cand) {
+                MarchPlan p;
+                p.W = widths[wi];
+                p.block = b;
+                p.prefetch = cand < 6 ? cand >> 1 : 0;
+                p.tile = cand < 6 ? (cand & 1) : 0;
+                p.lpr = cand >= 6 ? (cand == 6 ? 2 : 4) : 1;
+                out[n++] = p;
+            }
+    return n;
+}
+
 int rt::substeps(float ds, float c, float dt, int cap) {
     if (!std::isfinite(ds) || !std::isfinite(c) || !std::isfinite(dt)) return -1;
     if (!(ds > 0.0f) || !(c > 0.0f) || !(dt >= 0.0f)) return -1;
@@ -393,53 +415,42 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
             g->last_plan_ms = e.second.second;
             return RT_OK;
         }
-    std::vector<int> widths{pick_width(a.n_freq)};
-    if (a.n_freq >= 3) widths.push_back(2);
-    if (a.n_freq >= 2) widths.push_back(1);
-    const int blocks[] = {32, 64, 128, 256};
+    rt::MarchPlan cands[88];
+    const int n_cand = rt::march_plan_candidates(a.n_freq, cands);
     cudaEvent_t e[2] = {nullptr, nullptr};
     float best_ms = 3.0e38f;
     Plan bp;
-    bp.W = widths[0];
+    bp.W = cands[0].W;
     g->tune_report.clear();
     rt_status st = RT_OK;
     cudaError_t ce = cudaEventCreate(&e[0]);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e[1]);
     if (ce != cudaSuccess) st = cuda_fail(ce, "cudaEventCreate");
-    for (int W : widths) {
-        for (int b : blocks) {
-            for (int cand = 0; cand < (W == 4 ? 8 : 6); ++cand) {
-                if (st != RT_OK) break;
-                Plan p;
-                p.W = W; p.block = b;
-                // gather modes 0, 1, 2 with and without source tiles; W = 4 also tries split lanes
-                // (cand 6: 2 lanes, cand 7: 4 lanes per ray)
-                const int pf = cand < 6 ? cand >> 1 : 0;
-                p.prefetch = pf;
-                p.tile = cand < 6 ? (cand & 1) : 0;
-                p.lpr = cand >= 6 ? (cand == 6 ? 2 : 4) : 1;
-                rt::MarchArgs m;
-                if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
-                float cand_ms = 3.0e38f;
-                for (int rep = 0; rep < 2; ++rep) {
-                    ce = cudaMemsetAsync(m.acc, 0, acc_bytes(g, a, p), a.st);
-                    if (ce == cudaSuccess) ce = cudaEventRecord(e[0], a.st);
-                    if (ce == cudaSuccess) ce = rt::launch_march_fwd(W, m, a.st);
-                    if (ce == cudaSuccess) ce = cudaEventRecord(e[1], a.st);
-                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
-                    float ms = 0.0f;
-                    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[0], e[1]);
-                    if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune run"); break; }
-                    if (ms < cand_ms) cand_ms = ms;
-                    if (ms < best_ms) { best_ms = ms; bp = p; }
-                }
-                if (st == RT_OK) {
-                    char line[112];
-                    snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d %.4f ms\n", W, b,
-                             p.prefetch, p.lpr, p.tile, cand_ms);
-                    g->tune_report += line;
-                }
-            }
+    for (int ci = 0; ci < n_cand && st == RT_OK; ++ci) {
+        Plan p;
+        p.W = cands[ci].W; p.block = cands[ci].block; p.prefetch = cands[ci].prefetch;
+        p.lpr = cands[ci].lpr; p.tile = cands[ci].tile;
+        const int W = p.W, b = p.block;
+        rt::MarchArgs m;
+        if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
+        float cand_ms = 3.0e38f;
+        for (int rep = 0; rep < 2; ++rep) {
+            ce = cudaMemsetAsync(m.acc, 0, acc_bytes(g, a, p), a.st);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e[0], a.st);
+            if (ce == cudaSuccess) ce = rt::launch_march_fwd(W, m, a.st);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e[1], a.st);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
+            float ms = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[0], e[1]);
+            if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune run"); break; }
+            if (ms < cand_ms) cand_ms = ms;
+            if (ms < best_ms) { best_ms = ms; bp = p; }
+        }
+        if (st == RT_OK) {
+            char line[112];
+            snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d %.4f ms\n", W, b,
+                     p.prefetch, p.lpr, p.tile, cand_ms);
+            g->tune_report += line;
         }
     }
     for (auto ev : e)

@@ -2,13 +2,16 @@
 //
 // At creation the instances are validated, their scratch (packed j / kappa for instances with
 // two or more bins, one contiguous accumulator region for all) and lattice tables are
-// allocated, and the instances are grouped into waves whose working sets (packed inputs and
-// accumulator) fit in half the L2 cache. Each wave has its own work queue of 32-ray items,
-// longest first. The first run captures, per wave, batched pack, persistent march and batched
-// unpack into one CUDA graph (after an optional timing of persistent block sizes); every run
-// launches it. Packing every instance before marching any (one wave) made the march read its
-// packed grids back from DRAM: measured on GB300 with 8 copies of a 128^3, 4-bin problem,
-// 493 MB of DRAM reads per instance against 150 MB for a single call.
+// allocated. Instances with RT_BATCH_DEDICATED_LANES or more (source, ray, bin group) lanes
+// fill the GPU alone; they get their own pack / march / unpack launches with a single-call
+// plan (autotuned on the first run if asked): on GB300 the persistent kernel ran such
+// instances at 0.85x their one-by-one time. The rest are grouped into waves whose working
+// sets (packed inputs and accumulator) fit in half the L2 cache, each with its own work queue
+// of 32-ray items, longest first. The first run captures the dedicated launches and, per wave,
+// batched pack, persistent march and batched unpack into one CUDA graph; every run launches
+// it. Packing every instance before marching any (one wave) made the march read its packed
+// grids back from DRAM: measured on GB300 with 8 copies of a 128^3, 4-bin problem, 493 MB of
+// DRAM reads per instance against 150 MB for a single call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,6 +66,21 @@ struct rt_batch {
         int w_count[3] = {0, 0, 0};
     };
     std::vector<Wave> waves;
+    // an instance marched by its own launches: its position in host / d_insts and its plan
+    struct Dedicated {
+        int inst = 0;
+        int W = 1;                    // bin-group width of its march (its scratch fits any width
+                                      // up to the instance's own: groups * W never grows)
+        int block = 32, prefetch = 0, tile = 0, lpr = 1;
+    };
+    std::vector<Dedicated> ded;
+    // dedicated instances whose working sets together fit in half the L2 cache run as
+    // concurrent branches (up to three): [first, first + count) of ded
+    struct DedGroup {
+        int first = 0, count = 0;
+    };
+    std::vector<DedGroup> ded_groups;
+    std::vector<int> pos;             // caller's instance index -> position in host / d_insts
     int* d_counter = nullptr;         // one counter per wave and width
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
@@ -112,9 +130,107 @@ struct rt_batch {
         return RT_OK;
     }
 
+    rt::MarchArgs dedicated_args(const Dedicated& d) const {
+        const rt::BatchInst& b = host[d.inst];
+        rt::MarchArgs m{};
+        if (d.W == 1) { m.jp = b.j; m.kp = b.kappa; }
+        else { m.jp = b.jp_w; m.kp = b.kp_w; }
+        m.acc = b.acc;
+        m.dirs = b.dirs; m.src = b.src;
+        m.n0 = b.n0; m.n1 = b.n1; m.n2 = b.n2;
+        m.ns = b.ns; m.ds = b.ds;
+        m.dep_scale = 1.0f;           // 4 pi / N_Omega applied by the unpack, as for the waves
+        m.ray_count = b.ray_count; m.nsrc = b.nsrc;
+        m.groups = (b.n_freq + d.W - 1) / d.W; m.n_freq = b.n_freq; m.kappa_mode = b.kappa_mode;
+        m.block = d.block; m.prefetch = d.prefetch; m.lanes_per_ray = d.lpr; m.tile = d.lpr == 1 ? d.tile : 0;
+        return m;
+    }
+
+    rt_status pack_dedicated(const Dedicated& d, cudaStream_t st) {
+        const rt::BatchInst& b = host[d.inst];
+        if (d.W == 1) return RT_OK;
+        const long long ncell = (long long)b.n0 * b.n1 * b.n2;
+        const int groups = (b.n_freq + d.W - 1) / d.W;
+        B_CUDA(rt::launch_pack(b.j, b.jp_w, b.n_freq, d.W, groups, ncell, st), "pack(j) launch");
+        B_CUDA(rt::launch_pack(b.kappa, b.kp_w, b.n_freq, d.W, groups, ncell, st), "pack(kappa) launch");
+        return RT_OK;
+    }
+
+    // One bin per thread deposits straight into the caller's field with the 4 pi / N_Omega factor,
+    // as a single call does; wider groups go through the packed accumulator and the unpack.
+    rt_status run_dedicated(const Dedicated& d, cudaStream_t st) {
+        const rt::BatchInst& b = host[d.inst];
+        const long long ncell = (long long)b.n0 * b.n1 * b.n2;
+        rt_status rs = pack_dedicated(d, st);
+        if (rs != RT_OK) return rs;
+        rt::MarchArgs m = dedicated_args(d);
+        if (d.W == 1) {
+            B_CUDA(cudaMemsetAsync(b.out, 0, sizeof(float) * (size_t)b.n_freq * ncell, st), "clear field");
+            m.acc = b.out;
+            m.dep_scale = b.scale;
+        }
+        B_CUDA(rt::launch_march_fwd(d.W, m, st), "march launch");
+        if (d.W > 1)
+            B_CUDA(rt::launch_unpack(b.acc, b.out, b.n_freq, d.W, ncell, b.scale, 0, st), "unpack launch");
+        return RT_OK;
+    }
+
+    // Time the single-call tuner's candidate plans (rt::march_plan_candidates) for one dedicated
+    // instance's march on its own inputs and keep the best. Its scratch, sized for its own
+    // width, holds the packed copies of every narrower width.
+    rt_status tune_dedicated(Dedicated& d, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+        const rt::BatchInst& b = host[d.inst];
+        const size_t accb = sizeof(float) * (size_t)b.groups * b.n0 * b.n1 * b.n2 * b.W;
+        rt::MarchPlan cands[88];
+        const int n = rt::march_plan_candidates(b.n_freq, cands);
+        float best = 3.0e38f;
+        Dedicated win = d;
+        int packed_w = 0;
+        for (int ci = 0; ci < n; ++ci) {
+            Dedicated c = d;
+            c.W = cands[ci].W; c.block = cands[ci].block; c.prefetch = cands[ci].prefetch;
+            c.tile = cands[ci].tile; c.lpr = cands[ci].lpr;
+            if (c.W > b.W) continue;
+            if (c.W != packed_w) {
+                rt_status rs = pack_dedicated(c, st);
+                if (rs != RT_OK) return rs;
+                packed_w = c.W;
+            }
+            const rt::MarchArgs m = dedicated_args(c);
+            float ms = 3.0e38f;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run warms the caches
+                B_CUDA(cudaMemsetAsync(b.acc, 0, accb, st), "clear accumulator");
+                B_CUDA(cudaEventRecord(e0, st), "cudaEventRecord");
+                B_CUDA(rt::launch_march_fwd(c.W, m, st), "march launch");
+                B_CUDA(cudaEventRecord(e1, st), "cudaEventRecord");
+                B_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+                B_CUDA(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            }
+            if (ms < best) { best = ms; win = c; }
+        }
+        d = win;
+        return RT_OK;
+    }
+
     rt_status enqueue(cudaStream_t st) {
-        B_CUDA(cudaMemsetAsync(d_counter, 0, 3 * waves.size() * sizeof(int), st), "clear work counters");
+        B_CUDA(cudaMemsetAsync(d_counter, 0, 3 * std::max<size_t>(waves.size(), 1) * sizeof(int), st),
+               "clear work counters");
         B_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, st), "clear accumulators");
+        for (const DedGroup& dg : ded_groups) {
+            cudaStream_t on[3] = {st, side[0], side[1]};
+            if (dg.count > 1) {
+                B_CUDA(cudaEventRecord(fork, st), "fork");
+                for (int i = 1; i < dg.count; ++i) B_CUDA(cudaStreamWaitEvent(on[i], fork, 0), "fork wait");
+            }
+            for (int i = 0; i < dg.count; ++i) {
+                rt_status rs = run_dedicated(ded[dg.first + i], on[i]);
+                if (rs != RT_OK) return rs;
+            }
+            for (int i = 1; i < dg.count; ++i) {
+                B_CUDA(cudaEventRecord(join[i - 1], on[i]), "join");
+                B_CUDA(cudaStreamWaitEvent(st, join[i - 1], 0), "join wait");
+            }
+        }
         for (size_t wi = 0; wi < waves.size(); ++wi) {
             const Wave& w = waves[wi];
             const rt::BatchInst* in = d_insts + w.first_inst;
@@ -186,12 +302,23 @@ rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, c
         const double field = 4.0 * h[i].groups * (double)h[i].n0 * h[i].n1 * h[i].n2 * h[i].W;
         footprint[i] = 3.0 * field;   // j and kappa (packed, or the caller's arrays) and the accumulator
     }
+    // dedicated instances first (largest working set first), then the wave instances
+    std::vector<char> dedicated(n_inst);
+    int n_ded = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const long long lanes = (long long)h[i].nsrc * h[i].ray_count * h[i].groups;
+        dedicated[i] = lanes >= RT_BATCH_DEDICATED_LANES;
+        n_ded += dedicated[i];
+    }
     std::vector<int> order(n_inst);
     for (int i = 0; i < n_inst; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return footprint[a] > footprint[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (dedicated[a] != dedicated[b]) return dedicated[a] > dedicated[b];
+        return footprint[a] > footprint[b];
+    });
     std::vector<rt_batch::Wave> waves;
     double wave_bytes = 0.0;
-    for (int k = 0; k < n_inst; ++k) {
+    for (int k = n_ded; k < n_inst; ++k) {
         const int i = order[k];
         if (waves.empty() || (wave_bytes + footprint[i] > budget && waves.back().n_inst > 0)) {
             rt_batch::Wave w;
@@ -214,6 +341,28 @@ rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, c
     B->opt = o;
     B->updates = updates;
     B->waves = waves;
+    B->pos.assign(n_inst, 0);
+    for (int k = 0; k < n_inst; ++k) B->pos[order[k]] = k;
+    {
+        double group_bytes = 0.0;
+        for (int k = 0; k < n_ded; ++k) {
+            const double fp = footprint[order[k]];
+            if (B->ded_groups.empty() || B->ded_groups.back().count == 3 || group_bytes + fp > budget) {
+                B->ded_groups.push_back(rt_batch::DedGroup{k, 0});
+                group_bytes = 0.0;
+            }
+            B->ded_groups.back().count++;
+            group_bytes += fp;
+        }
+    }
+    for (int k = 0; k < n_ded; ++k) {
+        rt_batch::Dedicated d;
+        d.inst = k;
+        d.W = h[k].W;
+        d.prefetch = h[k].W == 1 ? 1 : 0;   // the single-call default plan
+        d.tile = h[k].W == 1 ? 1 : 0;
+        B->ded.push_back(d);
+    }
     auto fail_free = [&](rt_status st) { B->release(); delete B; return st; };
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device);
@@ -279,7 +428,7 @@ rt_status rt_batch_create(rt_batch** out, const rt_instance* inst, int n_inst, c
     if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(int4) * std::max<size_t>(items.size(), 1));
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpy(B->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, 3 * B->waves.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, 3 * std::max<size_t>(B->waves.size(), 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&B->side[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
@@ -299,14 +448,18 @@ rt_status rt_batch_run(rt_batch* B, void* cuda_stream) {
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!B->exec) {
         if (B->opt.autotune) {
-            // time the persistent march for a few block sizes on the real inputs (untimed clears)
+            // plans of the dedicated instances, then the persistent march for a few block sizes,
+            // timed on the real inputs (untimed clears)
             cudaEvent_t e0, e1;
             B_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
             B_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
             float best = 3.0e38f;
             int best_block = B->block;
             rt_status rs = RT_OK;
+            for (auto& d : B->ded)
+                if (rs == RT_OK) rs = B->tune_dedicated(d, B->cap, e0, e1);
             for (int blk : {32, 64, 128, 256}) {
+                if (rs != RT_OK || B->waves.empty()) break;
                 B->block = blk;
                 if ((rs = B->enqueue(B->cap)) != RT_OK) break;   // warm-up
                 cudaError_t e = cudaEventRecord(e0, B->cap);
@@ -338,6 +491,23 @@ rt_status rt_batch_run(rt_batch* B, void* cuda_stream) {
 }
 
 long long rt_batch_updates(const rt_batch* B) { return B ? B->updates : 0; }
+
+rt_status rt_batch_info(const rt_batch* B, int instance, int* dedicated, int* width, int* block, int* prefetch,
+                        int* tile) {
+    if (!B) return err(RT_ERR_INVALID_ARG, "rt_batch_info: batch is NULL");
+    if (instance < 0 || instance >= (int)B->pos.size())
+        return err(RT_ERR_INVALID_ARG, "rt_batch_info: instance %d outside [0, %d)", instance, (int)B->pos.size());
+    const int k = B->pos[instance];
+    int dd = 0, w = B->host[k].W, bl = B->block, pf = 0, tl = 0;
+    for (const auto& d : B->ded)
+        if (d.inst == k) { dd = 1; w = d.W; bl = d.block; pf = d.prefetch; tl = d.tile; }
+    if (dedicated) *dedicated = dd;
+    if (width) *width = w;
+    if (block) *block = bl;
+    if (prefetch) *prefetch = pf;
+    if (tile) *tile = tl;
+    return RT_OK;
+}
 
 rt_status rt_batch_destroy(rt_batch* B) {
     if (!B) return RT_OK;

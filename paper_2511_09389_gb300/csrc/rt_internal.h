@@ -58,6 +58,15 @@ struct MarchArgs {
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);
 
+// A forward launch plan: bins per thread W, threads per block, gather mode (MarchArgs::prefetch),
+// lanes per ray, source tiles.
+struct MarchPlan {
+    int W, block, prefetch, lpr, tile;
+};
+// The plans the autotuners time for n_freq bins (rt_api.cu for single calls, rt_batch.cu for the
+// batch's dedicated instances), at most 88; returns how many were written to out.
+int march_plan_candidates(int n_freq, MarchPlan* out);
+
 // [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).
 cudaError_t launch_pack(const float* in, float* out, int n_freq, int W, int groups, long long ncell,
                         cudaStream_t st);

@@ -66,6 +66,42 @@ def test_batch_matches_per_instance_and_oracle(torch_cuda, autotune):
     b.close()
 
 
+@pytest.mark.parametrize("autotune", [False, True])
+def test_mixed_batch_dedicated_and_persistent(torch_cuda, autotune):
+    """Instances with at least RT_BATCH_DEDICATED_LANES (source, ray, bin group) lanes get their own
+    launches (a 4-bin group pair and a one-bin instance here, just above the threshold of 19,456);
+    the rest share the persistent kernels. Every output equals its own rt_advance and the oracle."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Batch, Grid
+    big4 = inputs.random_small(240, shape=(20, 18, 16), n_freq=5, n_src=3, num_rays=3300, step_size=0.5,
+                               horizon=10.0)     # 3 x 3300 x 2 groups = 19,800 lanes
+    big1 = inputs.random_small(241, shape=(17, 15, 19), n_freq=1, n_src=7, num_rays=2800, step_size=0.5,
+                               horizon=8.0)      # 7 x 2800 = 19,600 lanes
+    probs = [small_instances()[1], big4, small_instances()[0], big1, small_instances()[3]]
+    dev = [{k: torch.from_numpy(v).cuda() for k, v in (("j", p.j), ("kappa", p.kappa), ("sources", p.sources))}
+           for p in probs]
+    for d, p in zip(dev, probs):
+        d.update(num_rays=p.num_rays, step_size=p.step_size, radiation_velocity=1.0, time_step=p.time_step)
+    b = Batch(dev, autotune=autotune)
+    for rep in range(2):
+        outs = [o.cpu().numpy() for o in b.run()]
+        torch.cuda.synchronize()
+        for p, d, F in zip(probs, dev, outs):
+            g = Grid(p.shape, 8)
+            single = g.advance(d["j"], d["kappa"], d["sources"], p.num_rays, p.step_size, 1.0, p.time_step)
+            assert rel(F, single.cpu().numpy()) <= 1e-5
+            R = oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size,
+                               oracle.num_substeps(p.step_size, 1.0, p.time_step))
+            for bb in range(p.n_freq):
+                assert rel(F[bb], R[bb]) <= 1e-5
+    info = [b.info(i) for i in range(len(probs))]
+    assert [x["dedicated"] for x in info] == [0, 1, 0, 1, 0]
+    assert info[3]["bins_per_thread"] == 1
+    assert info[1]["bins_per_thread"] in ((1, 2, 4) if autotune else (4,))
+    assert all(x["block"] in (32, 64, 128, 256) for x in info)
+    b.close()
+
+
 def test_batch_rejects_bad_instances(torch_cuda):
     torch = torch_cuda
     from paper_2511_09389_gb300.api import Batch, RTError
