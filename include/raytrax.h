@@ -67,14 +67,22 @@ typedef struct {
     int ckpt_stride;    /* adjoint checkpoint stride K in substeps; 0: automatic */
     int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
                            call's stream, readable with rt_kernel_ms */
-    int plan_width;     /* forward launch plan, used when autotune = 0 (0: default for each):  */
-    int plan_block;     /*   bins per group (1, 2 or 4), threads per block (32..256, multiple  */
-    int plan_prefetch;  /*   of 32), gathers (1: reused while the corner set is unchanged, 2:   */
-    int plan_lanes;     /*   one step ahead, 3: both), lanes per ray (1, or 2 / 4 adjacent      */
-                        /*   lanes sharing one ray of a 4-bin group, with gathers mode 1)      */
-    int plan_tile;      /*   and source deposit tiles (1: off, 2: on): each block sums the      */
-                        /*   deposits of its rays in the 8^3 cells around its source in shared  */
-                        /*   memory and adds them to the field once (not in deterministic mode) */
+    /* Forward launch plan, used when autotune = 0; 0 in a field means that field's default.
+       plan_width: bins per group (1, 2 or 4). plan_block: threads per block (32..256, a
+       multiple of 32). plan_prefetch: gathers mode + 1, where mode 0 keeps the 8 corners in
+       slots (when the ray crosses a face, the 4 corners on it keep their gathered j and their
+       summed deposits; the other 4 are flushed and re-gathered), mode 1 issues the next
+       substep's gathers before the current update, mode 2 does both, and mode 3 reuses the
+       whole corner set while it is unchanged and flushes and re-gathers all 8 corners when it
+       changes. plan_lanes: lanes per ray (1, or 2 / 4 adjacent lanes sharing one ray of a
+       4-bin group; gathers mode 0 only). plan_tile: source deposit tiles (1: off, 2: on): each
+       block sums the deposits of its rays in the 8^3 cells around its source in shared memory
+       and adds them to the field once (not in deterministic mode). */
+    int plan_width;
+    int plan_block;
+    int plan_prefetch;
+    int plan_lanes;
+    int plan_tile;
     int check_inputs;   /* 1: checked mode. rt_advance* and rt_backward* first scan j, kappa,
                            the sources (and grad_out) on the device and return
                            RT_ERR_INVALID_ARG, naming the array, if a value is not finite, a

@@ -54,7 +54,9 @@ class Grid:
     """A library handle for one grid shape (owns its scratch on one device).
 
     plan=(bins_per_group, block, gathers[, lanes_per_ray[, tile]]) pins the forward launch plan,
-    gathers 0 = reused, 1 = one step ahead, 2 = both, tile 0 / 1 = source deposit tiles off / on
+    gathers 0 = corner slots (a shared face keeps its gathers and sums), 1 = one step ahead,
+    2 = both, 3 = the whole corner set reused while unchanged; tile 0 / 1 = source deposit tiles
+    off / on
     (the library's default when not given; ignored when autotune=True, which times the
     candidates on the first call of each shape class)."""
 

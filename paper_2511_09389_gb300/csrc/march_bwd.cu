@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jc[c].v[b], jk);
                 const float kds = kc.v[b] * ds;
-                I[b] = fmaf(I[b], expf(-kds), jk * expf(-tau[b]) * ds);
+                I[b] = fmaf(I[b], neg_exp(kds), jk * neg_exp(tau[b]) * ds);
                 tau[b] += kds;
             }
             x = __fadd_rn(x, dx);
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jc[c].v[b], jk);
                 const float kds = kc.v[b] * ds;
-                const float att = expf(-kds), em = expf(-tau[b]);
+                const float att = neg_exp(kds), em = neg_exp(tau[b]);
                 const float emis = jk * em * ds;
                 rI[q][b] = I[b]; rE[q][b] = em; ra[q][b] = att; re[q][b] = emis;
                 I[b] = fmaf(I[b], att, emis);

@@ -85,6 +85,14 @@ __device__ __forceinline__ constexpr int tile_offset(int c) {
     return ((c >> 2) & 1) * kTile * kTile + ((c >> 1) & 1) * kTile + (c & 1);
 }
 
+// exp(-x) for the march's attenuation factors (x = kappa ds >= 0, or tau >= 0): CUDA's fast
+// exponential intrinsic, a few ulp in FP32 for the arguments of the march (its error grows
+// with |x|, where exp(-x) itself is negligible), far inside the relative 1e-5 the march is held
+// to against the FP64 oracle, at a fraction of the instructions of expf. Every kernel of the
+// library (forward, adjoint replay, batch) uses this one function, so a replayed march repeats
+// the forward's intensities exactly.
+__device__ __forceinline__ float neg_exp(float x) { return __expf(-x); }
+
 // ---- W-wide bin vectors -----------------------------------------------------------------
 template <int W> struct Vec;
 template <> struct Vec<1> { float v[1]; };
@@ -139,9 +147,33 @@ __device__ __forceinline__ void red_vec<4>(float* __restrict__ base, int cell, c
     red_add4(base + 4 * (size_t)cell, v[0], v[1], v[2], v[3]);
 }
 
+// Predicated form (no branch): the reduction happens only when p is true; the index must be a
+// valid cell either way (callers clamp it), so no address outside the grid is formed.
+template <int W>
+__device__ __forceinline__ void red_vec_if(bool p, float* __restrict__ base, int cell, const float* v);
+template <>
+__device__ __forceinline__ void red_vec_if<1>(bool p, float* __restrict__ base, int cell, const float* v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f32 [%1], %2;\n\t}"
+                 ::"r"((int)p), "l"(base + cell), "f"(v[0]));
+}
+template <>
+__device__ __forceinline__ void red_vec_if<2>(bool p, float* __restrict__ base, int cell, const float* v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.v2.f32 [%1], {%2, %3};\n\t}"
+                 ::"r"((int)p), "l"(base + 2 * (size_t)cell), "f"(v[0]), "f"(v[1]));
+}
+template <>
+__device__ __forceinline__ void red_vec_if<4>(bool p, float* __restrict__ base, int cell, const float* v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
+                 ::"r"((int)p), "l"(base + 4 * (size_t)cell), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
+}
+
 // 64-bit integer reduction for the deterministic (fixed-point) accumulation mode.
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long a) {
     asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(a));
+}
+__device__ __forceinline__ void red_add_u64_if(bool p, unsigned long long* a, unsigned long long v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.u64 [%1], %2;\n\t}"
+                 ::"r"((int)p), "l"(a), "l"(v));
 }
 
 }  // namespace rt

@@ -165,7 +165,7 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     const long long nblk = rblocks * a.nsrc * a.groups;
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (a.prefetch < 0 || a.prefetch > 2) return cudaErrorInvalidValue;
+    if (a.prefetch < 0 || a.prefetch > 3) return cudaErrorInvalidValue;
     if (a.acc64) {
         switch (W) {   // deterministic mode: gather reuse (PF = 0), every deposit quantised on its own
             case 1: k_march_fwd<1, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
@@ -176,15 +176,19 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
         return cudaGetLastError();
     }
     const bool tile = a.tile && a.n0 >= kTile && a.n1 >= kTile && a.n2 >= kTile;
-    if (a.ckpt) {   // recording the adjoint's checkpoints: gather mode 0
-        if (a.prefetch != 0 || a.ck_stride < 1) return cudaErrorInvalidValue;
-        switch (W * 2 + (tile ? 1 : 0)) {
-            case 2: k_march_fwd<1, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 3: k_march_fwd<1, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd<2, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 5: k_march_fwd<2, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 8: k_march_fwd<4, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 9: k_march_fwd<4, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+    if (a.ckpt) {   // recording the adjoint's checkpoints: gathers mode 0, or 1 / 3 for one bin per thread
+        if (a.ck_stride < 1 || (W != 1 && a.prefetch != 0) || a.prefetch == 2) return cudaErrorInvalidValue;
+        switch ((W * 4 + a.prefetch) * 2 + (tile ? 1 : 0)) {
+            case 8: k_march_fwd<1, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 9: k_march_fwd<1, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 10: k_march_fwd<1, 1, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 11: k_march_fwd<1, 1, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 14: k_march_fwd<1, 3, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 15: k_march_fwd<1, 3, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 16: k_march_fwd<2, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 17: k_march_fwd<2, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 32: k_march_fwd<4, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 33: k_march_fwd<4, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
@@ -193,9 +197,9 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
 #define RT_FWD_CASE(W_, PF_)                                                                     \
         case (W_ * 4 + PF_) * 2: k_march_fwd<W_, PF_, 0, false><<<(unsigned)nblk, block, 0, st>>>(a); break; \
         case (W_ * 4 + PF_) * 2 + 1: k_march_fwd<W_, PF_, 0, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        RT_FWD_CASE(1, 0) RT_FWD_CASE(1, 1) RT_FWD_CASE(1, 2)
-        RT_FWD_CASE(2, 0) RT_FWD_CASE(2, 1) RT_FWD_CASE(2, 2)
-        RT_FWD_CASE(4, 0) RT_FWD_CASE(4, 1) RT_FWD_CASE(4, 2)
+        RT_FWD_CASE(1, 0) RT_FWD_CASE(1, 1) RT_FWD_CASE(1, 2) RT_FWD_CASE(1, 3)
+        RT_FWD_CASE(2, 0) RT_FWD_CASE(2, 1) RT_FWD_CASE(2, 2) RT_FWD_CASE(2, 3)
+        RT_FWD_CASE(4, 0) RT_FWD_CASE(4, 1) RT_FWD_CASE(4, 2) RT_FWD_CASE(4, 3)
 #undef RT_FWD_CASE
         default: return cudaErrorInvalidValue;
     }

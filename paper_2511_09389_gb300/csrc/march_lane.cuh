@@ -108,6 +108,20 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
     }
 }
 
+// flush() when p is true, without a branch (callers pass a valid cell either way).
+template <int W, int DET>
+__device__ __forceinline__ void flush_if(bool p, const Lane& L, int cell, const float* v) {
+    if (DET) {
+        const float f = __ldg(L.fix);
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            red_add_u64_if(p && b < L.nbins, L.og64 + (size_t)cell * W + b,
+                           (unsigned long long)__float2ll_rn(v[b] * f));
+    } else {
+        red_vec_if<W>(p, L.og, cell, v);
+    }
+}
+
 // Send the merged deposits of one run (8 corners) to memory. Runs whose corners lie in the
 // block's tile (tl >= 0) go to shared memory: the rays of a block all start at its source, so
 // these are the most contended cells of the march; the block adds the tile to the field once.
@@ -173,8 +187,8 @@ __device__ __forceinline__ void march_lane_split(const Lane& L, int sub) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gj[c].v[b], jk);
             const float kds = gk.v[b] * ds;
-            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
-            const float em = expf(-tau[b]);               // exp(-tau_k)
+            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
             tau[b] += kds;                                // Eq. 2: tau_{k+1}
             dep[b] = I[b] * scale;
@@ -251,8 +265,8 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L, RayState<W>& R) 
 #pragma unroll
             for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
             const float kds = gd.k.v[b] * ds;
-            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
-            const float em = expf(-tau[b]);               // exp(-tau_k)
+            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
             tau[b] += kds;                                // Eq. 2: tau_{k+1}
             dep[b] = I[b] * scale;
@@ -282,14 +296,201 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L, RayState<W>& R) 
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
 }
 
-// REC (gather mode 0 only): store (x_k, I_k, tau_k) every ck_stride substeps, the forward sweep
-// the reverse march would otherwise repeat.
-template <int W, int PF, int DET = 0, bool TILE = false, bool REC = false>
-__device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
-    if (PF == 2) {
-        march_lane_ahead<W, DET, TILE>(L, R);
-        return;
+// Gathers mode 0: the corner slots. A lane keeps the 8 corners of its current corner set in 8
+// slots, each holding the corner's cell, its gathered j (W bins) and the sum of the deposits it
+// has received since it was filled. Slot s holds the corner whose bit along axis a is
+// bit_a(s) ^ P_a. Per axis the set is the clamped pair (lo, hi) of the current position. When
+// the pair moves up by one cell (the new lo is the old hi), the old hi face is shared by both
+// sets: its four slots keep their cells, j values and sums and only flip role (P_a ^= 1), while
+// the four slots of the old lo face are flushed (one reduction each) and refilled (one gather
+// each) as the new hi face; moving down is the mirror image, an unchanged pair changes nothing,
+// and any other change (a jump of more than one cell) flushes and refills every slot. A ray
+// crosses a face about every other substep at ds = 0.5, so against flushing and re-gathering
+// all eight corners at every change of the set this halves both the reductions and the gathers.
+// The deposits a cell receives are summed in its slot for as long as the ray keeps it, which
+// also means fewer FP32 additions into the large sums of the field.
+// REC: store (x_k, I_k, tau_k) every ck_stride substeps, the forward sweep the reverse march
+// would otherwise repeat.
+template <int W, int DET, bool TILE, bool REC>
+__device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = R.x, y = R.y, z = R.z;
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = R.I[b]; tau[b] = R.tau[b]; }
+    const float ds = L.ds, scale = L.scale;
+
+    int pc[8];           // cell of each slot, -1 while empty
+    int tl[8];           // TILE: its index in the block's shared-memory tile, or -1
+    float pend[8][W];    // deposits summed in the slot
+    Vec<W> gj[8];        // j at the slot's cell
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        pc[c] = -1;
+        tl[c] = -1;
+#pragma unroll
+        for (int b = 0; b < W; ++b) { pend[c][b] = 0.0f; gj[c].v[b] = 0.0f; }
     }
+    // per axis: the (lo, hi) pair of the current set (-2: none yet) and the role flip P_a
+    int rl0 = -2, rh0 = -2, rl1 = -2, rh1 = -2, rl2 = -2, rh2 = -2;
+    int P0 = 0, P1 = 0, P2 = 0;
+    Vec<W> gk;
+#pragma unroll
+    for (int b = 0; b < W; ++b) gk.v[b] = 0.0f;
+    int gnn = -1;
+
+    int ck_left = 0;     // REC: substeps until the next checkpoint
+    float* ckp = L.ck;   // REC: this lane's next checkpoint
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        if (REC) {
+            if (ck_left == 0) {
+                ckp[0] = x; ckp[L.ck_lanes] = y; ckp[2 * L.ck_lanes] = z;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    ckp[(3 + b) * L.ck_lanes] = I[b];
+                    ckp[(3 + W + b) * L.ck_lanes] = tau[b];
+                }
+                ckp += (3 + 2 * W) * L.ck_lanes;
+                ck_left = L.ck_stride;
+            }
+            --ck_left;
+        }
+        const Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, L.n1), a2 = axis_sample(z, L.n2);
+        // transition of each axis pair: same, up (new lo = old hi), down (new hi = old lo), other
+        const bool same0 = a0.lo == rl0 && a0.hi == rh0, same1 = a1.lo == rl1 && a1.hi == rh1,
+                   same2 = a2.lo == rl2 && a2.hi == rh2;
+        const bool up0 = !same0 && a0.lo == rh0, up1 = !same1 && a1.lo == rh1, up2 = !same2 && a2.lo == rh2;
+        const bool dn0 = !same0 && !up0 && a0.hi == rl0, dn1 = !same1 && !up1 && a1.hi == rl1,
+                   dn2 = !same2 && !up2 && a2.hi == rl2;
+        const bool change = !(same0 && same1 && same2);
+        bool flag[8];
+        if (change) {
+            const bool other = !(same0 || up0 || dn0) || !(same1 || up1 || dn1) || !(same2 || up2 || dn2);
+            // the leaving face: slots whose axis bit equals P_a ^ (1 if moving down)
+            const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
+            const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
+            const bool lo0 = sh0 && q0 == 0, hi0 = sh0 && q0 == 1;
+            const bool lo1 = sh1 && q1 == 0, hi1 = sh1 && q1 == 1;
+            const bool lo2 = sh2 && q2 == 0, hi2 = sh2 && q2 == 1;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                flag[c] = other || (((c >> 2) & 1) ? hi0 : lo0) || (((c >> 1) & 1) ? hi1 : lo1) ||
+                          ((c & 1) ? hi2 : lo2);
+                const bool send = flag[c] && pc[c] >= 0;
+                if (TILE) {
+                    if (send) {
+                        if (tl[c] >= 0) {
+                            float* t = L.tile + tl[c] * W;
+#pragma unroll
+                            for (int b = 0; b < W; ++b) atomicAdd(t + b, pend[c][b]);
+                        } else {
+                            flush<W, DET>(L, pc[c], pend[c]);
+                        }
+                    }
+                } else {
+                    flush_if<W, DET>(send, L, max(pc[c], 0), pend[c]);
+                }
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = flag[c] ? 0.0f : pend[c][b];
+            }
+            P0 ^= sh0 ? 1 : 0; P1 ^= sh1 ? 1 : 0; P2 ^= sh2 ? 1 : 0;
+            rl0 = a0.lo; rh0 = a0.hi; rl1 = a1.lo; rh1 = a1.hi; rl2 = a2.lo; rh2 = a2.hi;
+        }
+        // slot geometry: coordinate and weight factor of slot bit 0 / 1 along each axis
+        const int c00 = P0 ? a0.hi : a0.lo, c01 = P0 ? a0.lo : a0.hi;
+        const int c10 = P1 ? a1.hi : a1.lo, c11 = P1 ? a1.lo : a1.hi;
+        const int c20 = P2 ? a2.hi : a2.lo, c21 = P2 ? a2.lo : a2.hi;
+        const float u0 = 1.0f - a0.t, u1 = 1.0f - a1.t, u2 = 1.0f - a2.t;
+        const float f00 = P0 ? a0.t : u0, f01 = P0 ? u0 : a0.t;
+        const float f10 = P1 ? a1.t : u1, f11 = P1 ? u1 : a1.t;
+        const float f20 = P2 ? a2.t : u2, f21 = P2 ? u2 : a2.t;
+        float w[8];
+        {
+            const float w00 = f00 * f10, w01 = f00 * f11, w10 = f01 * f10, w11 = f01 * f11;
+            w[0] = w00 * f20; w[1] = w00 * f21; w[2] = w01 * f20; w[3] = w01 * f21;
+            w[4] = w10 * f20; w[5] = w10 * f21; w[6] = w11 * f20; w[7] = w11 * f21;
+        }
+        if (change) {
+            const int r00 = (c00 * L.n1 + c10) * L.n2, r01 = (c00 * L.n1 + c11) * L.n2;
+            const int r10 = (c01 * L.n1 + c10) * L.n2, r11 = (c01 * L.n1 + c11) * L.n2;
+            const int cell[8] = {r00 + c20, r00 + c21, r01 + c20, r01 + c21,
+                                 r10 + c20, r10 + c21, r11 + c20, r11 + c21};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (flag[c]) {
+                    gj[c] = ldg_vec<W>(jg, cell[c]);
+                    pc[c] = cell[c];
+                }
+                if (TILE && flag[c]) {
+                    const unsigned v0 = (unsigned)((((c >> 2) & 1) ? c01 : c00) - L.to0);
+                    const unsigned v1 = (unsigned)((((c >> 1) & 1) ? c11 : c10) - L.to1);
+                    const unsigned v2 = (unsigned)(((c & 1) ? c21 : c20) - L.to2);
+                    tl[c] = (v0 < (unsigned)kTile && v1 < (unsigned)kTile && v2 < (unsigned)kTile)
+                                ? (int)((v0 * kTile + v1) * kTile + v2) : -1;
+                }
+            }
+        }
+        // kappa at the nearest cell of x_k (the floor corner, or the rounded position)
+        const int nn = L.kappa_mode == 0 ? (a0.lo * L.n1 + a1.lo) * L.n2 + a2.lo
+                                         : (nearest_round(x, L.n0) * L.n1 + nearest_round(y, L.n1)) * L.n2 +
+                                               nearest_round(z, L.n2);
+        if (nn != gnn) {
+            gk = ldg_vec<W>(kg, nn);
+            gnn = nn;
+        }
+        float dep[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float jk = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) jk = fmaf(w[c], gj[c].v[b], jk);
+            const float kds = gk.v[b] * ds;
+            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+            tau[b] += kds;                                // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int b = 0; b < W; ++b) pend[c][b] = fmaf(w[c], dep[b], pend[c][b]);
+        }
+        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
+        y = __fadd_rn(y, dy);
+        z = __fadd_rn(z, dz);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (pc[c] >= 0) {
+            if (TILE && tl[c] >= 0) {
+                float* t = L.tile + tl[c] * W;
+#pragma unroll
+                for (int b = 0; b < W; ++b) atomicAdd(t + b, pend[c][b]);
+            } else {
+                flush<W, DET>(L, pc[c], pend[c]);
+            }
+        }
+    }
+    R.x = x; R.y = y; R.z = z;
+#pragma unroll
+    for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
+}
+
+// Gathers modes 1 and 3, the corner set as one unit: deposits are merged in registers while the
+// set is unchanged and all eight corners are flushed when it changes. AHEAD (mode 1): the gathers
+// of substep k+1 are issued before the update of substep k, every substep. Otherwise (mode 3)
+// the gathers are issued only when the set (or the kappa cell) changes and reused in between;
+// with few lanes per SM and one bin per thread this is faster than the slots of mode 0, whose
+// bookkeeping is paid per lane.
+// REC: store (x_k, I_k, tau_k) every ck_stride substeps, the forward sweep the reverse march
+// would otherwise repeat.
+template <int W, bool AHEAD, int DET, bool TILE, bool REC>
+__device__ __forceinline__ void march_lane_runs(const Lane& L, RayState<W>& R) {
+    constexpr int PF = AHEAD ? 1 : 0;
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
     float* __restrict__ og = L.og;
@@ -361,8 +562,8 @@ __device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
             const float kds = gd.k.v[b] * ds;
-            const float att = expf(-kds);                 // exp(-kappa(x_k) ds)
-            const float em = expf(-tau[b]);               // exp(-tau_k)
+            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
             tau[b] += kds;                                // Eq. 2: tau_{k+1}
             dep[b] = I[b] * scale;
@@ -396,6 +597,15 @@ __device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
 #pragma unroll
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
     (void)og;
+}
+
+// Gathers modes: PF = 0 march_lane_slots, 1 and 3 march_lane_runs, 2 march_lane_ahead. REC
+// (checkpoints) is available with modes 0, 1 and 3.
+template <int W, int PF, int DET = 0, bool TILE = false, bool REC = false>
+__device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
+    if (PF == 2) march_lane_ahead<W, DET, TILE>(L, R);
+    else if (PF == 0) march_lane_slots<W, DET, TILE, REC>(L, R);
+    else march_lane_runs<W, PF == 1, DET, TILE, REC>(L, R);
 }
 
 }  // namespace rt

@@ -220,7 +220,8 @@ def test_deterministic_mode_full_size(torch_cuda):
 
 @pytest.mark.parametrize("plan", [(4, 64, 0, 2), (4, 128, 0, 4), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
                                   (1, 32, 0, 1), (4, 32, 0, 1, 1), (2, 128, 1, 1, 1), (1, 64, 1, 1, 1),
-                                  (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0)])
+                                  (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0), (4, 32, 3, 1),
+                                  (2, 64, 3, 1, 0), (1, 64, 3, 1, 1), (4, 64, 3, 1, 1)])
 def test_every_launch_plan_meets_parity(torch_cuda, plan):
     """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray,
     source deposit tiles) on a ragged multi-bin problem."""
@@ -230,7 +231,8 @@ def test_every_launch_plan_meets_parity(torch_cuda, plan):
     assert_parity(run_gpu(torch_cuda, p, grid=g), run_oracle(p))
 
 
-@pytest.mark.parametrize("plan", [(1, 32, 1, 1, 1), (1, 128, 0, 1, 1), (4, 64, 0, 1, 1), (2, 32, 2, 1, 1)])
+@pytest.mark.parametrize("plan", [(1, 32, 1, 1, 1), (1, 128, 0, 1, 1), (4, 64, 0, 1, 1), (2, 32, 2, 1, 1),
+                                  (1, 64, 3, 1, 1), (4, 32, 3, 1, 1)])
 def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
     """Source deposit tiles: many sources packed into a few cells (the tiles overlap and take
     most deposits), plus sources on and outside the faces and corners (the tile origin is moved
@@ -249,3 +251,19 @@ def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
     F = run_gpu(torch_cuda, p, grid=g)
     assert g.last_plan()["tile"] == 1
     assert_parity(F, run_oracle(p))
+
+
+@pytest.mark.parametrize("step_size", [0.13, 0.5, 1.0, 1.7, 3.2])
+@pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3)])
+def test_corner_slots_across_step_sizes(torch_cuda, plan, step_size):
+    """Gathers mode 0 keeps a face shared by consecutive corner sets (a step of one cell along an
+    axis) and flushes everything else. Steps much shorter than a cell (long runs in one set), of
+    exactly one cell, and of more than one cell (no shared face: every corner leaves), with sources
+    inside, on and outside the faces (clamped pairs that collapse and reopen), on a box with one
+    axis of a single cell, against the oracle."""
+    from paper_2511_09389_gb300.api import Grid
+    for shape in ((14, 11, 17), (9, 1, 12)):
+        p = inputs.random_small(90, shape=shape, n_freq=5, n_src=4, num_rays=211, step_size=step_size,
+                                horizon=14.0)
+        g = Grid(p.shape, 8, plan=plan)
+        assert_parity(run_gpu(torch_cuda, p, grid=g), run_oracle(p))
