@@ -130,6 +130,16 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Write zeros to 32 columns of the warp's 32 tensor-memory lanes starting at taddr.
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
 constexpr int kTmemCols = 32;
 constexpr int kBox = 128 * 64;             // one tap box: 128 voxels x 32 channels x 2 bytes
 constexpr int kWBytes = 27 * 32 * 64;      // weights: 27 taps x 32 outputs x 64-byte rows
@@ -164,15 +174,21 @@ __device__ __forceinline__ int sw64(int r, int c) { return r * 64 + ((c ^ ((r >>
 // belongs to (dz = -1, 0, +1, with the weights of tap (dz, dy, dx)). A work item is a chain
 // segment of at most kChainMax outputs; its inputs are the segment's slices plus one on each
 // side (those outside the volume are zero padding and skipped). A ring stage carries the three
-// dx boxes of one (input slice, dy); up to 18 MMAs per stage into a ring of kChainSlots TMEM
-// accumulators, drained by the epilogue warps in output order. Per output tile ~11 boxes are
-// loaded instead of 27, and each stage's fixed round trip is shared by six times more MMAs.
+// dx boxes of one (input slice, dy). The weights sit in shared memory with the three dz taps of
+// each (dy, dx) back to back in the order dz = +1, 0, -1, and each output of the segment has its
+// own 32-column TMEM accumulator at its position in the segment, so the outputs an input feeds
+// (positions i - 1, i, i + 1 for dz = +1, 0, -1) are adjacent columns and adjacent weight rows:
+// one MMA of N = 96 (64 or 32 at the ends of the segment) per dx box and K half, 6 per stage,
+// reads the box once for all three outputs. Since such an MMA accumulates into two outputs that
+// are under way and one that is fresh, the accumulators are zero beforehand: the epilogue warps
+// clear each accumulator when they drain it (and all of them at the start). Per output tile ~11
+// boxes are loaded instead of 27.
 namespace {
 #ifndef RT_CHAIN_MAX
 #define RT_CHAIN_MAX 8
 #endif
 constexpr int kChainMax = RT_CHAIN_MAX;   // outputs per work item
-constexpr int kChainSlots = 4;
+constexpr int kChainSlots = kChainMax;   // one accumulator per output position of a segment
 #ifndef RT_CHAIN_CTAS
 #define RT_CHAIN_CTAS 2
 #endif
@@ -226,8 +242,10 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
         return;
     }
     for (int i = tid; i < kWBytes / 16; i += kConvThreads) {
+        // packed tap (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) goes to block ((dy + 1) * 3 + dx + 1) * 3 + (1 - dz)
         const int c = i & 3, r = (i >> 2) & 31, tap = i >> 7;
-        *reinterpret_cast<uint4*>(sw + tap * 2048 + sw64(r, c)) = __ldg(a.w_packed + i);
+        const int pos = (tap % 9) * 3 + (2 - tap / 9);
+        *reinterpret_cast<uint4*>(sw + pos * 2048 + sw64(r, c)) = __ldg(a.w_packed + i);
     }
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
@@ -253,7 +271,15 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = idesc_bf16(128, 32);
+    if (warp >= 2) {   // the MMAs accumulate from the start: clear every accumulator first
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) tmem_zero32(tmem + lanes + (uint32_t)(j * kTmemCols));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -283,32 +309,34 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int q = 0, seq = 0;
-            bool first[NS];
-#pragma unroll
-            for (int k = 0; k < NS; ++k) first[k] = false;
+            int q = 0;
+            uint32_t phase = 0;   // bit j: parity of accumulator j's next acc_empty wait, flipped per use
             bool ok = true;
             for (int item = blockIdx.x; item < n_items && ok && !*abort_flag; item += gridDim.x) {
                 ChainItem it;
                 if (!chain_item(a, item, Q, it)) continue;
-                const int base = seq;
                 int started = it.n0;   // outputs [n0, started) have their accumulators
                 for (int i = it.n0 - 1; i <= it.n1 && ok; ++i) {
                     const int zi = it.r + i * a.dil;
                     if (zi >= 0 && zi < a.D) {
-                        // outputs fed by this input: i + 1 (dz = -1), i (dz = 0), i - 1 (dz = +1)
-                        const int last = min(i + 1, it.n1 - 1);
-                        for (; started <= last && ok; ++started) {
-                            const int sq = base + (started - it.n0);
-                            if (!mbar_wait(&acc_empty[sq % NS], ((uint32_t)(sq / NS) & 1u) ^ 1u)) {
+                        // outputs fed by this input: i - 1 (dz = +1), i (dz = 0), i + 1 (dz = -1)
+                        const int lo = max(i - 1, it.n0), hi = min(i + 1, it.n1 - 1);
+                        for (; started <= hi && ok; ++started) {
+                            const int j = started - it.n0;
+                            if (!mbar_wait(&acc_empty[j], ((phase >> j) & 1u) ^ 1u)) {
                                 *abort_flag = 1;
                                 atomicExch(a.err, 3);
                                 ok = false;
                             }
-                            first[sq % NS] = true;
+                            phase ^= 1u << j;
                         }
                         if (!ok) break;
                         tc_fence_after();
+                        const int cnt = hi - lo + 1;
+                        const uint32_t idesc = cnt == 3 ? idesc_bf16(128, 96)
+                                               : (cnt == 2 ? idesc_bf16(128, 64) : idesc_bf16(128, 32));
+                        const uint32_t d = tmem + (uint32_t)((lo - it.n0) * kTmemCols);
+                        const int block0 = 1 - (i - lo);   // weight block of output lo: dz = i - lo
                         for (int dy = -1; dy <= 1; ++dy, ++q) {
                             const int st = q % S;
                             if (!mbar_wait(&full[st], (uint32_t)(q / S) & 1u)) {
@@ -320,23 +348,15 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
                             tc_fence_after();
                             const uint32_t sbase = smem_u32(sa + st * kChainStageBytes);
 #pragma unroll
-                            for (int dz = -1; dz <= 1; ++dz) {
-                                const int n = i - dz;
-                                if (n < it.n0 || n >= it.n1) continue;
-                                const int slot = (base + (n - it.n0)) % NS;
-                                const uint32_t d = tmem + (uint32_t)(slot * kTmemCols);
+                            for (int u = 0; u < 3; ++u) {
+                                const int pos = ((dy + 1) * 3 + u) * 3 + block0;
+                                const uint32_t abase = sbase + (uint32_t)(u * kBox);
+                                const uint32_t bbase = smem_u32(sw) + (uint32_t)(pos * 2048);
 #pragma unroll
-                                for (int u = 0; u < 3; ++u) {
-                                    const int tap = (dz + 1) * 9 + (dy + 1) * 3 + u;
-                                    const uint32_t abase = sbase + (uint32_t)(u * kBox);
-                                    const uint32_t bbase = smem_u32(sw) + (uint32_t)(tap * 2048);
-#pragma unroll
-                                    for (int k = 0; k < 2; ++k) {
-                                        const uint64_t ad = sdesc_sw64(abase + (uint32_t)(k * 32), 16, 512);
-                                        const uint64_t bd = sdesc_sw64(bbase + (uint32_t)(k * 32), 16, 512);
-                                        mma_bf16(d, ad, bd, idesc, (first[slot] && k == 0) ? 0u : 1u);
-                                        first[slot] = false;
-                                    }
+                                for (int k = 0; k < 2; ++k) {
+                                    const uint64_t ad = sdesc_sw64(abase + (uint32_t)(k * 32), 16, 512);
+                                    const uint64_t bd = sdesc_sw64(bbase + (uint32_t)(k * 32), 16, 512);
+                                    mma_bf16(d, ad, bd, idesc, 1u);
                                 }
                             }
                             mma_commit(&empty[st]);
@@ -344,23 +364,23 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
                         if (!ok) break;
                     }
                     // after input i, output i - 1 has all its contributions
-                    if (i - 1 >= it.n0 && i - 1 < it.n1) mma_commit(&acc_full[(base + (i - 1 - it.n0)) % NS]);
+                    if (i - 1 >= it.n0 && i - 1 < it.n1) mma_commit(&acc_full[i - 1 - it.n0]);
                 }
-                seq = base + (it.n1 - it.n0);
             }
             mma_commit(mma_done);
         }
     } else {
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        int seq = 0;
+        uint32_t phase = 0;   // bit j: parity of accumulator j's next acc_full wait
         bool live = true;
         for (int item = blockIdx.x; item < n_items && live; item += gridDim.x) {
             ChainItem it;
             if (!chain_item(a, item, Q, it)) continue;
-            for (int n = it.n0; n < it.n1; ++n, ++seq) {
-                const int slot = seq % NS;
-                const bool ready = mbar_wait(&acc_full[slot], (uint32_t)(seq / NS) & 1u);
+            for (int n = it.n0; n < it.n1; ++n) {
+                const int slot = n - it.n0;
+                const bool ready = mbar_wait(&acc_full[slot], (phase >> slot) & 1u);
+                phase ^= 1u << slot;
                 if (!ready || *abort_flag) {
                     if (!ready) { *abort_flag = 1; atomicExch(a.err, 4); }
                     live = false;
@@ -369,7 +389,10 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
                 __syncwarp();
                 tc_fence_after();
                 float v[32];
-                tmem_load<32>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * kTmemCols), v);
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * kTmemCols);
+                tmem_load<32>(taddr, v);
+                tmem_zero32(taddr);   // the next segment's MMAs accumulate onto zero
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&acc_empty[slot]);
                 const int z = it.r + n * a.dil;
