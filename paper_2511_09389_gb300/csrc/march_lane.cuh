@@ -360,8 +360,9 @@ __device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) 
         }
         const Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, L.n1), a2 = axis_sample(z, L.n2);
         // transition of each axis pair: same, up (new lo = old hi), down (new hi = old lo), other
-        const bool same0 = a0.lo == rl0 && a0.hi == rh0, same1 = a1.lo == rl1 && a1.hi == rh1,
-                   same2 = a2.lo == rl2 && a2.hi == rh2;
+        const int key0 = a0.lo | (a0.hi << 16), key1 = a1.lo | (a1.hi << 16), key2 = a2.lo | (a2.hi << 16);
+        const bool same0 = key0 == (rl0 | (rh0 << 16)), same1 = key1 == (rl1 | (rh1 << 16)),
+                   same2 = key2 == (rl2 | (rh2 << 16));
         const bool up0 = !same0 && a0.lo == rh0, up1 = !same1 && a1.lo == rh1, up2 = !same2 && a2.lo == rh2;
         const bool dn0 = !same0 && !up0 && a0.hi == rl0, dn1 = !same1 && !up1 && a1.hi == rl1,
                    dn2 = !same2 && !up2 && a2.hi == rl2;
@@ -372,13 +373,15 @@ __device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) 
             // the leaving face: slots whose axis bit equals P_a ^ (1 if moving down)
             const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
             const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
-            const bool lo0 = sh0 && q0 == 0, hi0 = sh0 && q0 == 1;
-            const bool lo1 = sh1 && q1 == 0, hi1 = sh1 && q1 == 1;
-            const bool lo2 = sh2 && q2 == 0, hi2 = sh2 && q2 == 1;
+            // leaving slots as a bit mask: the bit-0 / bit-1 face of axis 0 is 0x0F / 0xF0, of axis
+            // 1 0x33 / 0xCC, of axis 2 0x55 / 0xAA
+            unsigned mask = other ? 0xFFu : 0u;
+            mask |= sh0 ? (q0 ? 0xF0u : 0x0Fu) : 0u;
+            mask |= sh1 ? (q1 ? 0xCCu : 0x33u) : 0u;
+            mask |= sh2 ? (q2 ? 0xAAu : 0x55u) : 0u;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                flag[c] = other || (((c >> 2) & 1) ? hi0 : lo0) || (((c >> 1) & 1) ? hi1 : lo1) ||
-                          ((c & 1) ? hi2 : lo2);
+                flag[c] = (mask >> c) & 1u;
                 const bool send = flag[c] && pc[c] >= 0;
                 if (TILE) {
                     if (send) {
