@@ -522,7 +522,7 @@ def native_arm(args):
         "e2e_serial": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": ems,
                        "api": "rt_advance_host (copy in, march, copy out, synchronise) per step, L2 flushed before each"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
     }

@@ -229,6 +229,38 @@ __global__ void k_pack(const float* __restrict__ in, float* __restrict__ out, in
     }
 }
 
+// j and kappa in one pass, and the packed accumulator cleared (acc != NULL): one launch instead
+// of three before a march.
+template <int W>
+__global__ void k_pack_pair(const float* __restrict__ j, const float* __restrict__ kap, float* __restrict__ jp,
+                            float* __restrict__ kp, float* __restrict__ acc, int n_freq, long long ncell,
+                            long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long g = i / ncell, c = i - g * ncell;
+        float vj[W], vk[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const long long b = g * W + w;
+            vj[w] = b < n_freq ? __ldg(j + b * ncell + c) : 0.0f;
+            vk[w] = b < n_freq ? __ldg(kap + b * ncell + c) : 0.0f;
+        }
+        if (W == 4) {
+            reinterpret_cast<float4*>(jp)[i] = make_float4(vj[0], vj[1 % W], vj[2 % W], vj[3 % W]);
+            reinterpret_cast<float4*>(kp)[i] = make_float4(vk[0], vk[1 % W], vk[2 % W], vk[3 % W]);
+            if (acc) reinterpret_cast<float4*>(acc)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else if (W == 2) {
+            reinterpret_cast<float2*>(jp)[i] = make_float2(vj[0], vj[1 % W]);
+            reinterpret_cast<float2*>(kp)[i] = make_float2(vk[0], vk[1 % W]);
+            if (acc) reinterpret_cast<float2*>(acc)[i] = make_float2(0.0f, 0.0f);
+        } else {
+            jp[i] = vj[0];
+            kp[i] = vk[0];
+            if (acc) acc[i] = 0.0f;
+        }
+    }
+}
+
 template <int W>
 __global__ void k_unpack(const float* __restrict__ acc, float* __restrict__ out, int n_freq,
                          long long ncell, long long total, float scale, int accumulate) {
@@ -272,6 +304,19 @@ cudaError_t launch_pack(const float* in, float* out, int n_freq, int W, int grou
         case 1: k_pack<1><<<grid, 256, 0, st>>>(in, out, n_freq, ncell, total); break;
         case 2: k_pack<2><<<grid, 256, 0, st>>>(in, out, n_freq, ncell, total); break;
         case 4: k_pack<4><<<grid, 256, 0, st>>>(in, out, n_freq, ncell, total); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_pair(const float* j, const float* kappa, float* jp, float* kp, float* acc, int n_freq, int W,
+                             int groups, long long ncell, cudaStream_t st) {
+    const long long total = (long long)groups * ncell;
+    const unsigned grid = grid_for(total, 256);
+    switch (W) {
+        case 1: k_pack_pair<1><<<grid, 256, 0, st>>>(j, kappa, jp, kp, acc, n_freq, ncell, total); break;
+        case 2: k_pack_pair<2><<<grid, 256, 0, st>>>(j, kappa, jp, kp, acc, n_freq, ncell, total); break;
+        case 4: k_pack_pair<4><<<grid, 256, 0, st>>>(j, kappa, jp, kp, acc, n_freq, ncell, total); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

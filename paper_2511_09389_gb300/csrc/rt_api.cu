@@ -349,9 +349,10 @@ int pick_width(int n_freq) {
 }
 
 // Lay out the inputs for bin-group width W (packing for W > 1) and fill the march arguments.
-// The accumulator is `out` itself for W = 1 with an output, else the handle's scratch.
+// The accumulator is `out` itself for W = 1 with an output, else the handle's scratch; with
+// clear_acc, packing for W > 1 also zeroes the packed accumulator (same launch).
 rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const float4* dirs, float scale,
-                  float* out, rt::MarchArgs* m) {
+                  float* out, rt::MarchArgs* m, bool clear_acc = false) {
     rt_status st;
     const long long ncell = g->ncell();
     *m = rt::MarchArgs{};
@@ -386,8 +387,9 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
     if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::ACC, packed, &acc)) != RT_OK) return st;
-    RT_CUDA(rt::launch_pack(a.j, (float*)jp, a.n_freq, W, groups, ncell, a.st), "pack(j) launch");
-    RT_CUDA(rt::launch_pack(a.kappa, (float*)kp, a.n_freq, W, groups, ncell, a.st), "pack(kappa) launch");
+    RT_CUDA(rt::launch_pack_pair(a.j, a.kappa, (float*)jp, (float*)kp, clear_acc ? (float*)acc : nullptr, a.n_freq,
+                                 W, groups, ncell, a.st),
+            "pack launch");
     m->jp = (const float*)jp; m->kp = (const float*)kp; m->acc = (float*)acc;
     m->groups = groups;
     m->dep_scale = 1.0f;
@@ -573,7 +575,7 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     g->last_plan = plan;
 
     rt::MarchArgs m;
-    if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
+    if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m, true)) != RT_OK) return st;
     m.st_pos_in = a.st_pos_in;
     m.st_pos_out = a.st_pos_out;
     m.st_I = a.st_I;
@@ -592,9 +594,8 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         g->rec = rt_grid::Recording{true, a.j, a.kappa, a.src, a.nsrc, a.num_rays, ns, a.n_freq, sz.stride,
                                     plan.W, g->opt.kappa_mode, a.ds};
     }
-    if (plan.W > 1 || !a.accumulate)
-        RT_CUDA(cudaMemsetAsync(m.acc, 0, plan.W == 1 ? field_bytes : acc_bytes(g, a, plan), a.st),
-                "cudaMemsetAsync(accumulator)");
+    if (plan.W == 1 && !a.accumulate)   // (for W > 1 the packing launch cleared the accumulator)
+        RT_CUDA(cudaMemsetAsync(m.acc, 0, field_bytes, a.st), "cudaMemsetAsync(accumulator)");
     if ((st = g->mark(0, a.st)) != RT_OK) return st;
     RT_CUDA(rt::launch_march_fwd(plan.W, m, a.st), "march kernel launch");
     if ((st = g->mark(1, a.st)) != RT_OK) return st;

@@ -72,6 +72,9 @@ int march_plan_candidates(int n_freq, MarchPlan* out);
 // [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).
 cudaError_t launch_pack(const float* in, float* out, int n_freq, int W, int groups, long long ncell,
                         cudaStream_t st);
+// j and kappa packed in one launch, and acc (if not NULL) set to zero, all [groups][ncell][W].
+cudaError_t launch_pack_pair(const float* j, const float* kappa, float* jp, float* kp, float* acc, int n_freq, int W,
+                             int groups, long long ncell, cudaStream_t st);
 // out[b][c] (+)= scale * acc[b / W][c][b % W]
 cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long long ncell,
                           float scale, int accumulate, cudaStream_t st);
