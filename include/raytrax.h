@@ -74,8 +74,8 @@ typedef struct {
        summed deposits; the other 4 are flushed and re-gathered), mode 1 issues the next
        substep's gathers before the current update, mode 2 does both, and mode 3 reuses the
        whole corner set while it is unchanged and flushes and re-gathers all 8 corners when it
-       changes. plan_lanes: lanes per ray (1, or 2 / 4 adjacent lanes sharing one ray of a
-       4-bin group; gathers mode 0 only). plan_tile: source deposit tiles (1: off, 2: on): each
+       changes. plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
+       the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 only). plan_tile: source deposit tiles (1: off, 2: on): each
        block sums the deposits of its rays in the 8^3 cells around its source in shared memory
        and adds them to the field once (not in deterministic mode). */
     int plan_width;

@@ -113,24 +113,25 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
     }
 }
 
-// Split lanes over a 4-bin packed group: LPR lanes per (ray, source, group), adjacent in a warp.
-template <int LPR>
-__global__ void __launch_bounds__(256) k_march_fwd_split(MarchArgs a) {
-    constexpr int WL = 4 / LPR;
-    const int rays_per_block = blockDim.x / LPR;
+// Lanes per ray = 2: adjacent lanes (sub = threadIdx.x & 1) share one (ray, source, bin group),
+// each with half of its corner slots (march_lane_pair).
+template <int W>
+__global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
+    const int rays_per_block = blockDim.x / 2;
     const int rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
     const int rb = blockIdx.x % rblocks;
     const int sg = blockIdx.x / rblocks;
     const int s = sg % a.nsrc;
     const int g = sg / a.nsrc;
-    const int sub = threadIdx.x % LPR;
-    const int r = rb * rays_per_block + threadIdx.x / LPR;
-    if (r >= a.ray_count) return;
+    const int sub = threadIdx.x & 1;
+    const int r = rb * rays_per_block + (threadIdx.x >> 1);
+    if (r >= a.ray_count) return;   // both lanes of a pair leave together
+    const unsigned pmask = 3u << (threadIdx.x & 30);
     const long long ncell = (long long)a.n0 * a.n1 * a.n2;
     Lane L;
-    L.jg = a.jp + (size_t)g * ncell * 4;
-    L.kg = a.kp + (size_t)g * ncell * 4;
-    L.og = a.acc + (size_t)g * ncell * 4;
+    L.jg = a.jp + (size_t)g * ncell * W;
+    L.kg = a.kp + (size_t)g * ncell * W;
+    L.og = a.acc + (size_t)g * ncell * W;
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
@@ -138,24 +139,23 @@ __global__ void __launch_bounds__(256) k_march_fwd_split(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
-    L.tile = nullptr;
-    march_lane_split<WL, 4>(L, sub);
+    march_lane_pair<W>(L, sub, pmask);
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     if (a.lanes_per_ray > 1) {
-        // split lanes (4-bin packed groups only): block counts threads, lanes_per_ray per ray
-        if (W != 4 || a.acc64) return cudaErrorInvalidValue;
-        const int block = a.block > 0 ? a.block : 128;
-        const int rpb = block / a.lanes_per_ray;
-        if (rpb < 1) return cudaErrorInvalidValue;
-        const long long rblocks = (a.ray_count + rpb - 1) / rpb;
+        // two lanes per ray: block counts threads (a multiple of 32), block / 2 rays per block
+        if (a.lanes_per_ray != 2 || a.acc64 || a.st_I || a.ckpt || a.prefetch != 0) return cudaErrorInvalidValue;
+        const int block = a.block > 0 ? a.block : 64;
+        if (block % 32) return cudaErrorInvalidValue;
+        const long long rblocks = (a.ray_count + block / 2 - 1) / (block / 2);
         const long long nblk = rblocks * a.nsrc * a.groups;
         if (nblk <= 0) return cudaSuccess;
         if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        switch (a.lanes_per_ray) {
-            case 2: k_march_fwd_split<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd_split<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        switch (W) {
+            case 1: k_march_fwd_pair<1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 2: k_march_fwd_pair<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd_pair<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

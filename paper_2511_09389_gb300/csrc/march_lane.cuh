@@ -65,32 +65,6 @@ struct RayState {
     float I[W], tau[W];
 };
 
-// A slice of WL bins out of a packed WP-wide cell vector (split lanes: WP / WL adjacent lanes
-// share one ray, lane `sub` owns bins [sub * WL, sub * WL + WL)).
-template <int WL, int WP>
-__device__ __forceinline__ Vec<WL> ldg_slice(const float* __restrict__ p, int cell, int sub) {
-    const float* q = p + (size_t)cell * WP + sub * WL;
-    Vec<WL> r;
-    if (WL == 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(q));
-        r.v[0] = t.x; r.v[1 % WL] = t.y; r.v[2 % WL] = t.z; r.v[3 % WL] = t.w;
-    } else if (WL == 2) {
-        const float2 t = __ldg(reinterpret_cast<const float2*>(q));
-        r.v[0] = t.x; r.v[1 % WL] = t.y;
-    } else {
-        r.v[0] = __ldg(q);
-    }
-    return r;
-}
-
-template <int WL, int WP>
-__device__ __forceinline__ void red_slice(float* __restrict__ p, int cell, int sub, const float* v) {
-    float* q = p + (size_t)cell * WP + sub * WL;
-    if (WL == 4) red_add4(q, v[0], v[1 % WL], v[2 % WL], v[3 % WL]);
-    else if (WL == 2) red_add2(q, v[0], v[1 % WL]);
-    else red_add(q, v[0]);
-}
-
 // Send one merged deposit (the sums for one corner) to memory: a W-wide FP32 reduction, or in
 // deterministic mode one 64-bit fixed-point reduction per real bin (integer addition is
 // associative, so the result does not depend on the order of the deposits).
@@ -138,83 +112,6 @@ __device__ __forceinline__ void flush_run(const Lane& L, const int* pc, const fl
 #pragma unroll
         for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
     }
-}
-
-// PF = 1: the gathers of substep k+1 are issued before the update of substep k (positions do
-// not depend on I, so they can run ahead), which doubles the loads in flight per thread.
-// PF = 0: gathers are issued only when the corner set (or the kappa cell) changes; otherwise
-// the values from the previous substep, still in registers, are reused.
-// Split lanes: WP / WL adjacent lanes march the same ray of a WP-packed bin group, lane `sub`
-// carrying bins [sub * WL, sub * WL + WL). Same algorithm as march_lane with PF = 0 (gathers
-// reused while the corner set is unchanged, deposits merged); the lanes of a ray touch the same
-// 16-byte cell vectors, so they share cache sectors while giving the GPU more warps.
-template <int WL, int WP>
-__device__ __forceinline__ void march_lane_split(const Lane& L, int sub) {
-    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
-    float x = L.sx, y = L.sy, z = L.sz;
-    float I[WL], tau[WL];
-#pragma unroll
-    for (int b = 0; b < WL; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
-    const float ds = L.ds, scale = L.scale;
-    int pc[8];
-    float pend[8][WL];
-    Vec<WL> gj[8];
-    Vec<WL> gk;
-    int gnn = -1;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        pc[c] = -1;
-#pragma unroll
-        for (int b = 0; b < WL; ++b) pend[c][b] = 0.0f;
-    }
-#pragma unroll 1
-    for (int k = 0; k < L.ns; ++k) {
-        Sample sm;
-        make_sample(x, y, z, L.n0, L.n1, L.n2, L.kappa_mode, sm);
-        const bool same = sm.cell[0] == pc[0] && sm.cell[7] == pc[7];
-        if (!same) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) gj[c] = ldg_slice<WL, WP>(L.jg, sm.cell[c], sub);
-        }
-        if (sm.nn != gnn) {
-            gk = ldg_slice<WL, WP>(L.kg, sm.nn, sub);
-            gnn = sm.nn;
-        }
-        float dep[WL];
-#pragma unroll
-        for (int b = 0; b < WL; ++b) {
-            float jk = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gj[c].v[b], jk);
-            const float kds = gk.v[b] * ds;
-            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
-            const float em = neg_exp(tau[b]);             // exp(-tau_k)
-            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
-            tau[b] += kds;                                // Eq. 2: tau_{k+1}
-            dep[b] = I[b] * scale;
-        }
-        if (!same) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                if (pc[c] >= 0) red_slice<WL, WP>(L.og, pc[c], sub, pend[c]);
-                pc[c] = sm.cell[c];
-#pragma unroll
-                for (int b = 0; b < WL; ++b) pend[c][b] = sm.w[c] * dep[b];
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-#pragma unroll
-                for (int b = 0; b < WL; ++b) pend[c][b] = fmaf(sm.w[c], dep[b], pend[c][b]);
-            }
-        }
-        x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
-        y = __fadd_rn(y, dy);
-        z = __fadd_rn(z, dz);
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-        if (pc[c] >= 0) red_slice<WL, WP>(L.og, pc[c], sub, pend[c]);
 }
 
 // PF = 2: prefetch and reuse combined. The corner set of substep k+1 is computed one step
@@ -600,6 +497,122 @@ __device__ __forceinline__ void march_lane_runs(const Lane& L, RayState<W>& R) {
 #pragma unroll
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
     (void)og;
+}
+
+// Two adjacent lanes march one ray with corner slots (lanes per ray = 2): lane `sub` keeps the
+// four slots whose axis-2 bit is `sub`, so each lane gathers, merges and flushes half of the
+// corners, and the workload has twice the warps. Both lanes compute the geometry and the
+// radiometry of Eq. 2 alike; the two halves of the trilinear sum of j are exchanged with one
+// shuffle per bin (a + b and b + a are the same FP32 number, so both lanes carry identical I
+// and tau). pmask holds the pair's two lanes.
+template <int W>
+__device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned pmask) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = L.sx, y = L.sy, z = L.sz;
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    const float ds = L.ds, scale = L.scale;
+    int pc[4];           // slot i of this lane is slot 2 i + sub of the ray: its cell, -1 while empty
+    float pend[4][W];
+    Vec<W> gj[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        pc[i] = -1;
+#pragma unroll
+        for (int b = 0; b < W; ++b) { pend[i][b] = 0.0f; gj[i].v[b] = 0.0f; }
+    }
+    int rl0 = -2, rh0 = -2, rl1 = -2, rh1 = -2, rl2 = -2, rh2 = -2;
+    int P0 = 0, P1 = 0, P2 = 0;
+    Vec<W> gk;
+#pragma unroll
+    for (int b = 0; b < W; ++b) gk.v[b] = 0.0f;
+    int gnn = -1;
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        const Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, L.n1), a2 = axis_sample(z, L.n2);
+        const int key0 = a0.lo | (a0.hi << 16), key1 = a1.lo | (a1.hi << 16), key2 = a2.lo | (a2.hi << 16);
+        const bool same0 = key0 == (rl0 | (rh0 << 16)), same1 = key1 == (rl1 | (rh1 << 16)),
+                   same2 = key2 == (rl2 | (rh2 << 16));
+        const bool up0 = !same0 && a0.lo == rh0, up1 = !same1 && a1.lo == rh1, up2 = !same2 && a2.lo == rh2;
+        const bool dn0 = !same0 && !up0 && a0.hi == rl0, dn1 = !same1 && !up1 && a1.hi == rl1,
+                   dn2 = !same2 && !up2 && a2.hi == rl2;
+        const bool change = !(same0 && same1 && same2);
+        bool flag[4];
+        if (change) {
+            const bool other = !(same0 || up0 || dn0) || !(same1 || up1 || dn1) || !(same2 || up2 || dn2);
+            const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
+            const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
+            unsigned mask = other ? 0xFFu : 0u;   // leaving slots of the ray, as in march_lane_slots
+            mask |= sh0 ? (q0 ? 0xF0u : 0x0Fu) : 0u;
+            mask |= sh1 ? (q1 ? 0xCCu : 0x33u) : 0u;
+            mask |= sh2 ? (q2 ? 0xAAu : 0x55u) : 0u;
+            mask >>= sub;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                flag[i] = (mask >> (2 * i)) & 1u;
+                red_vec_if<W>(flag[i] && pc[i] >= 0, L.og, max(pc[i], 0), pend[i]);
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[i][b] = flag[i] ? 0.0f : pend[i][b];
+            }
+            P0 ^= sh0 ? 1 : 0; P1 ^= sh1 ? 1 : 0; P2 ^= sh2 ? 1 : 0;
+            rl0 = a0.lo; rh0 = a0.hi; rl1 = a1.lo; rh1 = a1.hi; rl2 = a2.lo; rh2 = a2.hi;
+        }
+        const int c00 = P0 ? a0.hi : a0.lo, c01 = P0 ? a0.lo : a0.hi;
+        const int c10 = P1 ? a1.hi : a1.lo, c11 = P1 ? a1.lo : a1.hi;
+        const int c2 = (P2 ^ sub) ? a2.hi : a2.lo;   // this lane's axis-2 coordinate
+        const float u0 = 1.0f - a0.t, u1 = 1.0f - a1.t, u2 = 1.0f - a2.t;
+        const float f00 = P0 ? a0.t : u0, f01 = P0 ? u0 : a0.t;
+        const float f10 = P1 ? a1.t : u1, f11 = P1 ? u1 : a1.t;
+        const float f2 = (P2 ^ sub) ? a2.t : u2;
+        float w[4];
+        w[0] = (f00 * f10) * f2; w[1] = (f00 * f11) * f2; w[2] = (f01 * f10) * f2; w[3] = (f01 * f11) * f2;
+        if (change) {
+            const int cell[4] = {(c00 * L.n1 + c10) * L.n2 + c2, (c00 * L.n1 + c11) * L.n2 + c2,
+                                 (c01 * L.n1 + c10) * L.n2 + c2, (c01 * L.n1 + c11) * L.n2 + c2};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (flag[i]) {
+                    gj[i] = ldg_vec<W>(jg, cell[i]);
+                    pc[i] = cell[i];
+                }
+            }
+        }
+        const int nn = L.kappa_mode == 0 ? (a0.lo * L.n1 + a1.lo) * L.n2 + a2.lo
+                                         : (nearest_round(x, L.n0) * L.n1 + nearest_round(y, L.n1)) * L.n2 +
+                                               nearest_round(z, L.n2);
+        if (nn != gnn) {
+            gk = ldg_vec<W>(kg, nn);
+            gnn = nn;
+        }
+        float dep[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float part = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) part = fmaf(w[i], gj[i].v[b], part);
+            const float jk = part + __shfl_xor_sync(pmask, part, 1);
+            const float kds = gk.v[b] * ds;
+            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);               // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);           // Eq. 2: I_{k+1}
+            tau[b] += kds;                                  // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int b = 0; b < W; ++b) pend[i][b] = fmaf(w[i], dep[b], pend[i][b]);
+        }
+        x = __fadd_rn(x, dx);                               // Eq. 2: x_{k+1}
+        y = __fadd_rn(y, dy);
+        z = __fadd_rn(z, dz);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (pc[i] >= 0) red_vec<W>(L.og, pc[i], pend[i]);
 }
 
 // Gathers modes: PF = 0 march_lane_slots, 1 and 3 march_lane_runs, 2 march_lane_ahead. REC

@@ -257,7 +257,7 @@ int num_substeps(float ds, float c, float dt, int cap) { return rt::substeps(ds,
 }  // namespace
 
 // Widths W in {the default, 2, 1} that fit n_freq; 32, 64, 128, 256 threads per block; gather
-// modes 0, 1, 2, 3 with and without source tiles; for W = 4 also 2 and 4 lanes per ray.
+// modes 0, 1, 2, 3 with and without source tiles, and mode 0 with two lanes per ray.
 int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int widths[3], nw = 0;
     widths[nw++] = n_freq == 1 ? 1 : (n_freq == 2 ? 2 : 4);
@@ -266,13 +266,13 @@ int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int n = 0;
     for (int wi = 0; wi < nw; ++wi)
         for (int b : {32, 64, 128, 256})
-            for (int cand = 0; cand < (widths[wi] == 4 ? 10 : 8); ++cand) {
+            for (int cand = 0; cand < 9; ++cand) {
                 MarchPlan p;
                 p.W = widths[wi];
                 p.block = b;
                 p.prefetch = cand < 8 ? cand >> 1 : 0;
                 p.tile = cand < 8 ? (cand & 1) : 0;
-                p.lpr = cand >= 8 ? (cand == 8 ? 2 : 4) : 1;
+                p.lpr = cand == 8 ? 2 : 1;
                 out[n++] = p;
             }
     return n;
@@ -417,7 +417,7 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
             g->last_plan_ms = e.second.second;
             return RT_OK;
         }
-    rt::MarchPlan cands[104];
+    rt::MarchPlan cands[108];
     const int n_cand = rt::march_plan_candidates(a.n_freq, cands);
     cudaEvent_t e[2] = {nullptr, nullptr};
     float best_ms = 3.0e38f;
@@ -549,7 +549,8 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (g->opt.plan_prefetch) plan.prefetch = g->opt.plan_prefetch - 1;
     if (g->opt.plan_lanes) plan.lpr = g->opt.plan_lanes;
     if (g->opt.plan_tile) plan.tile = g->opt.plan_tile - 1;
-    if (plan.lpr > 1 && (plan.W != 4 || plan.prefetch)) return fail(RT_ERR_INVALID_ARG, "plan_lanes > 1 needs 4 bins per group and gathers mode 0");
+    if (plan.lpr != 1 && (plan.lpr != 2 || plan.prefetch))
+        return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 1, or 2 with gathers mode 0");
     g->last_plan_ms = -1.0f;
     if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
     if (a.st_I && plan.lpr > 1) {   // the stateful march runs one lane per (ray, source, bin group)

@@ -181,7 +181,7 @@ struct rt_batch {
     rt_status tune_dedicated(Dedicated& d, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
         const rt::BatchInst& b = host[d.inst];
         const size_t accb = sizeof(float) * (size_t)b.groups * b.n0 * b.n1 * b.n2 * b.W;
-        rt::MarchPlan cands[104];
+        rt::MarchPlan cands[108];
         const int n = rt::march_plan_candidates(b.n_freq, cands);
         float best = 3.0e38f;
         Dedicated win = d;

@@ -43,7 +43,7 @@ struct MarchArgs {
                             // sets keeps its gathers and sums); 1: the next substep's gathers
                             // issued before the current update; 2: both; 3: the whole corner set
                             // reused while unchanged, flushed and re-gathered when it changes
-    int lanes_per_ray;      // 1, or 2 / 4 adjacent lanes sharing a ray of a 4-bin group
+    int lanes_per_ray;      // 1, or 2 adjacent lanes sharing a ray (each with half of its corner slots)
     int tile;               // 1: source deposit tiles in shared memory (FP32 mode, one lane per ray)
     // stateful advance (NULL st_I: none): st_I / st_tau [n_freq][nsrc][ray_count], positions
     // [nsrc][ray_count][3] read from st_pos_in when st_read and written to st_pos_out (a
@@ -66,7 +66,7 @@ struct MarchPlan {
     int W, block, prefetch, lpr, tile;
 };
 // The plans the autotuners time for n_freq bins (rt_api.cu for single calls, rt_batch.cu for the
-// batch's dedicated instances), at most 104; returns how many were written to out.
+// batch's dedicated instances), at most 108; returns how many were written to out.
 int march_plan_candidates(int n_freq, MarchPlan* out);
 
 // [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).

@@ -218,7 +218,7 @@ def test_deterministic_mode_full_size(torch_cuda):
     assert_parity(a, run_oracle(p))
 
 
-@pytest.mark.parametrize("plan", [(4, 64, 0, 2), (4, 128, 0, 4), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
+@pytest.mark.parametrize("plan", [(4, 64, 0, 2), (1, 128, 0, 2), (2, 32, 0, 2), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
                                   (1, 32, 0, 1), (4, 32, 0, 1, 1), (2, 128, 1, 1, 1), (1, 64, 1, 1, 1),
                                   (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0), (4, 32, 3, 1),
                                   (2, 64, 3, 1, 0), (1, 64, 3, 1, 1), (4, 64, 3, 1, 1)])
@@ -254,7 +254,7 @@ def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
 
 
 @pytest.mark.parametrize("step_size", [0.13, 0.5, 1.0, 1.7, 3.2])
-@pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3)])
+@pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3), (4, 32, 0, 2), (1, 64, 0, 2)])
 def test_corner_slots_across_step_sizes(torch_cuda, plan, step_size):
     """Gathers mode 0 keeps a face shared by consecutive corner sets (a step of one cell along an
     axis) and flushes everything else. Steps much shorter than a cell (long runs in one set), of
