@@ -162,7 +162,7 @@ __device__ __forceinline__ void march_lane_ahead(const Lane& L, RayState<W>& R) 
 #pragma unroll
             for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
             const float kds = gd.k.v[b] * ds;
-            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
             const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
             tau[b] += kds;                                // Eq. 2: tau_{k+1}
@@ -293,8 +293,17 @@ __device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) 
                 } else {
                     flush_if<W, DET>(send, L, max(pc[c], 0), pend[c]);
                 }
+                if constexpr (W % 2 == 0) {   // a flushed slot starts again from zero
+                    const float keep = flag[c] ? 0.0f : 1.0f;
 #pragma unroll
-                for (int b = 0; b < W; ++b) pend[c][b] = flag[c] ? 0.0f : pend[c][b];
+                    for (int h = 0; h < W; h += 2) {
+                        const float2 v = __fmul2_rn(make_float2(pend[c][h], pend[c][h + 1]), make_float2(keep, keep));
+                        pend[c][h] = v.x; pend[c][h + 1] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < W; ++b) pend[c][b] = flag[c] ? 0.0f : pend[c][b];
+                }
             }
             P0 ^= sh0 ? 1 : 0; P1 ^= sh1 ? 1 : 0; P2 ^= sh2 ? 1 : 0;
             rl0 = a0.lo; rh0 = a0.hi; rl1 = a1.lo; rh1 = a1.hi; rl2 = a2.lo; rh2 = a2.hi;
@@ -342,22 +351,53 @@ __device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) 
             gnn = nn;
         }
         float dep[W];
+        if constexpr (W % 2 == 0) {
+            // bins in pairs: the paired FP32 instructions compute two round-to-nearest results
+            // each, the same numbers as the scalar code below
 #pragma unroll
-        for (int b = 0; b < W; ++b) {
-            float jk = 0.0f;
+            for (int h = 0; h < W; h += 2) {
+                float2 jk = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) jk = fmaf(w[c], gj[c].v[b], jk);
-            const float kds = gk.v[b] * ds;
-            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
-            const float em = neg_exp(tau[b]);             // exp(-tau_k)
-            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
-            tau[b] += kds;                                // Eq. 2: tau_{k+1}
-            dep[b] = I[b] * scale;
-        }
+                for (int c = 0; c < 8; ++c)
+                    jk = __ffma2_rn(make_float2(w[c], w[c]), make_float2(gj[c].v[h], gj[c].v[h + 1]), jk);
+                const float2 kds = __fmul2_rn(make_float2(gk.v[h], gk.v[h + 1]), make_float2(ds, ds));
+                const float2 att = make_float2(neg_exp(kds.x), neg_exp(kds.y));       // exp(-kappa(x_k) ds)
+                const float2 em = make_float2(neg_exp(tau[h]), neg_exp(tau[h + 1]));  // exp(-tau_k)
+                const float2 e = __fmul2_rn(__fmul2_rn(jk, em), make_float2(ds, ds));
+                const float2 In = __ffma2_rn(make_float2(I[h], I[h + 1]), att, e);    // Eq. 2: I_{k+1}
+                const float2 tn = __fadd2_rn(make_float2(tau[h], tau[h + 1]), kds);   // Eq. 2: tau_{k+1}
+                const float2 d = __fmul2_rn(In, make_float2(scale, scale));
+                I[h] = In.x; I[h + 1] = In.y;
+                tau[h] = tn.x; tau[h + 1] = tn.y;
+                dep[h] = d.x; dep[h + 1] = d.y;
+            }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < 8; ++c) {
 #pragma unroll
-            for (int b = 0; b < W; ++b) pend[c][b] = fmaf(w[c], dep[b], pend[c][b]);
+                for (int h = 0; h < W; h += 2) {
+                    const float2 v = __ffma2_rn(make_float2(w[c], w[c]), make_float2(dep[h], dep[h + 1]),
+                                                make_float2(pend[c][h], pend[c][h + 1]));
+                    pend[c][h] = v.x; pend[c][h + 1] = v.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                float jk = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) jk = fmaf(w[c], gj[c].v[b], jk);
+                const float kds = gk.v[b] * ds;
+                const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
+                const float em = neg_exp(tau[b]);             // exp(-tau_k)
+                I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+                tau[b] += kds;                                // Eq. 2: tau_{k+1}
+                dep[b] = I[b] * scale;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = fmaf(w[c], dep[b], pend[c][b]);
+            }
         }
         x = __fadd_rn(x, dx);                             // Eq. 2: x_{k+1}
         y = __fadd_rn(y, dy);
@@ -462,7 +502,7 @@ __device__ __forceinline__ void march_lane_runs(const Lane& L, RayState<W>& R) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], gd.j[c].v[b], jk);
             const float kds = gd.k.v[b] * ds;
-            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
             const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
             tau[b] += kds;                                // Eq. 2: tau_{k+1}
@@ -595,7 +635,7 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
             for (int i = 0; i < 4; ++i) part = fmaf(w[i], gj[i].v[b], part);
             const float jk = part + __shfl_xor_sync(pmask, part, 1);
             const float kds = gk.v[b] * ds;
-            const float att = neg_exp(kds);                 // exp(-kappa(x_k) ds)
+            const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
             const float em = neg_exp(tau[b]);               // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);           // Eq. 2: I_{k+1}
             tau[b] += kds;                                  // Eq. 2: tau_{k+1}
