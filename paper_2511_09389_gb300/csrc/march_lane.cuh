@@ -636,7 +636,7 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
             const float jk = part + __shfl_xor_sync(pmask, part, 1);
             const float kds = gk.v[b] * ds;
             const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
-            const float em = neg_exp(tau[b]);               // exp(-tau_k)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
             I[b] = fmaf(I[b], att, jk * em * ds);           // Eq. 2: I_{k+1}
             tau[b] += kds;                                  // Eq. 2: tau_{k+1}
             dep[b] = I[b] * scale;
