@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
 }
 
 // Lanes per ray = 2: adjacent lanes (sub = threadIdx.x & 1) share one (ray, source, bin group),
-// each with half of its corner slots (march_lane_pair).
-template <int W>
+// each with half of its corner slots (march_lane_pair). REC: also the reverse march's checkpoints.
+template <int W, bool REC = false>
 __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     const int rays_per_block = blockDim.x / 2;
     const int rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
@@ -139,23 +139,32 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
-    march_lane_pair<W>(L, sub, pmask);
+    if (REC) {
+        L.ck_lanes = (long long)a.ray_count * a.nsrc * a.groups;
+        L.ck = a.ckpt + ((long long)g * a.nsrc + s) * a.ray_count + r;
+        L.ck_stride = a.ck_stride;
+    }
+    march_lane_pair<W, REC>(L, sub, pmask);
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     if (a.lanes_per_ray > 1) {
         // two lanes per ray: block counts threads (a multiple of 32), block / 2 rays per block
-        if (a.lanes_per_ray != 2 || a.acc64 || a.st_I || a.ckpt || a.prefetch != 0) return cudaErrorInvalidValue;
+        if (a.lanes_per_ray != 2 || a.acc64 || a.st_I || a.prefetch != 0 || (a.ckpt && a.ck_stride < 1))
+            return cudaErrorInvalidValue;
         const int block = a.block > 0 ? a.block : 64;
         if (block % 32) return cudaErrorInvalidValue;
         const long long rblocks = (a.ray_count + block / 2 - 1) / (block / 2);
         const long long nblk = rblocks * a.nsrc * a.groups;
         if (nblk <= 0) return cudaSuccess;
         if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        switch (W) {
-            case 1: k_march_fwd_pair<1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 2: k_march_fwd_pair<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd_pair<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
+        switch (W * 2 + (a.ckpt ? 1 : 0)) {
+            case 2: k_march_fwd_pair<1><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 3: k_march_fwd_pair<1, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 4: k_march_fwd_pair<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 5: k_march_fwd_pair<2, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 8: k_march_fwd_pair<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
+            case 9: k_march_fwd_pair<4, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

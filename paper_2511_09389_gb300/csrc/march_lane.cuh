@@ -544,8 +544,9 @@ __device__ __forceinline__ void march_lane_runs(const Lane& L, RayState<W>& R) {
 // corners, and the workload has twice the warps. Both lanes compute the geometry and the
 // radiometry of Eq. 2 alike; the two halves of the trilinear sum of j are exchanged with one
 // shuffle per bin (a + b and b + a are the same FP32 number, so both lanes carry identical I
-// and tau). pmask holds the pair's two lanes.
-template <int W>
+// and tau). pmask holds the pair's two lanes. REC: lane 0 of the pair stores the reverse march's
+// checkpoints (x_k, I_k, tau_k) every ck_stride substeps (both lanes hold the same values).
+template <int W, bool REC = false>
 __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned pmask) {
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
@@ -570,8 +571,25 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
 #pragma unroll
     for (int b = 0; b < W; ++b) gk.v[b] = 0.0f;
     int gnn = -1;
+    int ck_left = 0;     // REC: substeps until the next checkpoint
+    float* ckp = L.ck;   // REC: this lane's next checkpoint
 #pragma unroll 1
     for (int k = 0; k < L.ns; ++k) {
+        if (REC) {
+            if (ck_left == 0) {
+                if (sub == 0) {
+                    ckp[0] = x; ckp[L.ck_lanes] = y; ckp[2 * L.ck_lanes] = z;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        ckp[(3 + b) * L.ck_lanes] = I[b];
+                        ckp[(3 + W + b) * L.ck_lanes] = tau[b];
+                    }
+                }
+                ckp += (3 + 2 * W) * L.ck_lanes;
+                ck_left = L.ck_stride;
+            }
+            --ck_left;
+        }
         const Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, L.n1), a2 = axis_sample(z, L.n2);
         const int key0 = a0.lo | (a0.hi << 16), key1 = a1.lo | (a1.hi << 16), key2 = a2.lo | (a2.hi << 16);
         const bool same0 = key0 == (rl0 | (rh0 << 16)), same1 = key1 == (rl1 | (rh1 << 16)),

@@ -557,21 +557,22 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         plan.lpr = 1;
         plan.prefetch = 0;
     }
-    // record the reverse march's checkpoints: its bin grouping, one lane per ray; gathers mode 0,
-    // or for one bin per thread mode 3 (measured on GB300, 64^3 with 24,576 lanes: 0.16 ms against
-    // 0.18 for mode 1 and 0.24 for mode 0) unless a plan with mode 0, 1 or 3 was pinned or tuned
+    // record the reverse march's checkpoints with the adjoint's bin grouping: gathers mode 0 with
+    // one lane per ray, or for one bin per thread two lanes per ray (measured on GB300, 64^3 with
+    // 24,576 lanes: 0.12 ms against 0.16 for mode 3, 0.16 for mode 1 and 0.24 for mode 0 with one
+    // lane), unless a plan with gathers mode 0, 1 or 3 was pinned or tuned
     const bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
     if (record) {
         const int w = pick_width(a.n_freq);
-        const bool keep = plan.W == w && plan.lpr == 1 && (g->opt.plan_prefetch || g->opt.autotune);
-        if (plan.W != w) {
+        const bool keep = plan.W == w && (g->opt.plan_prefetch || g->opt.plan_lanes || g->opt.autotune);
+        if (!keep) {
             plan.block = 32;
-            plan.tile = w == 1 ? 1 : 0;
+            plan.tile = 0;
+            plan.lpr = w == 1 ? 2 : 1;
         }
         plan.W = w;
-        plan.lpr = 1;
-        if (w != 1) plan.prefetch = 0;
-        else if (!keep || plan.prefetch == 2) plan.prefetch = 3;
+        if (plan.lpr == 2 || w != 1) plan.prefetch = 0;   // corner slots
+        else if (plan.prefetch == 2) plan.prefetch = 3;   // (recording has no gathers mode 2)
     }
     g->last_plan = plan;
 

@@ -232,7 +232,8 @@ def test_autograd_sources_kappa_scale_and_amplitudes(torch_cuda):
     assert rel(S.grad.cpu().numpy(), dS) <= GRAD_REL
 
 
-@pytest.mark.parametrize("n_freq,stride,plan", [(1, 16, None), (3, 8, None), (5, 32, (4, 64, 0, 2, 1)), (2, 16, None)])
+@pytest.mark.parametrize("n_freq,stride,plan", [(1, 16, None), (3, 8, None), (5, 32, (4, 64, 0, 2, 1)), (2, 16, None),
+                                                 (1, 16, (1, 32, 0, 2)), (2, 8, (2, 64, 0, 2))])
 def test_recorded_checkpoints_give_the_same_gradients(torch_cuda, n_freq, stride, plan):
     """record_checkpoints: the forward march stores the reverse march's checkpoints and the
     adjoint skips its forward sweep; gradients as without it. A backward whose arguments
