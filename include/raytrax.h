@@ -90,7 +90,8 @@ typedef struct {
                            synchronises the stream (one pass over the inputs). 0: no scan. */
     int record_checkpoints; /* 1: every full-range rt_advance also stores the reverse march's
                            checkpoints (every ckpt_stride substeps) in the handle, marching
-                           with the adjoint's bin grouping and gathers mode 0; a following
+                           with the adjoint's bin grouping (gathers mode 0; for one bin, two
+                           lanes per ray unless a plan is pinned or tuned); a following
                            rt_backward / rt_backward_sources with the same j_map, kappa_map and
                            source_pos pointers and the same scalars uses them instead of
                            repeating the forward sweep. The caller must not change the contents
