@@ -797,15 +797,31 @@ rt_status rt_advance_host_async(rt_grid* g, const float* j_map, const float* kap
         return fail(RT_ERR_INVALID_ARG, "host buffers must be non-NULL");
     rt_status st = check_device(g);
     if (st != RT_OK) return st;
+    {   // argument errors return before anything is enqueued
+        Call probe{j_map, kappa_map, source_pos, num_sources, num_rays, 0, num_rays, step_size, radiation_velocity,
+                   time_step, n_freq, out_field, 0, (cudaStream_t)cuda_stream};
+        int ns = 0;
+        if ((st = validate(g, probe, &ns)) != RT_OK) return st;
+    }
     auto& P = g->pipe;
-    if (!P.h2d) {
-        RT_CUDA(cudaStreamCreateWithFlags(&P.h2d, cudaStreamNonBlocking), "cudaStreamCreate(copy in)");
-        RT_CUDA(cudaStreamCreateWithFlags(&P.d2h, cudaStreamNonBlocking), "cudaStreamCreate(copy out)");
-        for (int i = 0; i < 2; ++i) {
-            RT_CUDA(cudaEventCreateWithFlags(&P.in_ready[i], cudaEventDisableTiming), "cudaEventCreate");
-            RT_CUDA(cudaEventCreateWithFlags(&P.done[i], cudaEventDisableTiming), "cudaEventCreate");
-            RT_CUDA(cudaEventCreateWithFlags(&P.out_done[i], cudaEventDisableTiming), "cudaEventCreate");
+    if (!P.h2d) {   // all or nothing: a failed set-up leaves no half-made pipeline behind
+        rt_grid::HostPipe q;
+        cudaError_t e = cudaStreamCreateWithFlags(&q.h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q.d2h, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&q.in_ready[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.done[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.out_done[i], cudaEventDisableTiming);
         }
+        if (e != cudaSuccess) {
+            for (int i = 0; i < 2; ++i)
+                for (cudaEvent_t ev : {q.in_ready[i], q.done[i], q.out_done[i]})
+                    if (ev) cudaEventDestroy(ev);
+            if (q.h2d) cudaStreamDestroy(q.h2d);
+            if (q.d2h) cudaStreamDestroy(q.d2h);
+            return cuda_fail(e, "host pipeline set-up");
+        }
+        P = q;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int b = (int)(P.calls & 1);

@@ -125,9 +125,26 @@ def test_join_orders_a_stream_after_the_copies(torch_cuda):
     g.host_wait()   # nothing left: returns at once
 
 
-def test_rejects_null_buffers(torch_cuda):
-    from paper_2511_09389_gb300.api import Grid
-    g = Grid((8, 8, 8), 1)
+def test_rejects_bad_arguments_before_enqueueing(torch_cuda):
+    """NULL buffers and bad scalars return INVALID_ARG with nothing enqueued; the handle's next
+    pipelined call still works."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid, RTError
+    g = Grid((8, 8, 8), 1, deterministic=True)
     st = g._lib.rt_advance_host_async(g._h, None, None, None, 0, 16, 0.5, 1.0, 2.0, 1, None, None)
     assert st == 1   # RT_ERR_INVALID_ARG
     assert g._lib.rt_host_wait(g._h) == 0
+    p = inputs.random_small(35, shape=(8, 8, 8), n_freq=1, n_src=2, num_rays=64, step_size=0.5, horizon=4.0)
+    jh, kh, sh = pinned(torch, p.j), pinned(torch, p.kappa), pinned(torch, p.sources)
+    out = torch.empty(jh.shape, dtype=torch.float32).pin_memory()
+    for bad in (dict(num_rays=0), dict(step_size=0.0), dict(time_step=-1.0)):
+        kw = dict(num_rays=p.num_rays, step_size=p.step_size, time_step=p.time_step)
+        kw.update(bad)
+        with pytest.raises(RTError, match="INVALID_ARG"):
+            g.advance_host_async(jh, kh, sh, kw["num_rays"], kw["step_size"], 1.0, kw["time_step"], out=out)
+    g.host_wait()
+    g.advance_host_async(jh, kh, sh, p.num_rays, p.step_size, 1.0, p.time_step, out=out)
+    g.host_wait()
+    want = Grid(p.shape, 1, deterministic=True).advance(jh.cuda(), kh.cuda(), sh.cuda(), p.num_rays,
+                                                        p.step_size, 1.0, p.time_step).cpu()
+    assert torch.equal(out, want)
