@@ -631,12 +631,9 @@ cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
     if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2) return cudaErrorInvalidValue;
     CUtensorMap map;
     if (!make_map(&map, c.x, c.B, c.D, c.H, c.W)) return cudaErrorInvalidValue;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, kChainBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // per launch: the attribute belongs to the current device's context (a few microseconds)
+    cudaError_t ea = cudaFuncSetAttribute(k_conv3d_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, kChainBytes);
+    if (ea != cudaSuccess) return ea;
     ConvArgs a{};
     a.w_packed = reinterpret_cast<const uint4*>(c.w_packed);
     a.bias = c.bias;
@@ -666,12 +663,8 @@ cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st) {
         return cudaErrorInvalidValue;
     // at most two CTAs per SM: each holds 256 tensor-memory columns of the SM's 512
     const int bytes = kWgBytes < 100 * 1024 ? 100 * 1024 : kWgBytes;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t ea = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (ea != cudaSuccess) return ea;
     WgradArgs a{};
     a.dw = c.dw;
     a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
