@@ -509,7 +509,9 @@ def native_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "updates_per_step": U, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "kernel_ms": kms, "wall_s": wall, "launch_plan": g.last_plan()},
+                   "kernel_ms": kms, "wall_s": wall, "launch_plan": g.last_plan(),
+                   "median_ms_per_step": statistics.median(step_ms), "median_kernel_ms": statistics.median(kern_ms),
+                   "timing": "value and ms_per_step use the mean over the K timed steps; medians beside them"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "basis": f"{ALGO_BYTES_PER_UPDATE} algorithmic bytes per update x {U} updates per launch / "
