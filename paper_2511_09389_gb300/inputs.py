@@ -108,8 +108,9 @@ def turbulent(n: int = 128, n_src: int = 16, num_rays: int = 3072, step_size: fl
 
 def paper_timing(n: int = 128, fraction: float = 0.001, num_rays: int = 4096, step_size: float = 0.5,
                  horizon: float = 128.0, blob_sigma: float = 1.5, seed: int = 5000) -> Problem:
-    """The paper's timing run (Sec. 3) with a synthetic medium: lognormal kappa on 128^3 (sigma_g
-    1, mean 0.05), sources at the `fraction` = 0.1 % cells of highest kappa (2097), each the
+    """The paper's timing run (Sec. 2; sources placed as in Sec. 3) with a synthetic medium:
+    lognormal kappa on 128^3 (sigma_g 1, mean 0.05), sources at the `fraction` = 0.1 % cells of
+    highest kappa (2097), each the
     centre of a Gaussian j blob (sigma 1.5, amplitude log-uniform in [0.1, 10]), N_Omega 4096,
     ds 0.5, one bin. The paper does not state its horizon; c dt = 128 (N_s 256) is assumed.
     Sources are listed by decreasing kappa (ties by cell index)."""

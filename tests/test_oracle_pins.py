@@ -5,7 +5,9 @@ uniform media, the analytic point-source solution (Eq. 3), limits, linearity, a 
 double-sum form of the recursion built on scipy's trilinear interpolation, exact identities
 of the adjoint, finite differences and the closed-form minimiser of the inversion (Sec. 4).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -13,6 +15,10 @@ from scipy.ndimage import map_coordinates
 
 import oracle
 from paper_2511_09389_gb300 import inputs
+
+# numbers the paper prints, each with its passage (small text fixture)
+with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.json")) as _f:
+    PAPER = json.load(_f)
 
 FOUR_PI = 4.0 * math.pi
 
@@ -232,7 +238,26 @@ def test_analytic_point_source_shape():
         bias = np.mean(F[m] / Jref[m] - 1.0)
         assert abs(bias) < 0.02, (lo, bias)
     err = np.mean(np.abs(F[mask] - Jref[mask]) / Jref[mask])
-    assert err < 0.05        # the paper reports 3.16 % average relative error
+    # the paper's average relative error against Eq. 3 (its N_Omega and ds are not stated): the
+    # oracle with N_Omega 3072, ds 0.5 and the same exclusions is at least as close
+    assert err <= PAPER["analytic_validation"]["mean_relative_error"], err
+
+
+def test_timing_run_recipe_matches_the_printed_workload():
+    """The synthetic stand-in for the paper's timing run has its printed shape: a 128^3 grid, 4,096
+    rays and 2,097 sources, the 0.1 % highest-kappa cells (Sec. 2 timing, Sec. 3 source placement)."""
+    t = PAPER["timing_run"]
+    p = inputs.paper_timing()
+    assert p.shape == (t["grid_edge"],) * 3
+    assert p.num_rays == t["num_rays"]
+    assert len(p.sources) == t["num_sources"]
+    assert len(p.sources) == round(PAPER["turbulent_sources"]["fraction_of_cells"] * t["grid_edge"] ** 3)
+    # the sources are the highest-kappa cells: every source cell's kappa >= every other cell's
+    kap = p.kappa[0]
+    idx = tuple(p.sources.astype(int).T)
+    others = np.ones(kap.shape, bool)
+    others[idx] = False
+    assert kap[idx].min() >= kap[others].max()
 
 
 def test_analytic_convergence_monotone():
