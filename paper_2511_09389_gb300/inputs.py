@@ -110,10 +110,9 @@ def paper_timing(n: int = 128, fraction: float = 0.001, num_rays: int = 4096, st
                  horizon: float = 128.0, blob_sigma: float = 1.5, seed: int = 5000) -> Problem:
     """The paper's timing run (Sec. 2; sources placed as in Sec. 3) with a synthetic medium:
     lognormal kappa on 128^3 (sigma_g 1, mean 0.05), sources at the `fraction` = 0.1 % cells of
-    highest kappa (2097), each the
-    centre of a Gaussian j blob (sigma 1.5, amplitude log-uniform in [0.1, 10]), N_Omega 4096,
-    ds 0.5, one bin. The paper does not state its horizon; c dt = 128 (N_s 256) is assumed.
-    Sources are listed by decreasing kappa (ties by cell index)."""
+    highest kappa (2097), each the centre of a Gaussian j blob (sigma 1.5, amplitude log-uniform
+    in [0.1, 10]), N_Omega 4096, ds 0.5, one bin. The paper does not state its horizon; c dt =
+    128 (N_s 256) is assumed. Sources are listed by decreasing kappa (ties by cell index)."""
     kap = lognormal_field((n, n, n), 1.0, 0.05, seed)
     n_src = int(round(fraction * n ** 3))
     flat = kap.reshape(-1).astype(np.float64)
