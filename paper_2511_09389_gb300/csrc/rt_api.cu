@@ -186,6 +186,7 @@ struct rt_grid {
     long long ncell() const { return (long long)n0 * n1 * n2; }
 
     rt_status ensure(Slot s, size_t bytes, void** out) {
+        *out = nullptr;
         if (bytes == 0) bytes = 16;
         if (cap[s] < bytes) {
             if (buf[s]) {
@@ -383,7 +384,7 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
     }
     const int W = plan.W, groups = (a.n_freq + W - 1) / W;
     const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
-    void *jp, *kp, *acc;
+    void *jp = nullptr, *kp = nullptr, *acc = nullptr;
     if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::ACC, packed, &acc)) != RT_OK) return st;
@@ -514,7 +515,7 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         g->last_plan_ms = -1.0f;
         rt::MarchArgs m;
         if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
-        void *acc64, *dets;
+        void *acc64 = nullptr, *dets = nullptr;
         const int groups = (a.n_freq + plan.W - 1) / plan.W;
         const size_t acc64_bytes = sizeof(unsigned long long) * (size_t)groups * plan.W * ncell;
         if ((st = g->ensure(rt_grid::ACC64, acc64_bytes, &acc64)) != RT_OK) return st;
@@ -716,7 +717,7 @@ rt_status rt_advance_continue(rt_grid* g, const float* j_map, const float* kappa
     const bool fresh = restart || !c.valid || c.nsrc != num_sources || c.rays != num_rays || c.n_freq != n_freq ||
                        c.ds != step_size;
     const size_t lanes = (size_t)std::max(num_sources, 1) * (size_t)num_rays;
-    void *pos, *I, *tau;
+    void *pos = nullptr, *I = nullptr, *tau = nullptr;
     if ((st = g->ensure(rt_grid::STPOS, 2 * 3 * sizeof(float) * lanes, &pos)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::STI, sizeof(float) * (size_t)n_freq * lanes, &I)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::STTAU, sizeof(float) * (size_t)n_freq * lanes, &tau)) != RT_OK) return st;
@@ -768,7 +769,7 @@ rt_status rt_advance_host(rt_grid* g, const float* j_map, const float* kappa_map
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const size_t field = sizeof(float) * (size_t)n_freq * g->ncell();
     const size_t srcb = sizeof(float) * 3 * (size_t)std::max(num_sources, 1);
-    void *dj, *dk, *dout, *dsrc;
+    void *dj = nullptr, *dk = nullptr, *dout = nullptr, *dsrc = nullptr;
     if ((st = g->ensure(rt_grid::HJ, field, &dj)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::HK, field, &dk)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::HOUT, field, &dout)) != RT_OK) return st;
@@ -832,7 +833,7 @@ rt_status rt_advance_host_async(rt_grid* g, const float* j_map, const float* kap
     // growing a buffer set frees memory that enqueued copies may still use: drain the pipeline
     if (g->cap[sj] < field || g->cap[sk] < field || g->cap[so] < field || g->cap[ss] < srcb)
         if ((st = rt_host_wait(g)) != RT_OK) return st;
-    void *dj, *dk, *dout, *dsrc;
+    void *dj = nullptr, *dk = nullptr, *dout = nullptr, *dsrc = nullptr;
     if ((st = g->ensure(sj, field, &dj)) != RT_OK) return st;
     if ((st = g->ensure(sk, field, &dk)) != RT_OK) return st;
     if ((st = g->ensure(so, field, &dout)) != RT_OK) return st;
@@ -1001,7 +1002,7 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
         return g->mark(1, a.st);
     }
     const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
-    void *jp, *kp, *gp, *djp = nullptr, *dkp = nullptr;
+    void *jp = nullptr, *kp = nullptr, *gp = nullptr, *djp = nullptr, *dkp = nullptr;
     if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
     if ((st = g->ensure(rt_grid::GP, packed, &gp)) != RT_OK) return st;
