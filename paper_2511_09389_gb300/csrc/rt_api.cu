@@ -635,8 +635,8 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
     if (o.plan_block != 0 && (o.plan_block < 32 || o.plan_block > 256 || o.plan_block % 32))
         return fail(RT_ERR_INVALID_ARG, "plan_block must be 0 or a multiple of 32 in [32, 256]");
     if (o.plan_prefetch < 0 || o.plan_prefetch > 4) return fail(RT_ERR_INVALID_ARG, "plan_prefetch must be 0 .. 4");
-    if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2 && o.plan_lanes != 4)
-        return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1, 2 or 4");
+    if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2)
+        return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1 or 2");
     if (o.plan_tile < 0 || o.plan_tile > 2) return fail(RT_ERR_INVALID_ARG, "plan_tile must be 0, 1 or 2");
     rt_grid* g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ERR_OOM, "host allocation failed");

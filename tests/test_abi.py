@@ -64,3 +64,20 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.rt_create_grid(ctypes.byref(h), 2048, 2048, 1024, 1, None) == 1
     assert lib.rt_destroy(None) == 0
     assert lib.rt_direction_table(0, None) == 1
+
+
+@pytest.mark.parametrize("field,value,word", [("plan_lanes", 4, b"plan_lanes"), ("plan_lanes", 3, b"plan_lanes"),
+                                              ("plan_prefetch", 5, b"plan_prefetch"), ("plan_width", 3, b"plan_width"),
+                                              ("plan_block", 48, b"plan_block"), ("plan_tile", 3, b"plan_tile"),
+                                              ("kappa_mode", 2, b"kappa_mode"), ("ckpt_stride", -1, b"ckpt_stride")])
+def test_bad_options_rejected_at_creation(lib, field, value, word):
+    """Launch-plan and other options are checked by rt_create_grid on the host, before any device
+    call: an out-of-range value returns RT_ERR_INVALID_ARG naming the field."""
+    from paper_2511_09389_gb300 import _native
+    opt = _native.rt_options()
+    lib.rt_default_options(ctypes.byref(opt))
+    setattr(opt, field, value)
+    h = ctypes.c_void_p()
+    assert lib.rt_create_grid(ctypes.byref(h), 8, 8, 8, 1, ctypes.byref(opt)) == 1
+    assert word in lib.rt_last_error()
+    assert not h.value
