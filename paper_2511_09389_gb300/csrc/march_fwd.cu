@@ -1,8 +1,9 @@
 // march_fwd.cu -- forward march of one problem (paper Sec. 2, Eq. 2) and its layout kernels.
 //
-// One thread marches one (ray, source, bin-group) lane through all N_s substeps (march_lane.cuh).
-// Rays of a block are angular neighbours (the host sorts the lattice), so their gathers and
-// deposits share cache lines near the source.
+// One thread (or, with two lanes per ray, a pair of adjacent threads) marches one (ray, source,
+// bin-group) lane through all N_s substeps (march_lane.cuh). Rays of a block are angular
+// neighbours (the host sorts the lattice), so their gathers and deposits share cache lines near
+// the source.
 #include "march_lane.cuh"
 #include "rt_internal.h"
 

@@ -6,9 +6,12 @@
 // packed copy and each deposit is one W-wide `red.global.add.v{W}.f32`.
 //
 // Consecutive substeps of a ray often fall in the same cell (ds < 1), and once a ray has left
-// the box its clamped corners stay fixed for long stretches. The deposits of such runs are
-// summed in registers and sent to memory once, when the corner set changes: fewer L2 atomics,
-// and far fewer tiny FP32 additions into the large sums that pile up on boundary voxels.
+// the box its clamped corners stay fixed for long stretches. The deposits a corner receives are
+// summed in registers and sent to memory once: in gathers mode 0 (march_lane_slots, the
+// default) for as long as the ray keeps that corner, across face crossings; in modes 1 and 3
+// (march_lane_runs) until the corner set changes. Fewer L2 atomics, and far fewer tiny FP32
+// additions into the large sums that pile up on boundary voxels. One thread marches a lane, or
+// two adjacent threads share it (march_lane_pair).
 #pragma once
 
 #include "march_common.cuh"
