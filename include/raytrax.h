@@ -60,7 +60,10 @@ typedef struct {
                            keeps the a-priori bound 4 pi N_src ds max|j| N_s (N_s+1) / 2 below
                            2^62; needs kappa >= 0) and added as an integer: rt_advance's field is
                            bitwise identical for every launch plan and deposit order.
-                           rt_advance / rt_advance_rays only (no autotuning, no batch) */
+                           rt_advance / rt_advance_rays only (no autotuning, no batch). Honours
+                           plan_width and plan_block; rt_create_grid rejects plan_lanes 2,
+                           plan_tile 2 and plan_prefetch > 1 with it (one lane per ray, corner
+                           slots, no tiles). */
     int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
     int ns_cap;         /* 0: none; > 0: cap on the substep count (the optional cap of Sec. 2) */
     int autotune;       /* 1: time the launch shapes once per shape class and keep the best */
@@ -94,8 +97,11 @@ typedef struct {
                            lanes per ray unless a plan is pinned or tuned); a following
                            rt_backward / rt_backward_sources with the same j_map, kappa_map and
                            source_pos pointers and the same scalars uses them instead of
-                           repeating the forward sweep. The caller must not change the contents
-                           of those buffers in between (autograd guarantees it). 0: off. */
+                           repeating the forward sweep -- but only if a 64-bit content hash of
+                           j, kappa and the sources, taken on the device at the forward and again
+                           at the backward, is unchanged (decided on the device, no
+                           synchronisation): buffers rewritten in place in between get the
+                           gradients of their new contents. 0: off. */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
@@ -249,10 +255,14 @@ rt_status rt_kernel_ms(rt_grid* grid, float* ms);
    and for n_freq >= 2, 3 * ceil(n_freq / W) * W * n0 * n1 * n2 * 4 bytes (W = 2 for two bins,
    else 4) must fit in the rest of the array after the 256 KiB table (e.g. 64^3 with 4 bins);
    larger problems return RT_ERR_INVALID_ARG with the sizes in rt_last_error(). One bin needs
-   only the table. The first call on each device (with that device current) looks up the
-   array's device address, and a call with a new num_rays waits for the stream, rebuilds the
-   table and copies it in stream order, then waits again: make such calls before any stream
-   capture. All calls share the array
+   only the table. Under CUDA's default lazy module loading, the array and the kernels' code
+   are committed on a device by the first call there (with that device current), so that
+   first call can still fail for lack of memory: callers that must allocate nothing later
+   should make one warm-up call per device at start-up. Every call looks up the array's
+   device address (and starts afresh if the device's context was replaced, e.g. after
+   cudaDeviceReset); a call with a new num_rays, and the first call in a context, waits for the
+   stream, rebuilds the table and copies it in stream order, then waits again: make such calls
+   before any stream capture. All calls share the array
    and it keeps the last call's contents (the accumulator is cleared on the stream at every
    call); calls whose GPU work overlaps (other streams or host threads) race on it.
    Buffers, shapes and stream as in rt_advance; out_field is overwritten. */
@@ -403,12 +413,14 @@ rt_status rt_sync_status(void* cuda_stream);
      kind 2: the same into the 8 corners of a random cell of an edge^3 grid of vectors
              (cell-major, the march's packed accumulator layout; 8 operations per iteration);
      kind 3: read-only loads of uniformly random vectors;
-     kind 4: read-only loads of the 8 corners of a random cell of an edge^3 grid.
+     kind 4: read-only loads of the 8 corners of a random cell of an edge^3 grid;
+     kinds 5 / 6: kind 2 with 8-byte cells, red.global.add.u64 (the fixed-point deposit) /
+             red.global.add.f64 (vec must be 1).
    Addresses come from a per-thread linear congruential generator and are in bounds by
    construction. *ms = device time of the launch (CUDA events on the legacy default stream; the
    call synchronises), *ops = vector operations performed. Errors: RT_ERR_INVALID_ARG for a bad
    kind / vec / iters (1 .. 2^20), a NULL pointer, a buffer of fewer than 32 vectors (kinds 0,
-   1, 3) or one that does not hold edge^3 vectors (kinds 2, 4; 2 <= edge <= 2048). */
+   1, 3) or one that does not hold edge^3 vectors (kinds 2, 4, 5, 6; 2 <= edge <= 2048). */
 rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int edge, int iters, float* ms,
                         double* ops);
 

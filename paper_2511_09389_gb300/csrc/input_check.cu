@@ -47,6 +47,42 @@ __global__ void k_check_inputs(const float* __restrict__ j, const float* __restr
     }
 }
 
+// Content hash of a march's inputs, for checkpoint reuse: *out = sum over elements of a mixed
+// 64-bit word (the SplitMix64 finaliser of Steele, Lea and Flood, 2014) of each (j, kappa) bit
+// pair and each source coordinate, salted with its index. The sum is order-independent, so any
+// launch shape gives the same value; changing any element changes it except with probability
+// about 2^-64.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_input_hash(const float* __restrict__ j, const float* __restrict__ kappa, long long n,
+                             const float* __restrict__ src, int nsrc, unsigned long long* __restrict__ out) {
+    constexpr unsigned long long kGolden = 0x9e3779b97f4a7c15ULL;
+    unsigned long long h = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long w = ((unsigned long long)__float_as_uint(__ldg(kappa + i)) << 32) |
+                                     __float_as_uint(__ldg(j + i));
+        h += mix64(w + (unsigned long long)(i + 1) * kGolden);
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3LL * nsrc;
+         i += (long long)gridDim.x * blockDim.x)
+        h += mix64(((unsigned long long)__float_as_uint(__ldg(src + i)) | (1ULL << 40)) +
+                   (unsigned long long)(n + i + 1) * kGolden);
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, h);
+}
+
+cudaError_t launch_input_hash(const float* j, const float* kappa, long long n, const float* src, int nsrc,
+                              unsigned long long* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_input_hash<<<check_grid(n), 256, 0, st>>>(j, kappa, n, src, nsrc, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n, const float* src, int nsrc,
                                 const float* extra, int* flags, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), st);

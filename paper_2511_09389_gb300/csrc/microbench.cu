@@ -103,6 +103,26 @@ __global__ void k_gather_stencil(float* buf, int edge, int iters) {
     if (acc == -1.0f) buf[0] = acc;
 }
 
+// kinds 5 / 6: the 8-corner stencil of kind 2 with 64-bit reductions, red.global.add.u64 (the
+// fixed-point deposit) or red.global.add.f64, into an edge^3 grid of 8-byte cells
+template <bool F64>
+__global__ void k_red_stencil64(unsigned long long* buf, int edge, int iters) {
+    uint32_t s = 0x9e3779b9u ^ (blockIdx.x * blockDim.x + threadIdx.x);
+    const uint32_t m = (uint32_t)(edge - 1);
+    for (int i = 0; i < iters; ++i) {
+        const uint32_t x = below(lcg(s), m), y = below(lcg(s), m), z = below(lcg(s), m);
+        const size_t c = ((size_t)x * edge + y) * edge + z;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const size_t cell = c + (size_t)((k >> 2) & 1) * edge * edge + (size_t)((k >> 1) & 1) * edge + (k & 1);
+            if (F64)
+                asm volatile("red.global.add.f64 [%0], %1;" ::"l"(buf + cell), "d"(0.125) : "memory");
+            else
+                asm volatile("red.global.add.u64 [%0], %1;" ::"l"(buf + cell), "l"(1ull) : "memory");
+        }
+    }
+}
+
 template <int V>
 cudaError_t launch_kind(int kind, float* buf, uint32_t nvec, int edge, int iters, int grid, int block,
                         cudaStream_t st) {
@@ -122,6 +142,11 @@ cudaError_t launch_kind(int kind, float* buf, uint32_t nvec, int edge, int iters
 cudaError_t launch_microbench(int kind, int vec, float* buf, long long nvec, int edge, int iters, int grid,
                               int block, cudaStream_t st) {
     if (nvec < 32 || nvec > 0xffffffffLL) return cudaErrorInvalidValue;
+    if (kind == 5 || kind == 6) {
+        if (kind == 5) k_red_stencil64<false><<<grid, block, 0, st>>>((unsigned long long*)buf, edge, iters);
+        else k_red_stencil64<true><<<grid, block, 0, st>>>((unsigned long long*)buf, edge, iters);
+        return cudaGetLastError();
+    }
     return vec == 4 ? launch_kind<4>(kind, buf, (uint32_t)nvec, edge, iters, grid, block, st)
                     : launch_kind<1>(kind, buf, (uint32_t)nvec, edge, iters, grid, block, st);
 }
@@ -130,10 +155,12 @@ cudaError_t launch_microbench(int kind, int vec, float* buf, long long nvec, int
 
 extern "C" rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int edge, int iters, float* ms,
                                    double* ops) {
-    if (kind < 0 || kind > 4 || (vec != 1 && vec != 4) || !buf || !ms || !ops || iters < 1 || iters > (1 << 20))
-        return rt::set_error(RT_ERR_INVALID_ARG, "rt_microbench: need kind 0-4, vec 1 or 4, 1 <= iters <= 2^20");
-    const long long nvec = buf_bytes / (4LL * vec);
-    const bool stencil = kind == 2 || kind == 4;
+    if (kind < 0 || kind > 6 || (vec != 1 && vec != 4) || (kind >= 5 && vec != 1) || !buf || !ms || !ops ||
+        iters < 1 || iters > (1 << 20))
+        return rt::set_error(RT_ERR_INVALID_ARG,
+                             "rt_microbench: need kind 0-6, vec 1 or 4 (1 for kinds 5, 6), 1 <= iters <= 2^20");
+    const long long nvec = buf_bytes / (kind >= 5 ? 8LL : 4LL * vec);
+    const bool stencil = kind == 2 || kind == 4 || kind >= 5;
     if (stencil) {
         if (edge < 2 || edge > 2048 || (long long)edge * edge * edge > nvec)
             return rt::set_error(RT_ERR_INVALID_ARG, "rt_microbench: edge^3 vectors must fit in the buffer");

@@ -134,7 +134,7 @@ struct rt_grid {
     std::vector<DirTable> dirs;
     // scratch slots
     enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, CHK,
-                AJ0, AK0, AOUT0, ASRC0, AJ1, AK1, AOUT1, ASRC1, NSLOT };
+                AJ0, AK0, AOUT0, ASRC0, AJ1, AK1, AOUT1, ASRC1, HASH, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -594,6 +594,13 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
             return st;
         m.ckpt = (float*)ck;
         m.ck_stride = sz.stride;
+        // content hash of the recorded inputs: the reverse march reuses the checkpoints only if
+        // its own inputs hash alike (buffers rewritten in place in between do not)
+        void* h;
+        if ((st = g->ensure(rt_grid::HASH, 2 * sizeof(unsigned long long), &h)) != RT_OK) return st;
+        RT_CUDA(rt::launch_input_hash(a.j, a.kappa, (long long)a.n_freq * ncell, a.src, a.nsrc,
+                                      (unsigned long long*)h, a.st),
+                "input hash launch");
         g->rec = rt_grid::Recording{true, a.j, a.kappa, a.src, a.nsrc, a.num_rays, ns, a.n_freq, sz.stride,
                                     plan.W, g->opt.kappa_mode, a.ds};
     }
@@ -638,6 +645,11 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
     if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2)
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1 or 2");
     if (o.plan_tile < 0 || o.plan_tile > 2) return fail(RT_ERR_INVALID_ARG, "plan_tile must be 0, 1 or 2");
+    // the fixed-point march runs one lane per ray with corner slots and no tiles: a pinned plan
+    // asking for anything else would be accepted here and then silently not used
+    if (o.deterministic && (o.plan_lanes == 2 || o.plan_tile == 2 || o.plan_prefetch > 1))
+        return fail(RT_ERR_INVALID_ARG, "deterministic mode marches with plan_lanes 1, plan_tile 1 (off) and "
+                                        "plan_prefetch 1 (corner slots) only");
     rt_grid* g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ERR_OOM, "host allocation failed");
     g->n0 = n0; g->n1 = n1; g->n2 = n2; g->max_freq = max_freq;
@@ -989,6 +1001,16 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
                   r.nsrc == num_sources && r.rays == num_rays && r.ns == ns && r.n_freq == n_freq &&
                   r.stride == b.stride && r.W == W && r.kappa_mode == g->opt.kappa_mode && r.ds == step_size;
     if (!b.have_ckpt) g->rec.valid = false;   // this reverse march rewrites the checkpoint slot
+    if (b.have_ckpt) {
+        // the kernel reuses the recording only if the inputs still hash as they did at the forward
+        void* h;
+        if ((st = g->ensure(rt_grid::HASH, 2 * sizeof(unsigned long long), &h)) != RT_OK) return st;
+        b.hash_rec = (const unsigned long long*)h;
+        b.hash_now = (const unsigned long long*)h + 1;
+        RT_CUDA(rt::launch_input_hash(j_map, kappa_map, (long long)n_freq * ncell, source_pos, num_sources,
+                                      (unsigned long long*)h + 1, a.st),
+                "input hash launch");
+    }
     void* ck;
     if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(b, W), &ck)) != RT_OK) return st;
     b.ckpt = (float*)ck;

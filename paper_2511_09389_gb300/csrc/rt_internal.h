@@ -85,6 +85,10 @@ cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float
 // kappa / non-finite or too large source coordinates / non-finite extra (a loss gradient, may be NULL).
 cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n, const float* src, int nsrc,
                                 const float* extra, int* flags, cudaStream_t st);
+// *out = a 64-bit content hash of j and kappa (n floats each) and the source coordinates
+// (order-independent; equal inputs give equal hashes); checkpoint reuse compares two of them.
+cudaError_t launch_input_hash(const float* j, const float* kappa, long long n, const float* src, int nsrc,
+                              unsigned long long* out, cudaStream_t st);
 cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
                                   float* out, int accumulate, cudaStream_t st);
 
@@ -101,7 +105,10 @@ struct BackArgs {
     float* dj;              // accumulator packed like j, or NULL (not wanted)
     float* dk;              // accumulator packed like j, or NULL (not wanted)
     float* dsrc;            // dL/d(source positions) [nsrc][3], accumulated, or NULL (not wanted)
-    int have_ckpt;          // 1: ckpt already holds this problem's checkpoints (skip the forward sweep)
+    int have_ckpt;          // 1: ckpt may hold this problem's checkpoints (skip the forward sweep when
+                            // the hashes below agree, or when they are NULL)
+    const unsigned long long* hash_rec;   // input hash taken when the checkpoints were recorded
+    const unsigned long long* hash_now;   // input hash of this call
     float* ckpt;            // checkpoint scratch
     const float4* dirs;
     const float* src;

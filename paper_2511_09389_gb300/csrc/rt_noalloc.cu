@@ -12,6 +12,7 @@
 // until the process exits. All calls share it and it keeps the last call's contents; the
 // accumulator part is cleared on the stream at every call. Calls whose work overlaps on the
 // GPU (different streams, or different host threads) race on the array.
+#include <cuda.h>   // driver types only: the two driver calls below are looked up at run time
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,9 +37,36 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct DeviceState {
-    void* base = nullptr;   // device address of g_scratch on this device
-    int dirs_n = 0;         // lattice size whose sorted table is in the scratch (0: none)
+    void* base = nullptr;        // device address of g_scratch on this device
+    unsigned long long ctx = 0;  // unique id of the context that address belongs to (0: unknown)
+    int dirs_n = 0;              // lattice size whose sorted table is in the scratch (0: none)
 };
+
+// Unique id of the calling thread's current context, or 0 if the driver cannot say. The driver
+// entry points come through the runtime (no link against the driver library).
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 std::mutex g_mutex;
 DeviceState g_dev[kMaxDevices];
@@ -60,13 +88,6 @@ rt_status cuda_err(cudaError_t e, const char* what) {
     return err(RT_ERR_CUDA, "rt_advance_noalloc: %s: %s", what, cudaGetErrorString(e));
 }
 
-int substeps(float ds, float c, float dt) {
-    const double q = (double)c * (double)dt / (double)ds;
-    const double n = std::ceil(q - 1e-9 * q);
-    if (!(n <= 2147483647.0)) return -1;
-    return n < 0.0 ? 0 : (int)n;
-}
-
 }  // namespace
 
 extern "C" rt_status rt_advance_noalloc(const float* j_map, const float* kappa_map, const float* source_pos,
@@ -85,7 +106,7 @@ extern "C" rt_status rt_advance_noalloc(const float* j_map, const float* kappa_m
         !std::isfinite(radiation_velocity) || !(time_step >= 0.0f) || !std::isfinite(time_step))
         return err(RT_ERR_INVALID_ARG, "rt_advance_noalloc: need step_size > 0, radiation_velocity > 0, "
                                        "time_step >= 0, all finite");
-    const int ns = substeps(step_size, radiation_velocity, time_step);
+    const int ns = rt::substeps(step_size, radiation_velocity, time_step, 0);   // the rule of rt_advance
     if (ns < 0 || (double)ns * step_size > 1.6e7)
         return err(RT_ERR_INVALID_ARG, "rt_advance_noalloc: ray length c*dt too large");
     const long long ncell = (long long)n0 * n1 * n2;
@@ -109,12 +130,21 @@ extern "C" rt_status rt_advance_noalloc(const float* j_map, const float* kappa_m
     if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return err(RT_ERR_UNSUPPORTED, "rt_advance_noalloc: device index too large");
     DeviceState& ds = g_dev[dev];
-    // ---- set-up, once per device: device address of the static scratch ----
-    if (!ds.base) {
+    // ---- device address of the static scratch, looked up on every call ----
+    // Cheap once the module is loaded. When the device's context has been replaced since the
+    // last call (cudaDeviceReset, a new primary context), the module was loaded again: the old
+    // address may point at freed memory and the direction table stored there is gone, whether or
+    // not the new array landed at the same address. Either change starts the state afresh.
+    {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);   // also makes sure the context exists
         if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress(scratch)");
-        ds.base = p;
+        const unsigned long long ctx = current_context_id();
+        if (p != ds.base || ctx != ds.ctx || ctx == 0) {
+            ds.base = p;
+            ds.ctx = ctx;
+            ds.dirs_n = 0;   // a new array: its direction table must be rebuilt
+        }
     }
     unsigned char* base = (unsigned char*)ds.base;
     float4* d_dirs = (float4*)base;

@@ -4,7 +4,8 @@ L2-resident array, with random, warp-coherent and 8-corner-stencil addresses.
 
 The march's deposit is a `red.global.add.v4.f32` into the 8 corners of a cell of a cell-major
 accumulator and its gather is 8 + 1 16-byte loads, so the stencil kinds with 16-byte vectors
-are the denominators of its roofline fractions. The paper has no counterpart.
+are the denominators of its roofline fractions; the 8-byte stencil reductions (u64, f64) are
+those of the fixed-point deposits. The paper has no counterpart.
 
     python -m paper_2511_09389_gb300.peaks [--edge 128] [--out peaks.json]
 """
@@ -46,6 +47,16 @@ def measure(edge: int = 128, vecs=(4, 1), reps: int = 3, device=None) -> dict:
                 rate = ops.value / (best * 1e-3)
                 out[f"{name}_v{vec}"] = {"ops_per_s": rate, "bytes_per_s": rate * 4 * vec, "ms": best,
                                          "ops": ops.value}
+        # the stencil with 8-byte reductions: the fixed-point deposit (u64) and FP64
+        for name, kind in (("red_stencil_u64", 5), ("red_stencil_f64", 6)):
+            best = None
+            for r in range(reps + 1):
+                check(lib.rt_microbench(kind, 1, buf.data_ptr(), buf.numel() * 4, edge, 64, ctypes.byref(ms),
+                                        ctypes.byref(ops)))
+                if r > 0 and (best is None or ms.value < best):
+                    best = ms.value
+            rate = ops.value / (best * 1e-3)
+            out[name] = {"ops_per_s": rate, "bytes_per_s": rate * 8, "ms": best, "ops": ops.value}
     return out
 
 

@@ -81,3 +81,20 @@ def test_bad_options_rejected_at_creation(lib, field, value, word):
     assert lib.rt_create_grid(ctypes.byref(h), 8, 8, 8, 1, ctypes.byref(opt)) == 1
     assert word in lib.rt_last_error()
     assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("plan_lanes", 2), ("plan_tile", 2), ("plan_prefetch", 2),
+                                         ("plan_prefetch", 4)])
+def test_deterministic_rejects_plans_it_cannot_run(lib, field, value):
+    """The fixed-point march runs one lane per ray with corner slots and no tiles: a pinned plan
+    asking for two lanes, tiles or another gathers mode is refused at creation, naming the mode,
+    instead of being accepted and then ignored."""
+    from paper_2511_09389_gb300 import _native
+    opt = _native.rt_options()
+    lib.rt_default_options(ctypes.byref(opt))
+    opt.deterministic = 1
+    setattr(opt, field, value)
+    h = ctypes.c_void_p()
+    assert lib.rt_create_grid(ctypes.byref(h), 8, 8, 8, 1, ctypes.byref(opt)) == 1
+    assert b"deterministic" in lib.rt_last_error()
+    assert not h.value

@@ -266,3 +266,65 @@ def test_recorded_checkpoints_give_the_same_gradients(torch_cuda, n_freq, stride
     # then the original call again: its recording was replaced by that sweep, still correct
     gj3, _ = g.backward(Gt, j, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
     assert rel(gj3.cpu().numpy(), rj) <= GRAD_REL
+
+
+@pytest.mark.parametrize("n_freq,which", [(1, "j"), (1, "kappa"), (4, "j"), (3, "sources")])
+def test_recorded_checkpoints_after_inputs_rewritten_in_place(torch_cuda, n_freq, which):
+    """A C caller that rewrites j_map, kappa_map or source_pos IN PLACE between a recording
+    rt_advance and rt_backward (same pointers, same scalars) gets the gradients of the new
+    contents: the reverse march compares a content hash of the inputs taken at the forward with
+    one taken at the backward, on the device, and repeats the forward sweep when they differ. The
+    result is bit-equal to a handle that never recorded; with the inputs untouched the recording is
+    used and gives the same gradients within the bar."""
+    import ctypes
+    torch = torch_cuda
+    from paper_2511_09389_gb300 import _native
+    from paper_2511_09389_gb300.api import Grid
+    lib = _native.load()
+    p = inputs.random_small(340 + n_freq, shape=(13, 12, 15), n_freq=n_freq, n_src=3, num_rays=90,
+                            step_size=0.6, horizon=14.0)
+    G = np.random.default_rng(9).standard_normal(p.j.shape)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    j, k, s, Gt = t(p.j), t(p.kappa), t(p.sources), t(G)
+    out = torch.empty_like(j)
+    gj, gk, gsrc = torch.empty_like(j), torch.empty_like(j), torch.empty_like(s)
+    g = Grid(p.shape, 8, record_checkpoints=True)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def advance():
+        _native.check(lib.rt_advance(g._h, j.data_ptr(), k.data_ptr(), s.data_ptr(), s.shape[0], p.num_rays,
+                                     ctypes.c_float(p.step_size), ctypes.c_float(1.0), ctypes.c_float(p.time_step),
+                                     n_freq, out.data_ptr(), 0, stream))
+
+    def backward(h):
+        _native.check(lib.rt_backward_sources(h, Gt.data_ptr(), j.data_ptr(), k.data_ptr(), s.data_ptr(), s.shape[0],
+                                              p.num_rays, ctypes.c_float(p.step_size), ctypes.c_float(1.0),
+                                              ctypes.c_float(p.time_step), n_freq, gj.data_ptr(), gk.data_ptr(),
+                                              gsrc.data_ptr(), stream))
+        torch.cuda.synchronize()
+        return gj.cpu().numpy().copy(), gk.cpu().numpy().copy(), gsrc.cpu().numpy().copy()
+
+    advance()
+    kept = backward(g._h)                       # untouched inputs: the recording is reused
+    rj, rk = oracle_backward(p, G)
+    assert rel(kept[0], rj) <= GRAD_REL and rel(kept[1], rk) <= GRAD_REL
+
+    advance()                                   # record again, then rewrite in place
+    if which == "j":
+        j.mul_(1.7).add_(0.01)
+    elif which == "kappa":
+        k.mul_(1.3)
+    else:
+        s[0, 1] += 0.37
+    torch.cuda.synchronize()
+    new = backward(g._h)
+    fresh = Grid(p.shape, 8)                    # never recorded: its own forward sweep
+    ref = backward(fresh._h)
+    for a, b in zip(new, ref):
+        assert np.array_equal(a, b)
+    q = inputs.Problem(p.name, j.cpu().numpy(), k.cpu().numpy(), s.cpu().numpy(), p.num_rays, p.step_size,
+                       p.radiation_velocity, p.time_step)
+    nj, nk = oracle_backward(q, G)
+    assert rel(new[0], nj) <= GRAD_REL and rel(new[1], nk) <= GRAD_REL
+    g.close()
+    fresh.close()
