@@ -32,7 +32,6 @@ METRIC = "ray-substep updates/s (forward march)"
 UNIT = "updates/s"
 WORKLOAD = ("turbulent lognormal kappa 128^3 (sigma_g 1, mean 0.05), 16 sources with Gaussian j blobs, "
             "N_Omega 3072, ds 0.5, c*dt 128 (N_s 256), 4 frequency bins, FP32")
-ALGO_BYTES_PER_UPDATE = 68     # 9 gathered floats (8 j corners + 1 kappa) + 8 deposited floats
 FLUSH_BYTES = 256 << 20
 
 
@@ -74,33 +73,48 @@ def profiled_counter(src_hash, key="dram_bytes_per_launch"):
     return float(m_tr.group(1))
 
 
-def l2_roofline(plan, U, kms, src_hash):
-    """The march kernel against L2 peaks measured on this GPU by the library's microbenchmarks
-    (stencil kinds: 8 corners of a random cell of a 128^3 cell-major grid, the march's access
-    pattern). Algorithmic operations per (ray, source, bin group) substep: 8 deposits and 9
-    gathers of W-float vectors; merging in registers issues fewer deposits, so the algorithmic
-    fraction can exceed 1. `issued` uses the L2 red sectors ncu counted per launch."""
+def march_roofline(plan, U, kms, src_hash, hbm_peak, hbm_kind):
+    """The march kernel against the bound that limits it: L2 reductions (`red`), with L2 gathers
+    and HBM beside it. Peaks of the reductions and gathers are measured here by the library's
+    microbenchmark with the march's access pattern (the 8 corners of a random cell of a 128^3
+    cell-major grid of W-float vectors); the HBM peak is the driver's copy bandwidth. Issued
+    reductions and gathers per launch are the L2 sectors ncu counted for this kernel source (the
+    committed summary in profiles/, hash-checked), divided by this run's CUDA-event kernel time.
+    Algorithmic counts (8 deposits and 9 gathers of a W-vector per (ray, source, bin group)
+    substep) are reported beside them: merging deposits in registers issues fewer reductions than
+    the algorithm names, so the algorithmic fraction can exceed 1."""
     from paper_2511_09389_gb300 import peaks
     pk = peaks.measure(edge=128, vecs=(4, 1))
     W = int(plan["width"])
     vec = 4 if W == 4 else 1
     t = kms * 1e-3
     lane_steps = U / W
-    reds, gathers = 8 * lane_steps, 9 * lane_steps
     red_peak = pk[f"red_stencil_v{vec}"]["ops_per_s"]
     gather_peak = pk[f"gather_stencil_v{vec}"]["ops_per_s"]
-    issued = profiled_counter(src_hash, "l2_red_sectors_per_launch")
-    return {
-        "bound": "l2_red", "unit": "ops/s", "vector_bytes": 4 * vec,
-        "red": {"algorithmic": reds / t, "peak": red_peak, "frac": reds / t / red_peak,
-                "issued": None if issued is None else issued / t,
-                "issued_frac": None if issued is None else issued / t / red_peak},
-        "gather": {"algorithmic": gathers / t, "peak": gather_peak, "frac": gathers / t / gather_peak},
+    reds = profiled_counter(src_hash, "l2_red_sectors_per_launch")
+    reads = profiled_counter(src_hash, "l2_read_sectors_per_launch")
+    dram = profiled_counter(src_hash)
+    fresh = reds is not None
+    red_rate = (reds if fresh else 8 * lane_steps) / t
+    line = {
+        "bound": "l2_red", "achieved": red_rate / 1e9, "peak": red_peak / 1e9, "unit": "Gop/s",
+        "frac": red_rate / red_peak, "traffic": dram,
+        "peak_kind": f"measured here (rt_microbench: red.global.add.v{vec}.f32 into the 8 corners of random cells "
+                     "of a 128^3 cell-major grid)",
+        "basis": (f"issued L2 red sectors per launch ({int(reds)}, ncu, profiles/march_fwd_turbulent128.md) / "
+                  "march-kernel CUDA-event time" if fresh else
+                  "ALGORITHMIC deposits (the committed ncu count is stale for this kernel source) / kernel time"),
+        "gather": {"issued_per_s": None if reads is None else reads / t,
+                   "frac": None if reads is None else reads / t / gather_peak, "peak_per_s": gather_peak},
+        "hbm": {"achieved_gbs": None if dram is None else dram / t / 1e9, "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
+                "frac": None if dram is None else dram / t / 1e9 / hbm_peak},
+        "algorithmic": {"deposits_per_s": 8 * lane_steps / t, "deposit_frac": 8 * lane_steps / t / red_peak,
+                        "gathers_per_s": 9 * lane_steps / t, "gather_frac": 9 * lane_steps / t / gather_peak,
+                        "basis": f"8 deposits and 9 gathers of {W}-float vectors per (ray, source, bin group) substep "
+                                 f"x {int(lane_steps)} substeps per launch"},
         "peaks": {k: v["ops_per_s"] for k, v in pk.items() if isinstance(v, dict)},
-        "peak_kind": "measured here (rt_microbench)",
-        "basis": f"8 deposits and 9 gathers of {W}-float vectors per (ray, source, bin group) substep x "
-                 f"{int(lane_steps)} substeps per launch / march-kernel CUDA-event time",
     }
+    return line
 
 
 class ClockSampler:
@@ -271,14 +285,25 @@ def paper_workload(args, dev, flush, stream):
             steps.append(e0.elapsed_time(e1))
             kern.append(g.kernel_ms())
     plan = g.last_plan()
+    acc = g.last_accumulation()
     g.close()
     t = st.mean(steps)
-    return {"value": U / (t * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": t,
-            "kernel_ms": st.mean(kern), "launch_plan": plan,
-            "workload": f"128^3 lognormal kappa, {len(p.sources)} sources at the 0.1 % highest-kappa cells, "
-                        f"N_Omega {p.num_rays}, ds {p.step_size}, N_s {ns} (c dt 128 assumed), 1 bin",
-            "paper": {"seconds": 4.49, "hardware": "1x H200 (JAX)", "speedup_context": 4.49 / (t * 1e-3),
-                      "note": "context only: another machine; the paper does not state N_s or bins"}}
+    res = {"value": U / (t * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": t,
+           "kernel_ms": st.mean(kern), "launch_plan": plan, "accumulation": acc,
+           "workload": f"128^3 lognormal kappa, {len(p.sources)} sources at the 0.1 % highest-kappa cells, "
+                       f"N_Omega {p.num_rays}, ds {p.step_size}, N_s {ns} (c dt 128 assumed), 1 bin",
+           "paper": {"seconds": 4.49, "hardware": "1x H200 (JAX)", "speedup_context": 4.49 / (t * 1e-3),
+                     "note": "context only: another machine; the paper does not state N_s or bins"}}
+    if not args.no_cpu_baseline:
+        # parity of the timed field against the FP64 oracle over all sources (all host cores)
+        import numpy as np
+        import oracle
+        F = out.double().cpu().numpy()
+        R = oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, threads=host_cores(), ray_block=256)
+        res["parity_vs_oracle"] = {"rel_l2": float(np.linalg.norm(F - R) / np.linalg.norm(R)),
+                                   "max_abs_rel": float(np.abs(F - R).max() / np.abs(R).max()),
+                                   "bar": {"rel_l2": 1e-5, "max_abs_rel": 1e-4}}
+    return res
 
 
 def _batch_vs_one_by_one(probs, args, dev, stream):
@@ -497,9 +522,7 @@ def native_arm(args):
         ms, kms, ems, pipe_ms = t.tolist()
 
     peak, peak_kind, _ = load_peaks()
-    achieved = ALGO_BYTES_PER_UPDATE * U / (kms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
-    traffic = profiled_counter(src_hash)
     h2d = p.j.nbytes + p.kappa.nbytes + p.sources.nbytes
     d2h = p.j.nbytes
 
@@ -510,12 +533,10 @@ def native_arm(args):
         "config": {"workload": WORKLOAD, "updates_per_step": U, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "kernel_ms": kms, "wall_s": wall, "launch_plan": g.last_plan(),
+                   "accumulation": g.last_accumulation(),
                    "median_ms_per_step": statistics.median(step_ms), "median_kernel_ms": statistics.median(kern_ms),
                    "timing": "value and ms_per_step use the mean over the K timed steps; medians beside them"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "basis": f"{ALGO_BYTES_PER_UPDATE} algorithmic bytes per update x {U} updates per launch / "
-                              "march-kernel CUDA-event time"},
+        "roofline": march_roofline(g.last_plan(), U, kms, src_hash, peak, peak_kind),
         "e2e": {"value": world * U / (pipe_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": pipe_ms,
                 "api": "rt_advance_host_async x K steps, one event pair around all K (fill and drain included)",
@@ -528,8 +549,6 @@ def native_arm(args):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
     }
-
-    line["l2_roofline"] = l2_roofline(g.last_plan(), U, kms, src_hash)
 
     # the same step with the deterministic (64-bit fixed-point) accumulation
     gd = Grid(p.shape, 8, deterministic=True)

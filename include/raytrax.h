@@ -102,6 +102,25 @@ typedef struct {
                            at the backward, is unchanged (decided on the device, no
                            synchronisation): buffers rewritten in place in between get the
                            gradients of their new contents. 0: off. */
+    int accumulation;   /* how deposits are summed into the field (deterministic = 1 implies 3):
+                           0: automatic (default): 64-bit fixed point for groups of one bin,
+                              FP32 for wider groups. A one-bin FP32 reduction and an 8-byte one
+                              are one L2 operation each (the same march time was measured on
+                              GB300), a W-bin group's FP32 reduction is one vector operation
+                              against W 8-byte ones. One-bin groups sum in FP64 instead when the
+                              fixed-point unit would be coarse (num_sources * N_s (N_s + 1) / 2
+                              above 2^32) and in rt_advance_continue.
+                           1: FP32 reductions (W-wide vectors). A cell that takes very many
+                              small deposits on top of a large sum -- next to many clustered
+                              sources, on the clamped box corners -- loses them to rounding:
+                              relative L2 error ~1e-4 on 2,097 clustered sources.
+                           2: FP64 reductions (one per bin), converted to FP32 once.
+                           3: 64-bit fixed point as in deterministic mode (unit: the bound given
+                              there over 2^62; needs kappa >= 0), any launch plan that has it.
+                           Sums in 8-byte words take no source tiles (a plan that pins them keeps
+                           FP32 in the automatic mode). Fixed-point sums are independent of the
+                           deposit order, FP64 ones up to FP64 rounding. rt_advance_noalloc and
+                           batches sum in FP32. */
 } rt_options;
 
 /* Fill *opt with the defaults (all zero: FP32 atomics, floor kappa cell, no cap,
@@ -432,6 +451,10 @@ rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int e
    times every candidate plan on its own inputs before running; it synchronises the stream. */
 rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray, int* tile,
                        float* tuned_ms);
+
+/* Accumulation of the last forward call on this handle: *mode = 1 FP32 reductions, 2 FP64
+   reductions, 3 64-bit fixed point (deterministic mode). */
+rt_status rt_last_accumulation(rt_grid* grid, int* mode);
 
 /* Text of the last autotuning pass on this handle: one line per candidate plan with its best
    march time ("W=4 block=64 prefetch=0 lanes=2 0.5123 ms"), copied NUL-terminated into the HOST

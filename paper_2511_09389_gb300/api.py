@@ -53,6 +53,9 @@ def direction_table(num_rays: int) -> np.ndarray:
 class Grid:
     """A library handle for one grid shape (owns its scratch on one device).
 
+    accumulation: "auto" (64-bit fixed point for one-bin groups, FP32 for wider ones), "fp32",
+    "fp64" or "fixed"; deterministic=True also sums in fixed point, with one launch plan.
+
     plan=(bins_per_group, block, gathers[, lanes_per_ray[, tile]]) pins the forward launch plan,
     gathers 0 = corner slots (a shared face keeps its gathers and sums), 1 = one step ahead,
     2 = both, 3 = the whole corner set reused while unchanged; tile 0 / 1 = source deposit tiles
@@ -60,9 +63,12 @@ class Grid:
     (the library's default when not given; ignored when autotune=True, which times the
     candidates on the first call of each shape class)."""
 
+    ACCUMULATION = {"auto": 0, "fp32": 1, "fp64": 2, "fixed": 3}
+
     def __init__(self, shape, max_freq: int = 8, *, deterministic: bool = False, kappa_mode: int = 0,
                  ns_cap: int = 0, autotune: bool = False, ckpt_stride: int = 0, profile: bool = False,
-                 plan=None, check_inputs: bool = False, record_checkpoints: bool = False, device=None):
+                 plan=None, check_inputs: bool = False, record_checkpoints: bool = False,
+                 accumulation: str = "auto", device=None):
         self._lib = _native.load()
         self.shape = tuple(int(s) for s in shape)
         if len(self.shape) != 3:
@@ -73,9 +79,11 @@ class Grid:
         pw, pb, pp, pl, pt = (0, 0, 0, 0, 0) if plan is None else (
             int(plan[0]), int(plan[1]), int(plan[2]) + 1, int(plan[3]) if len(plan) > 3 else 1,
             int(plan[4]) + 1 if len(plan) > 4 else 0)
+        if accumulation not in self.ACCUMULATION:
+            raise ValueError(f"accumulation must be one of {sorted(self.ACCUMULATION)}")
         opt = _native.rt_options(int(bool(deterministic)), int(kappa_mode), int(ns_cap), int(bool(autotune)),
                                  int(ckpt_stride), int(bool(profile)), pw, pb, pp, pl, pt, int(bool(check_inputs)),
-                                 int(bool(record_checkpoints)))
+                                 int(bool(record_checkpoints)), self.ACCUMULATION[accumulation])
         self.options = opt
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -267,6 +275,12 @@ class Grid:
                                      ctypes.byref(tl), ctypes.byref(t)))
         return {"width": w.value, "block": b.value, "prefetch": p.value, "lanes_per_ray": n.value, "tile": tl.value,
                 "tuned_ms": t.value}
+
+    def last_accumulation(self) -> str:
+        """How the last forward call summed its deposits: "fp32", "fp64" or "fixed" (deterministic)."""
+        m = ctypes.c_int()
+        check(self._lib.rt_last_accumulation(self._h, ctypes.byref(m)))
+        return {1: "fp32", 2: "fp64", 3: "fixed"}[m.value]
 
     def tuning_report(self) -> str:
         """Candidates and times of the last autotuning pass ("" if none)."""

@@ -167,6 +167,29 @@ __device__ __forceinline__ void red_vec_if<4>(bool p, float* __restrict__ base, 
                  ::"r"((int)p), "l"(base + 4 * (size_t)cell), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
 }
 
+// FP64 reductions for the wide accumulation mode. The deposit is an FP32 number; it is widened
+// to FP64 exactly by integer operations on the IEEE-754 encodings (binary32: sign, 8 exponent
+// bits with bias 127, 23 fraction bits; binary64: sign, 11 exponent bits with bias 1023, 52
+// fraction bits): a normal number keeps its sign and fraction and has its exponent rebiased by
+// 1023 - 127 = 896; zeros and subnormals give a signed zero (the FP32 reductions flush
+// subnormals too); infinities and NaNs stay infinities and NaNs. No FP64 arithmetic runs on the
+// SM: the L2 performs the addition.
+__device__ __forceinline__ double widen_f32(float v) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long frac = e == 0u ? 0ull : (unsigned long long)(b & 0x7FFFFFu) << 29;
+    const unsigned long long e64 = e == 0u ? 0ull : (e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u));
+    return __longlong_as_double((long long)(sign | (e64 << 52) | frac));
+}
+__device__ __forceinline__ void red_add_f64(double* p, float v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(widen_f32(v)));
+}
+__device__ __forceinline__ void red_add_f64_if(bool q, double* p, float v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f64 [%1], %2;\n\t}"
+                 ::"r"((int)q), "l"(p), "d"(widen_f32(v)));
+}
+
 // 64-bit integer reduction for the deterministic (fixed-point) accumulation mode.
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long a) {
     asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(a));

@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
 
 // Lanes per ray = 2: adjacent lanes (sub = threadIdx.x & 1) share one (ray, source, bin group),
 // each with half of its corner slots (march_lane_pair). REC: also the reverse march's checkpoints.
-template <int W, bool REC = false>
+// DET: the accumulation (flush() in march_lane.cuh).
+template <int W, bool REC = false, int DET = 0>
 __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     const int rays_per_block = blockDim.x / 2;
     const int rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
@@ -140,79 +141,108 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     L.ds = a.ds;
     L.scale = a.dep_scale;
     L.kappa_mode = a.kappa_mode;
+    L.og64 = a.acc64 ? a.acc64 + (size_t)g * ncell * W : nullptr;
+    L.ncell = ncell;
+    L.nbins = min(W, a.n_freq - g * W);
+    L.fix = a.fix;
     if (REC) {
         L.ck_lanes = (long long)a.ray_count * a.nsrc * a.groups;
         L.ck = a.ckpt + ((long long)g * a.nsrc + s) * a.ray_count + r;
         L.ck_stride = a.ck_stride;
     }
-    march_lane_pair<W, REC>(L, sub, pmask);
+    march_lane_pair<W, REC, DET>(L, sub, pmask);
+}
+
+// ---- kernel table ------------------------------------------------------------------------
+// The compiled (W, gathers mode, accumulation, tiles, checkpoints, lanes per ray) combinations:
+//   FP32: every W and gathers mode with and without tiles; recording with gathers mode 0 (and
+//         1 or 3 for one bin); two lanes per ray for every W.
+//   fixed point: corner slots for every W; for one bin also recording and two lanes per ray.
+//   FP64: corner slots for every W, with and without recording; two lanes per ray for one bin.
+using MarchKernel = void (*)(MarchArgs);
+
+template <int W>
+MarchKernel pick_one_lane(int pf, int acc, bool tile, bool rec) {
+    if (acc == 0 && !rec) {
+        switch (pf * 2 + (tile ? 1 : 0)) {
+            case 0: return k_march_fwd<W, 0, 0, false>;
+            case 1: return k_march_fwd<W, 0, 0, true>;
+            case 2: return k_march_fwd<W, 1, 0, false>;
+            case 3: return k_march_fwd<W, 1, 0, true>;
+            case 4: return k_march_fwd<W, 2, 0, false>;
+            case 5: return k_march_fwd<W, 2, 0, true>;
+            case 6: return k_march_fwd<W, 3, 0, false>;
+            case 7: return k_march_fwd<W, 3, 0, true>;
+        }
+        return nullptr;
+    }
+    if (acc == 0) {   // recording
+        if (pf == 0) return tile ? k_march_fwd<W, 0, 0, true, true> : k_march_fwd<W, 0, 0, false, true>;
+        if (W == 1 && pf == 1) return tile ? k_march_fwd<1, 1, 0, true, true> : k_march_fwd<1, 1, 0, false, true>;
+        if (W == 1 && pf == 3) return tile ? k_march_fwd<1, 3, 0, true, true> : k_march_fwd<1, 3, 0, false, true>;
+        return nullptr;
+    }
+    if (tile || pf != 0) return nullptr;
+    if (acc == 1) {
+        if (!rec) return k_march_fwd<W, 0, 1, false>;
+        return W == 1 ? k_march_fwd<1, 0, 1, false, true> : nullptr;
+    }
+    return rec ? k_march_fwd<W, 0, 2, false, true> : k_march_fwd<W, 0, 2, false>;
+}
+
+MarchKernel pick_pair(int W, int acc, bool rec) {
+    if (acc == 0) {
+        switch (W * 2 + (rec ? 1 : 0)) {
+            case 2: return k_march_fwd_pair<1>;
+            case 3: return k_march_fwd_pair<1, true>;
+            case 4: return k_march_fwd_pair<2>;
+            case 5: return k_march_fwd_pair<2, true>;
+            case 8: return k_march_fwd_pair<4>;
+            case 9: return k_march_fwd_pair<4, true>;
+        }
+        return nullptr;
+    }
+    if (W != 1) return nullptr;
+    if (acc == 1) return rec ? k_march_fwd_pair<1, true, 1> : k_march_fwd_pair<1, false, 1>;
+    return rec ? k_march_fwd_pair<1, true, 2> : k_march_fwd_pair<1, false, 2>;
+}
+
+MarchKernel pick_march(int W, int pf, int acc, bool tile, bool rec, int lpr) {
+    if (pf < 0 || pf > 3 || acc < 0 || acc > 2) return nullptr;
+    if (lpr == 2) return pf == 0 && !tile ? pick_pair(W, acc, rec) : nullptr;
+    if (lpr != 1) return nullptr;
+    switch (W) {
+        case 1: return pick_one_lane<1>(pf, acc, tile, rec);
+        case 2: return pick_one_lane<2>(pf, acc, tile, rec);
+        case 4: return pick_one_lane<4>(pf, acc, tile, rec);
+    }
+    return nullptr;
+}
+
+bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray) {
+    return pick_march(W, prefetch, acc_mode, tile != 0 && lanes_per_ray == 1, record != 0, lanes_per_ray) != nullptr;
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
-    if (a.lanes_per_ray > 1) {
-        // two lanes per ray: block counts threads (a multiple of 32), block / 2 rays per block
-        if (a.lanes_per_ray != 2 || a.acc64 || a.st_I || a.prefetch != 0 || (a.ckpt && a.ck_stride < 1))
-            return cudaErrorInvalidValue;
-        const int block = a.block > 0 ? a.block : 64;
-        if (block % 32) return cudaErrorInvalidValue;
-        const long long rblocks = (a.ray_count + block / 2 - 1) / (block / 2);
-        const long long nblk = rblocks * a.nsrc * a.groups;
-        if (nblk <= 0) return cudaSuccess;
-        if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        switch (W * 2 + (a.ckpt ? 1 : 0)) {
-            case 2: k_march_fwd_pair<1><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 3: k_march_fwd_pair<1, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd_pair<2><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 5: k_march_fwd_pair<2, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 8: k_march_fwd_pair<4><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 9: k_march_fwd_pair<4, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    const int block = a.block > 0 ? a.block : 128;
-    const long long rblocks = (a.ray_count + block - 1) / block;
+    if (a.acc_mode < 0 || a.acc_mode > 2 || ((a.acc_mode != 0) != (a.acc64 != nullptr))) return cudaErrorInvalidValue;
+    if (a.acc_mode == 1 && !a.fix) return cudaErrorInvalidValue;
+    if (a.ckpt && a.ck_stride < 1) return cudaErrorInvalidValue;
+    const int lpr = a.lanes_per_ray <= 1 ? 1 : a.lanes_per_ray;   // 0: one lane per ray
+    const bool pair = lpr == 2;
+    if (pair && a.st_I) return cudaErrorInvalidValue;   // the stateful march runs one lane per ray
+    // tiles only when every grid extent is at least kTile (and never with two lanes per ray)
+    const bool tile = !pair && a.tile && a.n0 >= kTile && a.n1 >= kTile && a.n2 >= kTile;
+    const MarchKernel k = pick_march(W, a.prefetch, a.acc_mode, tile, a.ckpt != nullptr, lpr);
+    if (!k) return cudaErrorInvalidValue;
+    // two lanes per ray: block counts threads (a multiple of 32), block / 2 rays per block
+    const int block = a.block > 0 ? a.block : (pair ? 64 : 128);
+    if (block % 32 || block > 256) return cudaErrorInvalidValue;
+    const int rays_per_block = pair ? block / 2 : block;
+    const long long rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
     const long long nblk = rblocks * a.nsrc * a.groups;
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (a.prefetch < 0 || a.prefetch > 3) return cudaErrorInvalidValue;
-    if (a.acc64) {
-        switch (W) {   // deterministic mode: gather reuse (PF = 0), every deposit quantised on its own
-            case 1: k_march_fwd<1, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 2: k_march_fwd<2, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 4: k_march_fwd<4, 0, 1, false><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    const bool tile = a.tile && a.n0 >= kTile && a.n1 >= kTile && a.n2 >= kTile;
-    if (a.ckpt) {   // recording the adjoint's checkpoints: gathers mode 0, or 1 / 3 for one bin per thread
-        if (a.ck_stride < 1 || (W != 1 && a.prefetch != 0) || a.prefetch == 2) return cudaErrorInvalidValue;
-        switch ((W * 4 + a.prefetch) * 2 + (tile ? 1 : 0)) {
-            case 8: k_march_fwd<1, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 9: k_march_fwd<1, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 10: k_march_fwd<1, 1, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 11: k_march_fwd<1, 1, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 14: k_march_fwd<1, 3, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 15: k_march_fwd<1, 3, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 16: k_march_fwd<2, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 17: k_march_fwd<2, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 32: k_march_fwd<4, 0, 0, false, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            case 33: k_march_fwd<4, 0, 0, true, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    switch ((W * 4 + a.prefetch) * 2 + (tile ? 1 : 0)) {
-#define RT_FWD_CASE(W_, PF_)                                                                     \
-        case (W_ * 4 + PF_) * 2: k_march_fwd<W_, PF_, 0, false><<<(unsigned)nblk, block, 0, st>>>(a); break; \
-        case (W_ * 4 + PF_) * 2 + 1: k_march_fwd<W_, PF_, 0, true><<<(unsigned)nblk, block, 0, st>>>(a); break;
-        RT_FWD_CASE(1, 0) RT_FWD_CASE(1, 1) RT_FWD_CASE(1, 2) RT_FWD_CASE(1, 3)
-        RT_FWD_CASE(2, 0) RT_FWD_CASE(2, 1) RT_FWD_CASE(2, 2) RT_FWD_CASE(2, 3)
-        RT_FWD_CASE(4, 0) RT_FWD_CASE(4, 1) RT_FWD_CASE(4, 2) RT_FWD_CASE(4, 3)
-#undef RT_FWD_CASE
-        default: return cudaErrorInvalidValue;
-    }
+    k<<<(unsigned)nblk, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -346,42 +376,81 @@ cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long 
     return cudaGetLastError();
 }
 
-// ---- deterministic mode: fixed-point scale and conversion -------------------------------------
-__global__ void k_abs_max(const float* __restrict__ x, long long n, float* __restrict__ out) {
+// ---- fixed-point accumulation: unit and conversion ----------------------------------------
+// One launch clears the 8-byte accumulator and finds max|j|; the last block to finish turns it
+// into the unit fix = the largest power of two with fix * per_jmax * max|j| <= 2^62, by integer
+// operations on the encodings (no FP64 arithmetic beyond the one product), and resets the
+// reduction words for the next call. work[0]: max|j| as float bits; work[1]: finished blocks
+// (both zero before the first call).
+__global__ void k_fix_prepare(const float* __restrict__ j, long long nj, unsigned long long* __restrict__ acc,
+                              long long nacc, double per_jmax, unsigned* __restrict__ work, float* __restrict__ fix) {
     float m = 0.0f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(__ldg(x + i)));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nj || i < nacc; i += stride) {
+        if (i < nj) m = fmaxf(m, fabsf(__ldg(j + i)));
+        if (i < nacc) acc[i] = 0ull;
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) atomicMax(work, __float_as_uint(m));   // m >= 0: bit order = value order
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(work + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const float jmax = __uint_as_float(atomicExch(work, 0u));
+    atomicExch(work + 1, 0u);
+    const double bound = per_jmax * (double)jmax;
+    int e = 0;   // a zero field needs no particular unit
+    if (bound > 0.0) {
+        // bound = 2^E (1 + f): ceil(log2 bound) = E, or E + 1 when f > 0; e = 62 - ceil(log2 bound)
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(bound);
+        const int E = (int)((bits >> 52) & 0x7FF) - 1023;
+        e = 62 - E - ((bits & 0xFFFFFFFFFFFFFull) != 0ull ? 1 : 0);
+    }
+    e = max(-126, min(127, e));
+    *fix = __uint_as_float((unsigned)(e + 127) << 23);
 }
 
-// fix = the largest power of two with fix * bound <= 2^62, bound = per_jmax * max|j|
-__global__ void k_fix_scale(const float* __restrict__ jmax, double per_jmax, float* __restrict__ fix) {
-    const double bound = per_jmax * (double)*jmax;
-    double e = bound > 0.0 ? floor(log2(4.611686018427388e18 / bound)) : 0.0;
-    if (e > 126.0) e = 126.0;
-    if (e < -126.0) e = -126.0;
-    *fix = (float)exp2(e);
-}
-
-// out[b][c] (+)= acc[g][c][w] / fix for bin b = g * W + w (the packed fixed-point layout)
+// out[b][c] (+)= acc[g][c][w] / fix for bin b = g * W + w (the packed fixed-point layout): the
+// integer is rounded once to FP32 and scaled by the power of two 1 / fix (exact)
 __global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int n_freq, int W, long long ncell,
                                  const float* __restrict__ fix, float* __restrict__ out, int accumulate) {
-    const double inv = 1.0 / (double)*fix;
+    const float inv = 1.0f / *fix;
     const long long n = (long long)n_freq * ncell;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long b = i / ncell, c = i - b * ncell;
         const long long g = b / W, w = b - g * W;
-        const float v = (float)((double)(long long)acc[(g * ncell + c) * W + w] * inv);
+        const float v = __ll2float_rn((long long)acc[(g * ncell + c) * W + w]) * inv;
         out[i] = accumulate ? out[i] + v : v;
     }
 }
 
-cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, float* fix, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(jmax_tmp, 0, sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    k_abs_max<<<grid_for(n, 256), 256, 0, st>>>(j, n, jmax_tmp);
-    k_fix_scale<<<1, 1, 0, st>>>(jmax_tmp, per_jmax, fix);
+// out[b][c] (+)= (float) (scale * acc[g][c][w]) for bin b = g * W + w (the packed FP64 layout)
+__global__ void k_f64_to_float(const double* __restrict__ acc, int n_freq, int W, long long ncell, double scale,
+                               float* __restrict__ out, int accumulate) {
+    const long long n = (long long)n_freq * ncell;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / ncell, c = i - b * ncell;
+        const long long g = b / W, w = b - g * W;
+        const float v = (float)(scale * __ldg(acc + (g * ncell + c) * W + w));
+        out[i] = accumulate ? out[i] + v : v;
+    }
+}
+
+cudaError_t launch_f64_to_float(const double* acc, int n_freq, int W, long long ncell, double scale, float* out,
+                                int accumulate, cudaStream_t st) {
+    k_f64_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, W, ncell, scale, out,
+                                                                            accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_prepare(const float* j, long long nj, unsigned long long* acc, long long nacc,
+                               double per_jmax, unsigned* work, float* fix, cudaStream_t st) {
+    k_fix_prepare<<<grid_for(nj > nacc ? nj : nacc, 256), 256, 0, st>>>(j, nj, acc, nacc, per_jmax, work, fix);
     return cudaGetLastError();
 }
 

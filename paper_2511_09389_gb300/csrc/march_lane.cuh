@@ -38,8 +38,9 @@ struct Lane {
     const float* __restrict__ jg;
     const float* __restrict__ kg;
     float* __restrict__ og;
-    unsigned long long* __restrict__ og64;   // deterministic mode: fixed-point accumulator of the
-                                              //   group, packed like og ([cell][W], 8-byte units)
+    unsigned long long* __restrict__ og64;   // 8-byte accumulator of the group, packed like og
+                                              //   ([cell][W]): fixed point (deterministic mode) or
+                                              //   FP64 (the wide accumulation), see flush()
     long long ncell;
     int nbins;                                //   real bins in this group (the rest are padding)
     const float* fix;                         //   units per unit deposit, a power of two (device)
@@ -68,12 +69,21 @@ struct RayState {
     float I[W], tau[W];
 };
 
-// Send one merged deposit (the sums for one corner) to memory: a W-wide FP32 reduction, or in
-// deterministic mode one 64-bit fixed-point reduction per real bin (integer addition is
-// associative, so the result does not depend on the order of the deposits).
+// Send one merged deposit (the sums for one corner) to memory. DET (the accumulation):
+//   0: one W-wide FP32 reduction;
+//   1: deterministic mode, one 64-bit fixed-point reduction per real bin (integer addition is
+//      associative, so the result does not depend on the order of the deposits);
+//   2: one FP64 reduction per real bin (the sums keep 53 bits however many small deposits a
+//      large cell sum takes; same L2 rate per operation as the W-wide FP32 one).
+// Modes 1 and 2 use the 8-byte accumulator og64, packed like og ([cell][W]).
 template <int W, int DET>
 __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
-    if (DET) {
+    if (DET == 2) {
+        double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            if (b < L.nbins) red_add_f64(o + b, v[b]);
+    } else if (DET) {
         // v * 2^k is exact in FP32; its rounding to an integer is the fixed-point quantisation
         const float f = __ldg(L.fix);
 #pragma unroll
@@ -88,7 +98,11 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
 // flush() when p is true, without a branch (callers pass a valid cell either way).
 template <int W, int DET>
 __device__ __forceinline__ void flush_if(bool p, const Lane& L, int cell, const float* v) {
-    if (DET) {
+    if (DET == 2) {
+        double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
+#pragma unroll
+        for (int b = 0; b < W; ++b) red_add_f64_if(p && b < L.nbins, o + b, v[b]);
+    } else if (DET) {
         const float f = __ldg(L.fix);
 #pragma unroll
         for (int b = 0; b < W; ++b)
@@ -549,7 +563,7 @@ __device__ __forceinline__ void march_lane_runs(const Lane& L, RayState<W>& R) {
 // shuffle per bin (a + b and b + a are the same FP32 number, so both lanes carry identical I
 // and tau). pmask holds the pair's two lanes. REC: lane 0 of the pair stores the reverse march's
 // checkpoints (x_k, I_k, tau_k) every ck_stride substeps (both lanes hold the same values).
-template <int W, bool REC = false>
+template <int W, bool REC = false, int DET = 0>
 __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned pmask) {
     const float* __restrict__ jg = L.jg;
     const float* __restrict__ kg = L.kg;
@@ -614,7 +628,7 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 flag[i] = (mask >> (2 * i)) & 1u;
-                red_vec_if<W>(flag[i] && pc[i] >= 0, L.og, max(pc[i], 0), pend[i]);
+                flush_if<W, DET>(flag[i] && pc[i] >= 0, L, max(pc[i], 0), pend[i]);
 #pragma unroll
                 for (int b = 0; b < W; ++b) pend[i][b] = flag[i] ? 0.0f : pend[i][b];
             }
@@ -673,7 +687,7 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        if (pc[i] >= 0) red_vec<W>(L.og, pc[i], pend[i]);
+        if (pc[i] >= 0) flush<W, DET>(L, pc[i], pend[i]);
 }
 
 // Gathers modes: PF = 0 march_lane_slots, 1 and 3 march_lane_runs, 2 march_lane_ahead. REC

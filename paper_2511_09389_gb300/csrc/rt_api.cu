@@ -149,6 +149,8 @@ struct rt_grid {
     };
     std::vector<std::pair<TuneKey, std::pair<Plan, float>>> tuned;
     Plan last_plan;
+    int last_acc = 0;          // accumulation of the last forward call (MarchArgs::acc_mode)
+    bool dets_zeroed = false;  // the fixed-point reduction words of the DETS slot are zero
     float last_plan_ms = -1.0f;
     std::string tune_report;   // candidates timed by the last autotuning pass
     // state of the stateful advance (rt_advance_continue): which problem it belongs to, which of
@@ -248,6 +250,7 @@ struct rt_grid {
             buf[s] = nullptr;
             cap[s] = 0;
         }
+        dets_zeroed = false;
     }
 };
 
@@ -349,6 +352,100 @@ int pick_width(int n_freq) {
     return 4;
 }
 
+// Accumulation of a launch plan (MarchArgs::acc_mode: 0 FP32, 1 fixed point, 2 FP64).
+// deterministic = 1 or rt_options.accumulation 3: 64-bit fixed point; 1: FP32; 2: FP64;
+// 0 (automatic): FP32 unless the call deposits at least kDenseUpdates updates per cell and bin on
+// average (N_src N_Omega N_s >= kDenseUpdates n0 n1 n2), where crowded cells -- around clustered
+// sources, on the clamped corners of the box -- take so many small deposits on top of large sums
+// that FP32 rounds a measurable part of them away (rel-L2 ~1e-4 against the oracle on 2,097
+// clustered sources, ~1,000 updates per cell); such calls sum in 64-bit fixed point (measured on
+// GB300: the same one-bin march time as FP32 there), or in FP64 where the fixed-point unit would
+// be coarse (fixed_point_fits) or a continued march carries intensities past its bound. Source
+// tiles sum in FP32 shared memory: a plan that pins them keeps FP32.
+constexpr double kDenseUpdates = 32.0;
+
+bool fixed_point_fits(const Call& a, int ns) {
+    // the fixed-point unit is the bound 4 pi N_src ds max|j| N_s (N_s + 1) / 2 over 2^62; with
+    // N_src N_s (N_s + 1) / 2 <= 2^32 it is at most 2^-30 of 4 pi ds max|j|, the scale of one
+    // ray's first deposit
+    return (double)a.nsrc * (double)ns * ((double)ns + 1.0) * 0.5 <= 4294967296.0;
+}
+
+// The automatic choice for the call, before any plan: 0 FP32, 1 fixed point, 2 FP64.
+int auto_accumulation(const rt_grid* g, const Call& a, int ns) {
+    const double updates = (double)a.nsrc * (double)(a.ray_end - a.ray_begin) * (double)ns;
+    if (updates < kDenseUpdates * (double)g->ncell()) return 0;
+    return fixed_point_fits(a, ns) && !a.st_I ? 1 : 2;
+}
+
+int acc_mode_for(const rt_grid* g, const Plan& p, const Call& a, int ns) {
+    // (carried intensities of a continued march void the fixed-point bound: FP64 then)
+    if (g->opt.deterministic || g->opt.accumulation == 3) return a.st_I ? 2 : 1;
+    if (g->opt.accumulation == 1) return 0;
+    if (g->opt.accumulation == 2) return 2;
+    if (p.lpr == 1 && p.tile) return 0;
+    return auto_accumulation(g, a, ns);
+}
+
+// Set up the accumulator of acc_mode on the call's stream (after prepare()): mode 1 computes the
+// fixed-point unit from max|j| and clears the 8-byte accumulator, mode 2 clears it; mode 0 was
+// set up by prepare() (packing cleared the packed FP32 accumulator; for W = 1 the caller clears
+// out_field unless accumulating). Fills m->acc_mode, acc64, fix and dep_scale.
+rt_status setup_accumulator(rt_grid* g, const Call& a, int ns, const Plan& plan, int acc, float scale,
+                            rt::MarchArgs* m) {
+    m->acc_mode = acc;
+    if (acc == 0) return RT_OK;
+    const int groups = (a.n_freq + plan.W - 1) / plan.W;
+    const long long ncell = g->ncell();
+    const size_t bytes = 8 * (size_t)groups * plan.W * ncell;
+    void* p = nullptr;
+    rt_status st = g->ensure(rt_grid::ACC64, bytes, &p);
+    if (st != RT_OK) return st;
+    m->acc64 = (unsigned long long*)p;
+    if (acc == 1) {
+        // 64-bit fixed point: every flushed deposit s * w * I is rounded to a multiple of 1 / fix
+        // and added as an integer, so the sums are independent of the order of the deposits. With
+        // kappa >= 0 each I_{k+1} <= (k+1) ds max|j|, so a cell sums to at most
+        // 4 pi N_src ds max|j| N_s (N_s + 1) / 2 per bin; fix keeps that below 2^62. One launch
+        // clears the accumulator and computes fix.
+        void* dets = nullptr;
+        if ((st = g->ensure(rt_grid::DETS, 16, &dets)) != RT_OK) return st;
+        if (!g->dets_zeroed) {   // the reduction words start at zero; each call leaves them so
+            RT_CUDA(cudaMemsetAsync(dets, 0, 16, a.st), "cudaMemsetAsync(fixed-point words)");
+            g->dets_zeroed = true;
+        }
+        float* fix = (float*)dets;
+        unsigned* work = (unsigned*)((char*)dets + 8);
+        const double per_jmax = 4.0 * 3.14159265358979323846 * (double)a.nsrc * (double)a.ds * (double)ns *
+                                ((double)ns + 1.0) * 0.5;
+        RT_CUDA(rt::launch_fix_prepare(a.j, (long long)a.n_freq * ncell, (unsigned long long*)p,
+                                       (long long)(bytes / 8), per_jmax, work, fix, a.st),
+                "fixed-point set-up");
+        m->fix = fix;
+        m->dep_scale = scale;
+        return RT_OK;
+    }
+    m->dep_scale = 1.0f;   // 4 pi / N_Omega is applied in FP64 by the conversion
+    RT_CUDA(cudaMemsetAsync(p, 0, bytes, a.st), "cudaMemsetAsync(8-byte accumulator)");
+    return RT_OK;
+}
+
+// After the march: the 8-byte accumulators are converted into out_field (scaled, unpacked,
+// added when accumulating); the packed FP32 one is unpacked for W > 1.
+rt_status finish_accumulator(rt_grid* g, const Call& a, const Plan& plan, float scale, const rt::MarchArgs& m) {
+    const long long ncell = g->ncell();
+    if (m.acc_mode == 1)
+        RT_CUDA(rt::launch_fixed_to_float(m.acc64, a.n_freq, plan.W, ncell, m.fix, a.out, a.accumulate, a.st),
+                "fixed-point conversion");
+    else if (m.acc_mode == 2)
+        RT_CUDA(rt::launch_f64_to_float((const double*)m.acc64, a.n_freq, plan.W, ncell, (double)scale, a.out,
+                                        a.accumulate, a.st),
+                "FP64 conversion launch");
+    else if (plan.W > 1)
+        RT_CUDA(rt::launch_unpack(m.acc, a.out, a.n_freq, plan.W, ncell, scale, a.accumulate, a.st), "unpack launch");
+    return RT_OK;
+}
+
 // Lay out the inputs for bin-group width W (packing for W > 1) and fill the march arguments.
 // The accumulator is `out` itself for W = 1 with an output, else the handle's scratch; with
 // clear_acc, packing for W > 1 also zeroes the packed accumulator (same launch).
@@ -434,11 +531,22 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
         p.W = cands[ci].W; p.block = cands[ci].block; p.prefetch = cands[ci].prefetch;
         p.lpr = cands[ci].lpr; p.tile = cands[ci].tile;
         const int W = p.W, b = p.block;
+        // tiles sum in FP32: not a plan of an 8-byte accumulation, nor of the automatic mode for one
+        // bin (whose other plans sum in 8-byte words)
+        if (p.lpr == 1 && p.tile && g->opt.accumulation == 0 && auto_accumulation(g, a, ns) != 0) continue;
+        const int acc = acc_mode_for(g, p, a, ns);
+        if (acc != 0 && p.lpr == 1 && p.tile) continue;
+        if (!rt::march_fwd_available(W, p.prefetch, acc, p.tile, 0, p.lpr)) continue;
         rt::MarchArgs m;
         if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
         float cand_ms = 3.0e38f;
         for (int rep = 0; rep < 2; ++rep) {
-            ce = cudaMemsetAsync(m.acc, 0, acc_bytes(g, a, p), a.st);
+            if (acc != 0) {
+                if ((st = setup_accumulator(g, a, ns, p, acc, scale, &m)) != RT_OK) break;
+                ce = cudaSuccess;
+            } else {
+                ce = cudaMemsetAsync(m.acc, 0, acc_bytes(g, a, p), a.st);
+            }
             if (ce == cudaSuccess) ce = cudaEventRecord(e[0], a.st);
             if (ce == cudaSuccess) ce = rt::launch_march_fwd(W, m, a.st);
             if (ce == cudaSuccess) ce = cudaEventRecord(e[1], a.st);
@@ -450,9 +558,9 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
             if (ms < best_ms) { best_ms = ms; bp = p; }
         }
         if (st == RT_OK) {
-            char line[112];
-            snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d %.4f ms\n", W, b,
-                     p.prefetch, p.lpr, p.tile, cand_ms);
+            char line[128];
+            snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d acc=%s %.4f ms\n", W, b,
+                     p.prefetch, p.lpr, p.tile, acc == 2 ? "fp64" : (acc == 1 ? "fixed" : "fp32"), cand_ms);
             g->tune_report += line;
         }
     }
@@ -502,50 +610,34 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if ((st = g->table(a.num_rays, a.ray_begin, a.ray_end, &dirs)) != RT_OK) return st;
     const float scale = (float)(4.0 * 3.14159265358979323846 / (double)a.num_rays);
 
-    if (g->opt.deterministic) {
-        // 64-bit fixed point: every flushed deposit s * w * I is rounded to a multiple of
-        // 1 / fix and added as an integer, so the sums are independent of the order of the
-        // deposits. With kappa >= 0 each I_{k+1} <= (k+1) ds max|j|, so the whole field is at
-        // most 4 pi N_src ds max|j| N_s (N_s + 1) / 2 per bin; fix keeps that below 2^62.
-        Plan plan;
-        plan.W = g->opt.plan_width ? g->opt.plan_width : pick_width(a.n_freq);
-        plan.block = g->opt.plan_block ? g->opt.plan_block : 32;
-        plan.prefetch = 0;
-        g->last_plan = plan;
-        g->last_plan_ms = -1.0f;
-        rt::MarchArgs m;
-        if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m)) != RT_OK) return st;
-        void *acc64 = nullptr, *dets = nullptr;
-        const int groups = (a.n_freq + plan.W - 1) / plan.W;
-        const size_t acc64_bytes = sizeof(unsigned long long) * (size_t)groups * plan.W * ncell;
-        if ((st = g->ensure(rt_grid::ACC64, acc64_bytes, &acc64)) != RT_OK) return st;
-        if ((st = g->ensure(rt_grid::DETS, 16, &dets)) != RT_OK) return st;
-        float* fix = (float*)dets;
-        float* jmax = (float*)((char*)dets + 8);
-        const double per_jmax = 4.0 * 3.14159265358979323846 * (double)a.nsrc * (double)a.ds * (double)ns *
-                                ((double)ns + 1.0) * 0.5;
-        RT_CUDA(rt::launch_fix_scale(a.j, (long long)a.n_freq * ncell, per_jmax, jmax, fix, a.st), "fixed-point scale");
-        RT_CUDA(cudaMemsetAsync(acc64, 0, acc64_bytes, a.st), "cudaMemsetAsync(fixed-point accumulator)");
-        m.acc64 = (unsigned long long*)acc64;
-        m.fix = fix;
-        m.dep_scale = scale;
-        if ((st = g->mark(0, a.st)) != RT_OK) return st;
-        RT_CUDA(rt::launch_march_fwd(plan.W, m, a.st), "march kernel launch");
-        if ((st = g->mark(1, a.st)) != RT_OK) return st;
-        RT_CUDA(rt::launch_fixed_to_float((const unsigned long long*)acc64, a.n_freq, plan.W, ncell, fix, a.out,
-                                          a.accumulate, a.st),
-                "fixed-point conversion");
-        return RT_OK;
-    }
-
-    // default plan (measured on GB300): 32-thread blocks; gather prefetch and source deposit
-    // tiles only pay for one bin per thread (a tiled 4-bin deposit is 32 shared-memory atomics)
+    // default plan (measured on GB300): 32-thread blocks. Summing in FP32: gather prefetch and
+    // source deposit tiles for one bin per thread, neither for wider groups (a tiled 4-bin deposit
+    // is 32 shared-memory atomics). Summing in 8-byte words (no tiles): corner slots, and for one
+    // bin two lanes per ray while the call has too few lanes to fill the GPU (twice as fast on 64^3
+    // with 8 sources, slower on 2,097 sources)
+    const bool det = g->opt.deterministic != 0;
     Plan plan;
     plan.W = pick_width(a.n_freq);
     plan.block = 32;
     plan.prefetch = plan.W == 1 ? 1 : 0;
     if (g->opt.plan_width) plan.W = g->opt.plan_width;
     plan.tile = plan.W == 1 ? 1 : 0;
+    {
+        Plan untiled = plan;
+        untiled.tile = 0;
+        if (acc_mode_for(g, untiled, a, ns) != 0) {
+            const double lanes = (double)a.nsrc * (a.ray_end - a.ray_begin) * ((a.n_freq + plan.W - 1) / plan.W);
+            plan.prefetch = 0;
+            plan.tile = 0;
+            plan.lpr = plan.W == 1 && lanes < 152.0 * 1024.0 ? 2 : 1;
+        }
+    }
+    if (det) {   // deterministic mode: corner slots, one lane per ray (validated at creation)
+        plan.prefetch = 0;
+        plan.tile = 0;
+        plan.lpr = 1;
+        plan.block = 32;
+    }
     if (g->opt.plan_block) plan.block = g->opt.plan_block;
     if (g->opt.plan_prefetch) plan.prefetch = g->opt.plan_prefetch - 1;
     if (g->opt.plan_lanes) plan.lpr = g->opt.plan_lanes;
@@ -553,7 +645,7 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (plan.lpr != 1 && (plan.lpr != 2 || plan.prefetch))
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 1, or 2 with gathers mode 0");
     g->last_plan_ms = -1.0f;
-    if (g->opt.autotune && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
+    if (g->opt.autotune && !det && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
     if (a.st_I && plan.lpr > 1) {   // the stateful march runs one lane per (ray, source, bin group)
         plan.lpr = 1;
         plan.prefetch = 0;
@@ -562,28 +654,40 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     // one lane per ray, or for one bin per thread two lanes per ray (measured on GB300, 64^3 with
     // 24,576 lanes: 0.12 ms against 0.16 for mode 3, 0.16 for mode 1 and 0.24 for mode 0 with one
     // lane), unless a plan with gathers mode 0, 1 or 3 was pinned or tuned
-    const bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
+    bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
     if (record) {
         const int w = pick_width(a.n_freq);
         const bool keep = plan.W == w && (g->opt.plan_prefetch || g->opt.plan_lanes || g->opt.autotune);
         if (!keep) {
             plan.block = 32;
             plan.tile = 0;
-            plan.lpr = w == 1 ? 2 : 1;
+            plan.lpr = w == 1 && !det ? 2 : 1;
         }
         plan.W = w;
         if (plan.lpr == 2 || w != 1) plan.prefetch = 0;   // corner slots
         else if (plan.prefetch == 2) plan.prefetch = 3;   // (recording has no gathers mode 2)
     }
+    const int acc = acc_mode_for(g, plan, a, ns);
+    if (acc != 0) plan.tile = 0;
+    // a plan that this accumulation has no kernel for falls back to corner slots (every mode has
+    // them); recording stays off where no recording kernel exists (the reverse march then makes
+    // its own forward sweep)
+    if (!rt::march_fwd_available(plan.W, plan.prefetch, acc, plan.tile, record, plan.lpr)) {
+        plan.prefetch = 0;
+        if (!rt::march_fwd_available(plan.W, 0, acc, plan.tile, record, plan.lpr)) plan.lpr = 1;
+        if (record && !rt::march_fwd_available(plan.W, 0, acc, plan.tile, 1, plan.lpr)) record = false;
+    }
     g->last_plan = plan;
+    g->last_acc = acc;
 
     rt::MarchArgs m;
-    if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m, true)) != RT_OK) return st;
+    if ((st = prepare(g, a, ns, plan, dirs, scale, plan.W == 1 ? a.out : nullptr, &m, acc == 0)) != RT_OK) return st;
     m.st_pos_in = a.st_pos_in;
     m.st_pos_out = a.st_pos_out;
     m.st_I = a.st_I;
     m.st_tau = a.st_tau;
     m.st_read = a.st_read;
+    if (!record && g->opt.record_checkpoints) g->rec.valid = false;
     if (record) {
         rt::BackArgs sz{};
         sz.ray_count = a.num_rays; sz.nsrc = a.nsrc; sz.n_freq = a.n_freq; sz.ns = ns;
@@ -604,15 +708,15 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         g->rec = rt_grid::Recording{true, a.j, a.kappa, a.src, a.nsrc, a.num_rays, ns, a.n_freq, sz.stride,
                                     plan.W, g->opt.kappa_mode, a.ds};
     }
-    if (plan.W == 1 && !a.accumulate)   // (for W > 1 the packing launch cleared the accumulator)
+    if (acc != 0) {
+        if ((st = setup_accumulator(g, a, ns, plan, acc, scale, &m)) != RT_OK) return st;
+    } else if (plan.W == 1 && !a.accumulate) {   // (for W > 1 the packing launch cleared the accumulator)
         RT_CUDA(cudaMemsetAsync(m.acc, 0, field_bytes, a.st), "cudaMemsetAsync(accumulator)");
+    }
     if ((st = g->mark(0, a.st)) != RT_OK) return st;
     RT_CUDA(rt::launch_march_fwd(plan.W, m, a.st), "march kernel launch");
     if ((st = g->mark(1, a.st)) != RT_OK) return st;
-    if (plan.W > 1)
-        RT_CUDA(rt::launch_unpack(m.acc, a.out, a.n_freq, plan.W, ncell, scale, a.accumulate, a.st),
-                "unpack launch");
-    return RT_OK;
+    return finish_accumulator(g, a, plan, scale, m);
 }
 
 }  // namespace
@@ -645,6 +749,8 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
     if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2)
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1 or 2");
     if (o.plan_tile < 0 || o.plan_tile > 2) return fail(RT_ERR_INVALID_ARG, "plan_tile must be 0, 1 or 2");
+    if (o.accumulation < 0 || o.accumulation > 3)
+        return fail(RT_ERR_INVALID_ARG, "accumulation must be 0, 1, 2 or 3");
     // the fixed-point march runs one lane per ray with corner slots and no tiles: a pinned plan
     // asking for anything else would be accepted here and then silently not used
     if (o.deterministic && (o.plan_lanes == 2 || o.plan_tile == 2 || o.plan_prefetch > 1))
@@ -929,6 +1035,12 @@ rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, int* l
     if (lanes_per_ray) *lanes_per_ray = g->last_plan.lpr;
     if (tile) *tile = g->last_plan.lpr == 1 ? g->last_plan.tile : 0;
     if (tuned_ms) *tuned_ms = g->last_plan_ms;
+    return RT_OK;
+}
+
+rt_status rt_last_accumulation(rt_grid* g, int* mode) {
+    if (!g || !mode) return fail(RT_ERR_INVALID_ARG, "NULL argument");
+    *mode = g->last_acc == 0 ? 1 : (g->last_acc == 2 ? 2 : 3);
     return RT_OK;
 }
 

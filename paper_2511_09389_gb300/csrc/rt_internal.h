@@ -25,7 +25,9 @@ struct MarchArgs {
     const float* jp;        // packed j    [groups][ncell][W]   (W = 1: plain [n_freq][ncell])
     const float* kp;        // packed kappa, same layout
     float* acc;             // FP32 accumulator, same layout (W = 1: may be the output itself)
-    unsigned long long* acc64;  // fixed-point accumulator [groups][ncell][W] (deterministic mode) or NULL
+    int acc_mode;               // 0: FP32 reductions into acc; 1: 64-bit fixed point into acc64
+                                // (deterministic mode); 2: FP64 reductions into acc64 (as double)
+    unsigned long long* acc64;  // 8-byte accumulator [groups][ncell][W] (modes 1 and 2) or NULL
     const float* fix;           // fixed-point units per unit deposit, a power of two (device scalar)
     const float4* dirs;     // ray directions (xyz, w unused), ray_count entries
     const float* src;       // device [nsrc][3]
@@ -59,6 +61,9 @@ struct MarchArgs {
 };
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);
+// Whether a forward kernel is compiled for this plan and accumulation (acc_mode as in MarchArgs;
+// record: with adjoint checkpoints). launch_march_fwd returns cudaErrorInvalidValue otherwise.
+bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray);
 
 // A forward launch plan: bins per thread W, threads per block, gather mode (MarchArgs::prefetch),
 // lanes per ray, source tiles.
@@ -78,9 +83,12 @@ cudaError_t launch_pack_pair(const float* j, const float* kappa, float* jp, floa
 // out[b][c] (+)= scale * acc[b / W][c][b % W]
 cudaError_t launch_unpack(const float* acc, float* out, int n_freq, int W, long long ncell,
                           float scale, int accumulate, cudaStream_t st);
-// Deterministic mode: *fix = largest power of two with fix * per_jmax * max|j| <= 2^62
-// (jmax_tmp: device float scratch), and out[b][c] (+)= acc[b / W][c][b % W] / *fix.
-cudaError_t launch_fix_scale(const float* j, long long n, double per_jmax, float* jmax_tmp, float* fix, cudaStream_t st);
+// Fixed-point accumulation: acc (nacc words) set to zero and *fix = the largest power of two with
+// fix * per_jmax * max|j| <= 2^62 (j: nj floats), in one launch; work: 2 device words, zero before
+// the first call and left zero by every call.
+cudaError_t launch_fix_prepare(const float* j, long long nj, unsigned long long* acc, long long nacc,
+                               double per_jmax, unsigned* work, float* fix, cudaStream_t st);
+// out[b][c] (+)= acc[b / W][c][b % W] / *fix.
 // Checked mode: flags (4 device ints, cleared first) mark non-finite j / negative or non-finite
 // kappa / non-finite or too large source coordinates / non-finite extra (a loss gradient, may be NULL).
 cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n, const float* src, int nsrc,
@@ -89,6 +97,9 @@ cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n,
 // (order-independent; equal inputs give equal hashes); checkpoint reuse compares two of them.
 cudaError_t launch_input_hash(const float* j, const float* kappa, long long n, const float* src, int nsrc,
                               unsigned long long* out, cudaStream_t st);
+// FP64 accumulation: out[b][c] (+)= (float) (scale * acc[b / W][c][b % W]), the product in FP64.
+cudaError_t launch_f64_to_float(const double* acc, int n_freq, int W, long long ncell, double scale, float* out,
+                                int accumulate, cudaStream_t st);
 cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
                                   float* out, int accumulate, cudaStream_t st);
 

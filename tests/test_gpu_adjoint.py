@@ -274,7 +274,8 @@ def test_recorded_checkpoints_after_inputs_rewritten_in_place(torch_cuda, n_freq
     rt_advance and rt_backward (same pointers, same scalars) gets the gradients of the new
     contents: the reverse march compares a content hash of the inputs taken at the forward with
     one taken at the backward, on the device, and repeats the forward sweep when they differ. The
-    result is bit-equal to a handle that never recorded; with the inputs untouched the recording is
+    result matches a handle that never recorded (up to the order of the FP32 gradient atomics), and
+    both match the oracle's adjoint of the new inputs; with the inputs untouched the recording is
     used and gives the same gradients within the bar."""
     import ctypes
     torch = torch_cuda
@@ -321,7 +322,7 @@ def test_recorded_checkpoints_after_inputs_rewritten_in_place(torch_cuda, n_freq
     fresh = Grid(p.shape, 8)                    # never recorded: its own forward sweep
     ref = backward(fresh._h)
     for a, b in zip(new, ref):
-        assert np.array_equal(a, b)
+        assert rel(a, b) <= 1e-5     # stale checkpoints would be off by the rewrite itself
     q = inputs.Problem(p.name, j.cpu().numpy(), k.cpu().numpy(), s.cpu().numpy(), p.num_rays, p.step_size,
                        p.radiation_velocity, p.time_step)
     nj, nk = oracle_backward(q, G)
