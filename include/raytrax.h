@@ -62,8 +62,9 @@ typedef struct {
                            bitwise identical for every launch plan and deposit order.
                            rt_advance / rt_advance_rays only (no autotuning, no batch). Honours
                            plan_width and plan_block; rt_create_grid rejects plan_lanes 2,
-                           plan_tile 2 and plan_prefetch > 1 with it (one lane per ray, corner
-                           slots, no tiles). */
+                           plan_tile 2 and plan_prefetch other than 0, 1 or 5 with it (one lane
+                           per ray, corner slots -- gathers mode 0 or 4, which sum alike -- and no
+                           tiles). */
     int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
     int ns_cap;         /* 0: none; > 0: cap on the substep count (the optional cap of Sec. 2) */
     int autotune;       /* 1: time the launch shapes once per shape class and keep the best */
@@ -75,9 +76,10 @@ typedef struct {
        multiple of 32). plan_prefetch: gathers mode + 1, where mode 0 keeps the 8 corners in
        slots (when the ray crosses a face, the 4 corners on it keep their gathered j and their
        summed deposits; the other 4 are flushed and re-gathered), mode 1 issues the next
-       substep's gathers before the current update, mode 2 does both, and mode 3 reuses the
+       substep's gathers before the current update, mode 2 does both, mode 3 reuses the
        whole corner set while it is unchanged and flushes and re-gathers all 8 corners when it
-       changes. plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
+       changes, and mode 4 is mode 0 with the corners that enter at substep k+1 gathered before
+       the update of substep k (no tiles, no checkpoint recording). plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
        the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 only). plan_tile: source deposit tiles (1: off, 2: on): each
        block sums the deposits of its rays in the 8^3 cells around its source in shared memory
        and adds them to the field once (not in deterministic mode). */

@@ -21,8 +21,16 @@ __device__ __forceinline__ int tile_origin(float src, int n) {
 // the field once per block. The cells next to a source receive a deposit from every ray of it,
 // so this takes the most contended L2 atomics off the march and sums them in shorter chains.
 // REC: also write the reverse march's checkpoints (march_lane).
+// Gathers mode 4 with four bins keeps a second set of slot values in registers: it launches with
+// 32-thread blocks only, bounded so that 11 of them fit on an SM (a 128^3 problem with 16 sources
+// and 3072 rays has 10.1 warps per SM of the 152).
+template <int W, int PF>
+constexpr int fwd_max_threads() { return PF == 4 && W == 4 ? 32 : 256; }
+template <int W, int PF>
+constexpr int fwd_min_blocks() { return PF == 4 && W == 4 ? 11 : 1; }
+
 template <int W, int PF, int DET, bool TILE, bool REC = false>
-__global__ void __launch_bounds__(256) k_march_fwd(MarchArgs a) {
+__global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF>()) k_march_fwd(MarchArgs a) {
     constexpr int TCELLS = kTile * kTile * kTile;
     __shared__ float tile[TILE ? TCELLS * W : 1];
     const int rblocks = (a.ray_count + blockDim.x - 1) / blockDim.x;
@@ -155,14 +163,21 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
 
 // ---- kernel table ------------------------------------------------------------------------
 // The compiled (W, gathers mode, accumulation, tiles, checkpoints, lanes per ray) combinations:
-//   FP32: every W and gathers mode with and without tiles; recording with gathers mode 0 (and
-//         1 or 3 for one bin); two lanes per ray for every W.
-//   fixed point: corner slots for every W; for one bin also recording and two lanes per ray.
+//   FP32: every W and gathers mode with and without tiles (mode 4: without); recording with
+//         gathers mode 0 (and 1 or 3 for one bin); two lanes per ray for every W.
+//   fixed point: corner slots and gathers mode 4 for every W; for one bin also recording and two
+//         lanes per ray.
 //   FP64: corner slots for every W, with and without recording; two lanes per ray for one bin.
 using MarchKernel = void (*)(MarchArgs);
 
 template <int W>
 MarchKernel pick_one_lane(int pf, int acc, bool tile, bool rec) {
+    if (pf == 4) {   // corner slots with the gathers one substep ahead: no tiles, no recording
+        if (tile || rec) return nullptr;
+        if (acc == 0) return k_march_fwd<W, 4, 0, false>;
+        if (acc == 1) return k_march_fwd<W, 4, 1, false>;
+        return nullptr;
+    }
     if (acc == 0 && !rec) {
         switch (pf * 2 + (tile ? 1 : 0)) {
             case 0: return k_march_fwd<W, 0, 0, false>;
@@ -208,7 +223,7 @@ MarchKernel pick_pair(int W, int acc, bool rec) {
 }
 
 MarchKernel pick_march(int W, int pf, int acc, bool tile, bool rec, int lpr) {
-    if (pf < 0 || pf > 3 || acc < 0 || acc > 2) return nullptr;
+    if (pf < 0 || pf > 4 || acc < 0 || acc > 2) return nullptr;
     if (lpr == 2) return pf == 0 && !tile ? pick_pair(W, acc, rec) : nullptr;
     if (lpr != 1) return nullptr;
     switch (W) {
@@ -219,8 +234,12 @@ MarchKernel pick_march(int W, int pf, int acc, bool tile, bool rec, int lpr) {
     return nullptr;
 }
 
-bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray) {
-    return pick_march(W, prefetch, acc_mode, tile != 0 && lanes_per_ray == 1, record != 0, lanes_per_ray) != nullptr;
+int max_block(int W, int pf, int lpr) { return lpr == 1 && pf == 4 && W == 4 ? fwd_max_threads<4, 4>() : 256; }
+
+bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray, int block) {
+    const int lpr = lanes_per_ray <= 1 ? 1 : lanes_per_ray;
+    if (block > max_block(W, prefetch, lpr)) return false;
+    return pick_march(W, prefetch, acc_mode, tile != 0 && lpr == 1, record != 0, lpr) != nullptr;
 }
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
@@ -235,8 +254,8 @@ cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st) {
     const MarchKernel k = pick_march(W, a.prefetch, a.acc_mode, tile, a.ckpt != nullptr, lpr);
     if (!k) return cudaErrorInvalidValue;
     // two lanes per ray: block counts threads (a multiple of 32), block / 2 rays per block
-    const int block = a.block > 0 ? a.block : (pair ? 64 : 128);
-    if (block % 32 || block > 256) return cudaErrorInvalidValue;
+    const int block = a.block > 0 ? a.block : (pair ? 64 : (a.prefetch == 4 && W == 4 ? 32 : 128));
+    if (block % 32 || block > max_block(W, a.prefetch, lpr)) return cudaErrorInvalidValue;
     const int rays_per_block = pair ? block / 2 : block;
     const long long rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
     const long long nblk = rblocks * a.nsrc * a.groups;

@@ -437,6 +437,208 @@ __device__ __forceinline__ void march_lane_slots(const Lane& L, RayState<W>& R) 
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
 }
 
+// Gathers mode 4: the corner slots of mode 0 with the gathers of each substep issued one substep
+// early. Positions do not depend on the intensity, so while substep k is updated, the slot
+// transition k -> k+1 is already known: as soon as the trilinear sum of substep k has read the
+// slots, the j values of the corners that enter at k+1 are loaded into the slots that they replace
+// (and, once kappa(x_k) has been used, kappa(x_{k+1}) into its register). Their latency overlaps
+// the rest of substep k and the geometry of k+1 instead of stalling the trilinear sum that needs
+// them. Flushes happen at the same points and the deposits are summed in the same order as in
+// mode 0, so the two modes produce the same sums. REC: checkpoints as in mode 0.
+template <int W, int DET, bool REC>
+__device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W>& R) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = R.x, y = R.y, z = R.z;
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = R.I[b]; tau[b] = R.tau[b]; }
+    const float ds = L.ds, scale = L.scale;
+    const int n1 = L.n1, n2 = L.n2;
+    auto kappa_cell = [&](const Axis& a0, const Axis& a1, const Axis& a2, float px, float py, float pz) {
+        return L.kappa_mode == 0 ? (a0.lo * n1 + a1.lo) * n2 + a2.lo
+                                 : (nearest_round(px, L.n0) * n1 + nearest_round(py, n1)) * n2 + nearest_round(pz, n2);
+    };
+
+    // the current corner set (x_k): per-axis samples, slot roles P_a, slot cells, j and sums
+    Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, n1), a2 = axis_sample(z, n2);
+    int P0 = 0, P1 = 0, P2 = 0;
+    int pc[8];
+    float pend[8][W];
+    Vec<W> gj[8];
+    {
+        const int r00 = (a0.lo * n1 + a1.lo) * n2, r01 = (a0.lo * n1 + a1.hi) * n2;
+        const int r10 = (a0.hi * n1 + a1.lo) * n2, r11 = (a0.hi * n1 + a1.hi) * n2;
+        const int cell[8] = {r00 + a2.lo, r00 + a2.hi, r01 + a2.lo, r01 + a2.hi,
+                             r10 + a2.lo, r10 + a2.hi, r11 + a2.lo, r11 + a2.hi};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            pc[c] = cell[c];
+            gj[c] = ldg_vec<W>(jg, cell[c]);
+#pragma unroll
+            for (int b = 0; b < W; ++b) pend[c][b] = 0.0f;
+        }
+    }
+    int gnn = kappa_cell(a0, a1, a2, x, y, z);
+    Vec<W> gk = ldg_vec<W>(kg, gnn);
+
+    int ck_left = 0;     // REC: substeps until the next checkpoint
+    float* ckp = L.ck;   // REC: this lane's next checkpoint
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        if (REC) {
+            if (ck_left == 0) {
+                ckp[0] = x; ckp[L.ck_lanes] = y; ckp[2 * L.ck_lanes] = z;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    ckp[(3 + b) * L.ck_lanes] = I[b];
+                    ckp[(3 + W + b) * L.ck_lanes] = tau[b];
+                }
+                ckp += (3 + 2 * W) * L.ck_lanes;
+                ck_left = L.ck_stride;
+            }
+            --ck_left;
+        }
+        // ---- x_{k+1}, its corner set and the slots that change (nothing changes after the last) ----
+        const float xn = __fadd_rn(x, dx), yn = __fadd_rn(y, dy), zn = __fadd_rn(z, dz);   // Eq. 2: x_{k+1}
+        const Axis b0 = axis_sample(xn, L.n0), b1 = axis_sample(yn, n1), b2 = axis_sample(zn, n2);
+        const bool more = k + 1 < L.ns;
+        const bool same0 = b0.lo == a0.lo && b0.hi == a0.hi, same1 = b1.lo == a1.lo && b1.hi == a1.hi,
+                   same2 = b2.lo == a2.lo && b2.hi == a2.hi;
+        const bool up0 = !same0 && b0.lo == a0.hi, up1 = !same1 && b1.lo == a1.hi, up2 = !same2 && b2.lo == a2.hi;
+        const bool dn0 = !same0 && !up0 && b0.hi == a0.lo, dn1 = !same1 && !up1 && b1.hi == a1.lo,
+                   dn2 = !same2 && !up2 && b2.hi == a2.lo;
+        const bool other = !(same0 || up0 || dn0) || !(same1 || up1 || dn1) || !(same2 || up2 || dn2);
+        const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
+        const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
+        unsigned mask = other ? 0xFFu : 0u;   // leaving slots, as in march_lane_slots
+        mask |= sh0 ? (q0 ? 0xF0u : 0x0Fu) : 0u;
+        mask |= sh1 ? (q1 ? 0xCCu : 0x33u) : 0u;
+        mask |= sh2 ? (q2 ? 0xAAu : 0x55u) : 0u;
+        if (!more) mask = 0u;
+        const int Q0 = P0 ^ (sh0 ? 1 : 0), Q1 = P1 ^ (sh1 ? 1 : 0), Q2 = P2 ^ (sh2 ? 1 : 0);   // roles at k+1
+
+        // ---- substep k with the current slots (weights of x_k in slot order) ----
+        const float u0 = 1.0f - a0.t, u1 = 1.0f - a1.t, u2 = 1.0f - a2.t;
+        const float f00 = P0 ? a0.t : u0, f01 = P0 ? u0 : a0.t;
+        const float f10 = P1 ? a1.t : u1, f11 = P1 ? u1 : a1.t;
+        const float f20 = P2 ? a2.t : u2, f21 = P2 ? u2 : a2.t;
+        float w[8];
+        {
+            const float w00 = f00 * f10, w01 = f00 * f11, w10 = f01 * f10, w11 = f01 * f11;
+            w[0] = w00 * f20; w[1] = w00 * f21; w[2] = w01 * f20; w[3] = w01 * f21;
+            w[4] = w10 * f20; w[5] = w10 * f21; w[6] = w11 * f20; w[7] = w11 * f21;
+        }
+        // trilinear sum of j(x_k) over the current slots
+        float jk[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) jk[b] = 0.0f;
+        if constexpr (W % 2 == 0) {
+#pragma unroll
+            for (int h = 0; h < W; h += 2) {
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    acc = __ffma2_rn(make_float2(w[c], w[c]), make_float2(gj[c].v[h], gj[c].v[h + 1]), acc);
+                jk[h] = acc.x; jk[h + 1] = acc.y;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) jk[b] = fmaf(w[c], gj[c].v[b], jk[b]);
+            }
+        }
+        // the slots are read: gather the corners that enter at k+1 into the slots they replace
+        // (slot bit 0 along axis a is Q_a ? hi : lo at k+1)
+        const int e00 = Q0 ? b0.hi : b0.lo, e01 = Q0 ? b0.lo : b0.hi;
+        const int e10 = Q1 ? b1.hi : b1.lo, e11 = Q1 ? b1.lo : b1.hi;
+        const int e20 = Q2 ? b2.hi : b2.lo, e21 = Q2 ? b2.lo : b2.hi;
+        const int s00 = (e00 * n1 + e10) * n2, s01 = (e00 * n1 + e11) * n2;
+        const int s10 = (e01 * n1 + e10) * n2, s11 = (e01 * n1 + e11) * n2;
+        const int ncell[8] = {s00 + e20, s00 + e21, s01 + e20, s01 + e21, s10 + e20, s10 + e21, s11 + e20, s11 + e21};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if ((mask >> c) & 1u) gj[c] = ldg_vec<W>(jg, ncell[c]);
+        // Eq. 2 with kappa(x_k); then kappa(x_{k+1}) is gathered
+        float dep[W];
+        if constexpr (W % 2 == 0) {
+#pragma unroll
+            for (int h = 0; h < W; h += 2) {
+                const float2 kds = __fmul2_rn(make_float2(gk.v[h], gk.v[h + 1]), make_float2(ds, ds));
+                const float2 att = make_float2(neg_exp(kds.x), neg_exp(kds.y));       // exp(-kappa(x_k) ds)
+                const float2 em = make_float2(neg_exp(tau[h]), neg_exp(tau[h + 1]));  // exp(-tau_k)
+                const float2 e = __fmul2_rn(__fmul2_rn(make_float2(jk[h], jk[h + 1]), em), make_float2(ds, ds));
+                const float2 In = __ffma2_rn(make_float2(I[h], I[h + 1]), att, e);    // Eq. 2: I_{k+1}
+                const float2 tn = __fadd2_rn(make_float2(tau[h], tau[h + 1]), kds);   // Eq. 2: tau_{k+1}
+                const float2 d = __fmul2_rn(In, make_float2(scale, scale));
+                I[h] = In.x; I[h + 1] = In.y;
+                tau[h] = tn.x; tau[h + 1] = tn.y;
+                dep[h] = d.x; dep[h + 1] = d.y;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float kds = gk.v[b] * ds;
+                const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
+                const float em = neg_exp(tau[b]);             // exp(-tau_k)
+                I[b] = fmaf(I[b], att, jk[b] * em * ds);      // Eq. 2: I_{k+1}
+                tau[b] += kds;                                // Eq. 2: tau_{k+1}
+                dep[b] = I[b] * scale;
+            }
+        }
+        const int nnn = kappa_cell(b0, b1, b2, xn, yn, zn);
+        if (more && nnn != gnn) gk = ldg_vec<W>(kg, nnn);
+        gnn = nnn;
+        // deposits of substep k into the current slots
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if constexpr (W % 2 == 0) {
+#pragma unroll
+                for (int h = 0; h < W; h += 2) {
+                    const float2 v = __ffma2_rn(make_float2(w[c], w[c]), make_float2(dep[h], dep[h + 1]),
+                                                make_float2(pend[c][h], pend[c][h + 1]));
+                    pend[c][h] = v.x; pend[c][h + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[c][b] = fmaf(w[c], dep[b], pend[c][b]);
+            }
+        }
+
+        // ---- the slots that leave at k+1: flush their sums (this substep included) and start the
+        // entering corners' sums from zero ----
+        if (mask) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const bool f = (mask >> c) & 1u;
+                flush_if<W, DET>(f, L, pc[c], pend[c]);
+                if constexpr (W % 2 == 0) {
+                    const float keep = f ? 0.0f : 1.0f;
+#pragma unroll
+                    for (int h = 0; h < W; h += 2) {
+                        const float2 v = __fmul2_rn(make_float2(pend[c][h], pend[c][h + 1]), make_float2(keep, keep));
+                        pend[c][h] = v.x; pend[c][h + 1] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < W; ++b) pend[c][b] = f ? 0.0f : pend[c][b];
+                }
+                pc[c] = f ? ncell[c] : pc[c];
+            }
+        }
+        P0 = Q0; P1 = Q1; P2 = Q2;
+        a0 = b0; a1 = b1; a2 = b2;
+        x = xn; y = yn; z = zn;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) flush<W, DET>(L, pc[c], pend[c]);
+    R.x = x; R.y = y; R.z = z;
+#pragma unroll
+    for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
+}
+
 // Gathers modes 1 and 3, the corner set as one unit: deposits are merged in registers while the
 // set is unchanged and all eight corners are flushed when it changes. AHEAD (mode 1): the gathers
 // of substep k+1 are issued before the update of substep k, every substep. Otherwise (mode 3)
@@ -690,11 +892,12 @@ __device__ __forceinline__ void march_lane_pair(const Lane& L, int sub, unsigned
         if (pc[i] >= 0) flush<W, DET>(L, pc[i], pend[i]);
 }
 
-// Gathers modes: PF = 0 march_lane_slots, 1 and 3 march_lane_runs, 2 march_lane_ahead. REC
-// (checkpoints) is available with modes 0, 1 and 3.
+// Gathers modes: PF = 0 march_lane_slots, 1 and 3 march_lane_runs, 2 march_lane_ahead, 4
+// march_lane_slots_ahead (no tiles). REC (checkpoints) is available with modes 0, 1, 3 and 4.
 template <int W, int PF, int DET = 0, bool TILE = false, bool REC = false>
 __device__ __forceinline__ void march_lane(const Lane& L, RayState<W>& R) {
-    if (PF == 2) march_lane_ahead<W, DET, TILE>(L, R);
+    if (PF == 4) march_lane_slots_ahead<W, DET, REC>(L, R);
+    else if (PF == 2) march_lane_ahead<W, DET, TILE>(L, R);
     else if (PF == 0) march_lane_slots<W, DET, TILE, REC>(L, R);
     else march_lane_runs<W, PF == 1, DET, TILE, REC>(L, R);
 }

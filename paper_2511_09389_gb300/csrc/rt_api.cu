@@ -261,7 +261,7 @@ int num_substeps(float ds, float c, float dt, int cap) { return rt::substeps(ds,
 }  // namespace
 
 // Widths W in {the default, 2, 1} that fit n_freq; 32, 64, 128, 256 threads per block; gather
-// modes 0, 1, 2, 3 with and without source tiles, and mode 0 with two lanes per ray.
+// modes 0, 1, 2, 3 with and without source tiles, mode 0 with two lanes per ray, and mode 4.
 int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int widths[3], nw = 0;
     widths[nw++] = n_freq == 1 ? 1 : (n_freq == 2 ? 2 : 4);
@@ -270,11 +270,11 @@ int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int n = 0;
     for (int wi = 0; wi < nw; ++wi)
         for (int b : {32, 64, 128, 256})
-            for (int cand = 0; cand < 9; ++cand) {
+            for (int cand = 0; cand < 10; ++cand) {
                 MarchPlan p;
                 p.W = widths[wi];
                 p.block = b;
-                p.prefetch = cand < 8 ? cand >> 1 : 0;
+                p.prefetch = cand < 8 ? cand >> 1 : (cand == 8 ? 0 : 4);
                 p.tile = cand < 8 ? (cand & 1) : 0;
                 p.lpr = cand == 8 ? 2 : 1;
                 out[n++] = p;
@@ -515,7 +515,7 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
             g->last_plan_ms = e.second.second;
             return RT_OK;
         }
-    rt::MarchPlan cands[108];
+    rt::MarchPlan cands[rt::kMaxMarchPlans];
     const int n_cand = rt::march_plan_candidates(a.n_freq, cands);
     cudaEvent_t e[2] = {nullptr, nullptr};
     float best_ms = 3.0e38f;
@@ -536,7 +536,7 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
         if (p.lpr == 1 && p.tile && g->opt.accumulation == 0 && auto_accumulation(g, a, ns) != 0) continue;
         const int acc = acc_mode_for(g, p, a, ns);
         if (acc != 0 && p.lpr == 1 && p.tile) continue;
-        if (!rt::march_fwd_available(W, p.prefetch, acc, p.tile, 0, p.lpr)) continue;
+        if (!rt::march_fwd_available(W, p.prefetch, acc, p.tile, 0, p.lpr, p.block)) continue;
         rt::MarchArgs m;
         if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
         float cand_ms = 3.0e38f;
@@ -611,29 +611,31 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     const float scale = (float)(4.0 * 3.14159265358979323846 / (double)a.num_rays);
 
     // default plan (measured on GB300): 32-thread blocks. Summing in FP32: gather prefetch and
-    // source deposit tiles for one bin per thread, neither for wider groups (a tiled 4-bin deposit
-    // is 32 shared-memory atomics). Summing in 8-byte words (no tiles): corner slots, and for one
-    // bin two lanes per ray while the call has too few lanes to fill the GPU (twice as fast on 64^3
-    // with 8 sources, slower on 2,097 sources)
+    // source deposit tiles for one bin per thread, corner slots with the gathers a substep ahead
+    // (gathers mode 4) for wider groups (a tiled 4-bin deposit is 32 shared-memory atomics).
+    // Summing in 8-byte words (no tiles): gathers mode 4, or for one bin two lanes per ray while the
+    // call has too few lanes to fill the GPU (twice as fast on 64^3 with 8 sources, slower on 2,097
+    // sources)
     const bool det = g->opt.deterministic != 0;
     Plan plan;
     plan.W = pick_width(a.n_freq);
     plan.block = 32;
-    plan.prefetch = plan.W == 1 ? 1 : 0;
+    plan.prefetch = plan.W == 1 ? 1 : 4;
     if (g->opt.plan_width) plan.W = g->opt.plan_width;
     plan.tile = plan.W == 1 ? 1 : 0;
+    if (plan.W > 1) plan.prefetch = 4;
     {
         Plan untiled = plan;
         untiled.tile = 0;
         if (acc_mode_for(g, untiled, a, ns) != 0) {
             const double lanes = (double)a.nsrc * (a.ray_end - a.ray_begin) * ((a.n_freq + plan.W - 1) / plan.W);
-            plan.prefetch = 0;
             plan.tile = 0;
             plan.lpr = plan.W == 1 && lanes < 152.0 * 1024.0 ? 2 : 1;
+            plan.prefetch = plan.lpr == 2 ? 0 : 4;
         }
     }
     if (det) {   // deterministic mode: corner slots, one lane per ray (validated at creation)
-        plan.prefetch = 0;
+        plan.prefetch = 4;
         plan.tile = 0;
         plan.lpr = 1;
         plan.block = 32;
@@ -672,10 +674,10 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     // a plan that this accumulation has no kernel for falls back to corner slots (every mode has
     // them); recording stays off where no recording kernel exists (the reverse march then makes
     // its own forward sweep)
-    if (!rt::march_fwd_available(plan.W, plan.prefetch, acc, plan.tile, record, plan.lpr)) {
+    if (!rt::march_fwd_available(plan.W, plan.prefetch, acc, plan.tile, record, plan.lpr, plan.block)) {
         plan.prefetch = 0;
-        if (!rt::march_fwd_available(plan.W, 0, acc, plan.tile, record, plan.lpr)) plan.lpr = 1;
-        if (record && !rt::march_fwd_available(plan.W, 0, acc, plan.tile, 1, plan.lpr)) record = false;
+        if (!rt::march_fwd_available(plan.W, 0, acc, plan.tile, record, plan.lpr, plan.block)) plan.lpr = 1;
+        if (record && !rt::march_fwd_available(plan.W, 0, acc, plan.tile, 1, plan.lpr, plan.block)) record = false;
     }
     g->last_plan = plan;
     g->last_acc = acc;
@@ -745,7 +747,7 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
         return fail(RT_ERR_INVALID_ARG, "plan_width must be 0, 1, 2 or 4");
     if (o.plan_block != 0 && (o.plan_block < 32 || o.plan_block > 256 || o.plan_block % 32))
         return fail(RT_ERR_INVALID_ARG, "plan_block must be 0 or a multiple of 32 in [32, 256]");
-    if (o.plan_prefetch < 0 || o.plan_prefetch > 4) return fail(RT_ERR_INVALID_ARG, "plan_prefetch must be 0 .. 4");
+    if (o.plan_prefetch < 0 || o.plan_prefetch > 5) return fail(RT_ERR_INVALID_ARG, "plan_prefetch must be 0 .. 5");
     if (o.plan_lanes != 0 && o.plan_lanes != 1 && o.plan_lanes != 2)
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 0, 1 or 2");
     if (o.plan_tile < 0 || o.plan_tile > 2) return fail(RT_ERR_INVALID_ARG, "plan_tile must be 0, 1 or 2");
@@ -753,9 +755,9 @@ rt_status rt_create_grid(rt_grid** out, int n0, int n1, int n2, int max_freq, co
         return fail(RT_ERR_INVALID_ARG, "accumulation must be 0, 1, 2 or 3");
     // the fixed-point march runs one lane per ray with corner slots and no tiles: a pinned plan
     // asking for anything else would be accepted here and then silently not used
-    if (o.deterministic && (o.plan_lanes == 2 || o.plan_tile == 2 || o.plan_prefetch > 1))
+    if (o.deterministic && (o.plan_lanes == 2 || o.plan_tile == 2 || (o.plan_prefetch > 1 && o.plan_prefetch != 5)))
         return fail(RT_ERR_INVALID_ARG, "deterministic mode marches with plan_lanes 1, plan_tile 1 (off) and "
-                                        "plan_prefetch 1 (corner slots) only");
+                                        "plan_prefetch 1 or 5 (corner slots, gathered in time or ahead) only");
     rt_grid* g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ERR_OOM, "host allocation failed");
     g->n0 = n0; g->n1 = n1; g->n2 = n2; g->max_freq = max_freq;

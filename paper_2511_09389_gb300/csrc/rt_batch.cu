@@ -181,7 +181,7 @@ struct rt_batch {
     rt_status tune_dedicated(Dedicated& d, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
         const rt::BatchInst& b = host[d.inst];
         const size_t accb = sizeof(float) * (size_t)b.groups * b.n0 * b.n1 * b.n2 * b.W;
-        rt::MarchPlan cands[108];
+        rt::MarchPlan cands[rt::kMaxMarchPlans];
         const int n = rt::march_plan_candidates(b.n_freq, cands);
         float best = 3.0e38f;
         Dedicated win = d;
@@ -190,7 +190,7 @@ struct rt_batch {
             Dedicated c = d;
             c.W = cands[ci].W; c.block = cands[ci].block; c.prefetch = cands[ci].prefetch;
             c.tile = cands[ci].tile; c.lpr = cands[ci].lpr;
-            if (c.W > b.W) continue;
+            if (c.W > b.W || !rt::march_fwd_available(c.W, c.prefetch, 0, c.tile, 0, c.lpr, c.block)) continue;
             if (c.W != packed_w) {
                 rt_status rs = pack_dedicated(c, st);
                 if (rs != RT_OK) return rs;

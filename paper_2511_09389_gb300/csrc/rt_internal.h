@@ -44,7 +44,8 @@ struct MarchArgs {
     int prefetch;           // gathers mode. 0: corner slots (a face shared by consecutive corner
                             // sets keeps its gathers and sums); 1: the next substep's gathers
                             // issued before the current update; 2: both; 3: the whole corner set
-                            // reused while unchanged, flushed and re-gathered when it changes
+                            // reused while unchanged, flushed and re-gathered when it changes;
+                            // 4: corner slots with the entering corners gathered a substep early
     int lanes_per_ray;      // 1, or 2 adjacent lanes sharing a ray (each with half of its corner slots)
     int tile;               // 1: source deposit tiles in shared memory (FP32 mode, one lane per ray)
     // stateful advance (NULL st_I: none): st_I / st_tau [n_freq][nsrc][ray_count], positions
@@ -62,8 +63,9 @@ struct MarchArgs {
 
 cudaError_t launch_march_fwd(int W, const MarchArgs& a, cudaStream_t st);
 // Whether a forward kernel is compiled for this plan and accumulation (acc_mode as in MarchArgs;
-// record: with adjoint checkpoints). launch_march_fwd returns cudaErrorInvalidValue otherwise.
-bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray);
+// record: with adjoint checkpoints) and accepts this block size. launch_march_fwd returns
+// cudaErrorInvalidValue otherwise.
+bool march_fwd_available(int W, int prefetch, int acc_mode, int tile, int record, int lanes_per_ray, int block);
 
 // A forward launch plan: bins per thread W, threads per block, gather mode (MarchArgs::prefetch),
 // lanes per ray, source tiles.
@@ -71,7 +73,8 @@ struct MarchPlan {
     int W, block, prefetch, lpr, tile;
 };
 // The plans the autotuners time for n_freq bins (rt_api.cu for single calls, rt_batch.cu for the
-// batch's dedicated instances), at most 108; returns how many were written to out.
+// batch's dedicated instances), at most kMaxMarchPlans; returns how many were written to out.
+constexpr int kMaxMarchPlans = 120;
 int march_plan_candidates(int n_freq, MarchPlan* out);
 
 // [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).

@@ -67,7 +67,7 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 
 @pytest.mark.parametrize("field,value,word", [("plan_lanes", 4, b"plan_lanes"), ("plan_lanes", 3, b"plan_lanes"),
-                                              ("plan_prefetch", 5, b"plan_prefetch"), ("plan_width", 3, b"plan_width"),
+                                              ("plan_prefetch", 6, b"plan_prefetch"), ("plan_width", 3, b"plan_width"),
                                               ("plan_block", 48, b"plan_block"), ("plan_tile", 3, b"plan_tile"),
                                               ("kappa_mode", 2, b"kappa_mode"), ("ckpt_stride", -1, b"ckpt_stride")])
 def test_bad_options_rejected_at_creation(lib, field, value, word):
@@ -84,7 +84,7 @@ def test_bad_options_rejected_at_creation(lib, field, value, word):
 
 
 @pytest.mark.parametrize("field,value", [("plan_lanes", 2), ("plan_tile", 2), ("plan_prefetch", 2),
-                                         ("plan_prefetch", 4)])
+                                         ("plan_prefetch", 4), ("plan_prefetch", 3)])
 def test_deterministic_rejects_plans_it_cannot_run(lib, field, value):
     """The fixed-point march runs one lane per ray with corner slots and no tiles: a pinned plan
     asking for two lanes, tiles or another gathers mode is refused at creation, naming the mode,

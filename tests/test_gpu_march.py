@@ -188,14 +188,14 @@ def test_invalid_arguments_raise(torch_cuda):
 
 def test_deterministic_mode_parity_and_bitwise_reproducible(torch_cuda):
     """Fixed-point accumulation: the field meets the same bar against the oracle and is bitwise
-    identical across runs and across launch plans (bins per thread, block size), i.e. for any
-    order in which the deposits arrive."""
+    identical across runs and across launch plans (bins per thread, block size, corner slots
+    gathered in time or a substep ahead), i.e. for any order in which the deposits arrive."""
     torch = torch_cuda
     from paper_2511_09389_gb300.api import Grid
     p = inputs.random_small(51, shape=(20, 16, 24), n_freq=5, n_src=4, num_rays=300, horizon=18.0)
     j, k, s = (torch.from_numpy(a).cuda() for a in (p.j, p.kappa, p.sources))
     outs = []
-    for plan in [(4, 32, 0), (4, 32, 0), (1, 64, 0), (2, 128, 0), (4, 256, 0)]:
+    for plan in [(4, 32, 0), (4, 32, 0), (1, 64, 0), (2, 128, 0), (4, 256, 0), (4, 32, 4), (1, 64, 4), (2, 32, 4)]:
         g = Grid(p.shape, 8, deterministic=True, plan=plan)
         outs.append(g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy())
         g.close()
@@ -221,7 +221,8 @@ def test_deterministic_mode_full_size(torch_cuda):
 @pytest.mark.parametrize("plan", [(4, 64, 0, 2), (1, 128, 0, 2), (2, 32, 0, 2), (4, 32, 0, 2), (4, 256, 1, 1), (2, 64, 1, 1), (4, 32, 2, 1), (1, 64, 2, 1),
                                   (1, 32, 0, 1), (4, 32, 0, 1, 1), (2, 128, 1, 1, 1), (1, 64, 1, 1, 1),
                                   (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0), (4, 32, 3, 1),
-                                  (2, 64, 3, 1, 0), (1, 64, 3, 1, 1), (4, 64, 3, 1, 1)])
+                                  (2, 64, 3, 1, 0), (1, 64, 3, 1, 1), (4, 64, 3, 1, 1),
+                                  (4, 32, 4, 1), (2, 64, 4, 1), (1, 128, 4, 1)])
 def test_every_launch_plan_meets_parity(torch_cuda, plan):
     """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray,
     source deposit tiles) on a ragged multi-bin problem."""
@@ -254,7 +255,8 @@ def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
 
 
 @pytest.mark.parametrize("step_size", [0.13, 0.5, 1.0, 1.7, 3.2])
-@pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3), (4, 32, 0, 2), (1, 64, 0, 2)])
+@pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3), (4, 32, 0, 2), (1, 64, 0, 2),
+                                  (4, 32, 4), (1, 64, 4), (2, 32, 4)])
 def test_corner_slots_across_step_sizes(torch_cuda, plan, step_size):
     """Gathers mode 0 keeps a face shared by consecutive corner sets (a step of one cell along an
     axis) and flushes everything else. Steps much shorter than a cell (long runs in one set), of
@@ -324,3 +326,18 @@ def test_one_bin_sums_on_clustered_sources(torch_cuda):
     e = [np.linalg.norm(X - R) / np.linalg.norm(R) for X in (F, F64, F32)]
     print(f"300 clustered sources: rel-L2 fixed point {e[0]:.2e}, FP64 {e[1]:.2e}, FP32 {e[2]:.2e}")
     assert max(e[0], e[1]) <= e[2]
+
+
+@pytest.mark.parametrize("width,shape,step_size", [(1, (17, 13, 21), 0.5), (4, (17, 13, 21), 0.5), (1, (9, 1, 12), 1.7),
+                                                   (4, (14, 11, 17), 0.13), (2, (14, 11, 17), 3.2)])
+def test_gathers_ahead_sums_equal_corner_slots(torch_cuda, width, shape, step_size):
+    """Gathers mode 4 is the corner slots of mode 0 with the entering corners gathered one substep
+    early: the same sums flushed at the same points. Summed in fixed point (order-independent),
+    the two fields are bitwise equal; and both meet the oracle."""
+    from paper_2511_09389_gb300.api import Grid
+    nf = 1 if width == 1 else 5
+    p = inputs.random_small(95, shape=shape, n_freq=nf, n_src=4, num_rays=199, step_size=step_size, horizon=14.0)
+    F = [run_gpu(torch_cuda, p, grid=Grid(p.shape, 8, plan=(width, 32, mode, 1), accumulation="fixed"))
+         for mode in (0, 4)]
+    assert np.array_equal(F[0].view(np.uint32), F[1].view(np.uint32))
+    assert_parity(F[1], run_oracle(p))
