@@ -504,12 +504,14 @@ __device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W
         const float xn = __fadd_rn(x, dx), yn = __fadd_rn(y, dy), zn = __fadd_rn(z, dz);   // Eq. 2: x_{k+1}
         const Axis b0 = axis_sample(xn, L.n0), b1 = axis_sample(yn, n1), b2 = axis_sample(zn, n2);
         const bool more = k + 1 < L.ns;
-        const bool same0 = b0.lo == a0.lo && b0.hi == a0.hi, same1 = b1.lo == a1.lo && b1.hi == a1.hi,
-                   same2 = b2.lo == a2.lo && b2.hi == a2.hi;
-        const bool up0 = !same0 && b0.lo == a0.hi, up1 = !same1 && b1.lo == a1.hi, up2 = !same2 && b2.lo == a2.hi;
-        const bool dn0 = !same0 && !up0 && b0.hi == a0.lo, dn1 = !same1 && !up1 && b1.hi == a1.lo,
-                   dn2 = !same2 && !up2 && b2.hi == a2.lo;
-        const bool other = !(same0 || up0 || dn0) || !(same1 || up1 || dn1) || !(same2 || up2 || dn2);
+        // The pair (lo, hi) = (max(f, 0), min(f + 1, n - 1)) of an axis with n >= 2 cells is a
+        // one-to-one function of the clamped floor f in [-1, n - 1], and f -> f + 1 makes the old hi
+        // the new lo (up), f -> f - 1 the old lo the new hi (down); a single-cell axis keeps (0, 0).
+        // So the change of f classifies each axis as march_lane_slots does from the pairs.
+        const int d0 = L.n0 > 1 ? b0.f - a0.f : 0, d1 = n1 > 1 ? b1.f - a1.f : 0, d2 = n2 > 1 ? b2.f - a2.f : 0;
+        const bool up0 = d0 == 1, up1 = d1 == 1, up2 = d2 == 1;
+        const bool dn0 = d0 == -1, dn1 = d1 == -1, dn2 = d2 == -1;
+        const bool other = (unsigned)(d0 + 1) > 2u || (unsigned)(d1 + 1) > 2u || (unsigned)(d2 + 1) > 2u;
         const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
         const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
         unsigned mask = other ? 0xFFu : 0u;   // leaving slots, as in march_lane_slots
