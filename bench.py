@@ -229,7 +229,7 @@ def fwd_adjoint(args, dev, flush, stream):
     from paper_2511_09389_gb300.api import Grid, num_substeps
     p = inputs.inverse_problem()
     U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
-    g = Grid(p.shape, 1, profile=True, record_checkpoints=True)
+    g = Grid(p.shape, 1, profile=True, record_checkpoints=True, autotune=True)
     j, k, s = (torch.from_numpy(a).to(dev) for a in (p.j, p.kappa, p.sources))
     G = torch.randn(p.j.shape, device=dev)
     out = torch.empty_like(j)
@@ -249,13 +249,28 @@ def fwd_adjoint(args, dev, flush, stream):
             bwd.append(e[1].elapsed_time(e[2]))
             kf.append(kfwd)
             kb.append(g.kernel_ms())
+    stride = g.last_ckpt_stride()
+    plan = g.last_plan()
+    # the config-4 inversion: j recovered from zero by Adam (lr 1e-2, 200 iterations, projected
+    # onto j >= 0) on the MSE of the log field, through the differentiable march
+    from paper_2511_09389_gb300 import inversion
+    target = g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step)
+    inv = inversion.recover_emissivity(target, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step,
+                                       iterations=200, lr=1e-2, grid=g)
     g.close()
     tf, tb = st.mean(fwd), st.mean(bwd)
     return {"value": U / ((tf + tb) * 1e-3), "unit": "updates/s", "updates_per_step": U,
             "workload": "inverse problem: lognormal kappa 64^3, 8 sources, N_Omega 3072, ds 0.5, N_s 128, 1 bin",
             "checkpoints": "recorded by the forward march, reused by the reverse march (record_checkpoints)",
+            "ckpt_stride": stride, "forward_plan": plan,
             "ms_fwd": tf, "ms_bwd": tb, "fwd_kernel_ms": st.mean(kf), "adjoint_kernel_ms": st.mean(kb),
-            "adjoint_updates_per_s": U / (tb * 1e-3)}
+            "adjoint_updates_per_s": U / (tb * 1e-3),
+            "inversion": {"iterations": inv["iterations"], "lr": 1e-2, "wall_s": inv["wall_s"],
+                          "ms_per_iteration": 1e3 * inv["wall_s"] / inv["iterations"],
+                          "loss_first": inv["losses"][0], "loss_last": inv["losses"][-1],
+                          "correlation_with_target_j": inversion.correlation(inv["j"], j),
+                          "loss": "mean (log(F + 1e-2 max F_t) - log(F_t + 1e-2 max F_t))^2",
+                          "optimiser": "Adam (rt_adam_step), projected onto j >= 0, j = 0 at the start"}}
 
 
 def paper_workload(args, dev, flush, stream):

@@ -68,7 +68,11 @@ typedef struct {
     int kappa_mode;     /* 0: floor cell of x_k (default); 1: round-to-nearest cell */
     int ns_cap;         /* 0: none; > 0: cap on the substep count (the optional cap of Sec. 2) */
     int autotune;       /* 1: time the launch shapes once per shape class and keep the best */
-    int ckpt_stride;    /* adjoint checkpoint stride K in substeps; 0: automatic */
+    int ckpt_stride;    /* adjoint checkpoint stride K in substeps, rounded to 4, 8, 16 or 32;
+                           0: automatic -- with autotune = 1 the first rt_backward* of each shape
+                           class (n_freq, sources, rays, N_s) times the reverse march for every K
+                           on its own inputs (synchronising the stream) and keeps the fastest for
+                           that class, its recordings included; otherwise 16 */
     int profile;        /* 1: bracket the march kernel of each call with CUDA events on the
                            call's stream, readable with rt_kernel_ms */
     /* Forward launch plan, used when autotune = 0; 0 in a field means that field's default.
@@ -453,6 +457,10 @@ rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int e
    times every candidate plan on its own inputs before running; it synchronises the stream. */
 rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray, int* tile,
                        float* tuned_ms);
+
+/* Checkpoint stride K of the last rt_backward* on this handle, and the reverse-march time in ms
+   the stride tuner measured for it (-1 when it was not tuned). Either pointer may be NULL. */
+rt_status rt_last_ckpt_stride(rt_grid* grid, int* stride, float* tuned_ms);
 
 /* Accumulation of the last forward call on this handle: *mode = 1 FP32 reductions, 2 FP64
    reductions, 3 64-bit fixed point (deterministic mode). */

@@ -276,6 +276,12 @@ class Grid:
         return {"width": w.value, "block": b.value, "prefetch": p.value, "lanes_per_ray": n.value, "tile": tl.value,
                 "tuned_ms": t.value}
 
+    def last_ckpt_stride(self) -> dict:
+        """Checkpoint stride K of the last backward call and its tuned reverse-march ms (-1: not tuned)."""
+        k, t = ctypes.c_int(), ctypes.c_float()
+        check(self._lib.rt_last_ckpt_stride(self._h, ctypes.byref(k), ctypes.byref(t)))
+        return {"stride": k.value, "tuned_ms": t.value}
+
     def last_accumulation(self) -> str:
         """How the last forward call summed its deposits: "fp32", "fp64" or "fixed" (deterministic)."""
         m = ctypes.c_int()
@@ -377,6 +383,18 @@ def _cached_grid(shape, n_freq, device, **opts) -> Grid:
     return g
 
 
+def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    """One bias-corrected Adam step (rt_adam_step) on float32 CUDA tensors of one size, in place."""
+    for t in (params, grads, m, v):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == params.numel()):
+            raise ValueError("adam_step needs contiguous float32 CUDA tensors of one size")
+    with torch.cuda.device(params.device):
+        check(_native.load().rt_adam_step(params.data_ptr(), grads.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                          params.numel(), float(lr), float(beta1), float(beta2), float(eps),
+                                          int(step), _stream_ptr(stream, params.device)))
+
+
 def advance(j, kappa, sources, num_rays: int, step_size: float, radiation_velocity: float = 1.0,
             time_step: float = 1.0, **opts) -> torch.Tensor:
     """Functional form of :meth:`Grid.advance` with a cached handle per (shape, device, options)."""
@@ -386,4 +404,4 @@ def advance(j, kappa, sources, num_rays: int, step_size: float, radiation_veloci
     return out if j.dim() == 4 else out[0]
 
 
-__all__ = ["Grid", "Batch", "advance", "num_substeps", "direction_table", "RTError"]
+__all__ = ["Grid", "Batch", "advance", "adam_step", "num_substeps", "direction_table", "RTError"]

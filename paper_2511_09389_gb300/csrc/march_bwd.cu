@@ -287,9 +287,9 @@ cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st) {
 #define RT_BWD_CASE(W_, K_)                                                                        \
         case (W_ * 100 + K_) * 2: k_march_bwd<W_, K_, false><<<grid, block, 0, st>>>(a); break;    \
         case (W_ * 100 + K_) * 2 + 1: k_march_bwd<W_, K_, true><<<grid, block, 0, st>>>(a); break;
-        RT_BWD_CASE(1, 8) RT_BWD_CASE(1, 16) RT_BWD_CASE(1, 32)
-        RT_BWD_CASE(2, 8) RT_BWD_CASE(2, 16) RT_BWD_CASE(2, 32)
-        RT_BWD_CASE(4, 8) RT_BWD_CASE(4, 16) RT_BWD_CASE(4, 32)
+        RT_BWD_CASE(1, 4) RT_BWD_CASE(1, 8) RT_BWD_CASE(1, 16) RT_BWD_CASE(1, 32)
+        RT_BWD_CASE(2, 4) RT_BWD_CASE(2, 8) RT_BWD_CASE(2, 16) RT_BWD_CASE(2, 32)
+        RT_BWD_CASE(4, 4) RT_BWD_CASE(4, 8) RT_BWD_CASE(4, 16) RT_BWD_CASE(4, 32)
 #undef RT_BWD_CASE
         default: return cudaErrorInvalidValue;
     }

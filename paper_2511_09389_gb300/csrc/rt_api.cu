@@ -148,6 +148,10 @@ struct rt_grid {
         }
     };
     std::vector<std::pair<TuneKey, std::pair<Plan, float>>> tuned;
+    // checkpoint strides picked by the reverse-march tuner: shape class -> (K, adjoint ms)
+    std::vector<std::pair<TuneKey, std::pair<int, float>>> tuned_k;
+    int last_k = 0;            // stride of the last reverse march
+    float last_k_ms = -1.0f;   // its tuned adjoint time (-1: not tuned)
     Plan last_plan;
     int last_acc = 0;          // accumulation of the last forward call (MarchArgs::acc_mode)
     bool dets_zeroed = false;  // the fixed-point reduction words of the DETS slot are zero
@@ -495,9 +499,18 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
 }
 
 // Adjoint checkpoint stride: the option, rounded to a supported value; automatic = 16.
-int ckpt_stride(const rt_grid* g) {
-    const int want = g->opt.ckpt_stride > 0 ? g->opt.ckpt_stride : 16;
-    return want <= 11 ? 8 : (want <= 23 ? 16 : 32);
+// Adjoint checkpoint stride K in {4, 8, 16, 32}: the option rounded to the nearest supported
+// value; automatic: the stride the reverse-march tuner picked for this shape class (n_freq,
+// sources, rays, N_s) when the handle autotunes and has tuned it, else 16.
+int ckpt_stride(const rt_grid* g, int n_freq = 0, int nsrc = 0, int rays = 0, int ns = 0) {
+    if (g->opt.ckpt_stride <= 0) {
+        const rt_grid::TuneKey key{n_freq, nsrc, rays, ns};
+        for (const auto& e : g->tuned_k)
+            if (e.first == key) return e.second.first;
+        return 16;
+    }
+    const int want = g->opt.ckpt_stride;
+    return want <= 5 ? 4 : (want <= 11 ? 8 : (want <= 23 ? 16 : 32));
 }
 
 size_t acc_bytes(const rt_grid* g, const Call& a, const Plan& plan) {
@@ -693,7 +706,7 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (record) {
         rt::BackArgs sz{};
         sz.ray_count = a.num_rays; sz.nsrc = a.nsrc; sz.n_freq = a.n_freq; sz.ns = ns;
-        sz.stride = ckpt_stride(g);
+        sz.stride = ckpt_stride(g, a.n_freq, a.nsrc, a.num_rays, ns);
         void* ck;
         g->rec.valid = false;
         if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(sz, plan.W), &ck)) != RT_OK)
@@ -1040,6 +1053,13 @@ rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, int* l
     return RT_OK;
 }
 
+rt_status rt_last_ckpt_stride(rt_grid* g, int* stride, float* tuned_ms) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (stride) *stride = g->last_k;
+    if (tuned_ms) *tuned_ms = g->last_k_ms;
+    return RT_OK;
+}
+
 rt_status rt_last_accumulation(rt_grid* g, int* mode) {
     if (!g || !mode) return fail(RT_ERR_INVALID_ARG, "NULL argument");
     *mode = g->last_acc == 0 ? 1 : (g->last_acc == 2 ? 2 : 3);
@@ -1106,12 +1126,77 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
     b.kappa_mode = g->opt.kappa_mode;
     b.block = 32;
     b.dsrc = grad_src;
-    b.stride = ckpt_stride(g);
     const int W = pick_width(n_freq);
     const int groups = (n_freq + W - 1) / W;
+    // inputs of the reverse march: the caller's arrays for one bin, packed copies otherwise
+    const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
+    void *djp = nullptr, *dkp = nullptr;
+    if (W == 1) {
+        b.grad = grad_out; b.j = j_map; b.kappa = kappa_map;
+        b.dj = grad_j; b.dk = grad_kappa;
+    } else {
+        void *jp = nullptr, *kp = nullptr, *gp = nullptr;
+        if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
+        if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
+        if ((st = g->ensure(rt_grid::GP, packed, &gp)) != RT_OK) return st;
+        if (grad_j && (st = g->ensure(rt_grid::DJ, packed, &djp)) != RT_OK) return st;
+        if (grad_kappa && (st = g->ensure(rt_grid::DK, packed, &dkp)) != RT_OK) return st;
+        RT_CUDA(rt::launch_pack(j_map, (float*)jp, n_freq, W, groups, ncell, a.st), "pack(j) launch");
+        RT_CUDA(rt::launch_pack(kappa_map, (float*)kp, n_freq, W, groups, ncell, a.st), "pack(kappa) launch");
+        RT_CUDA(rt::launch_pack(grad_out, (float*)gp, n_freq, W, groups, ncell, a.st), "pack(grad) launch");
+        b.grad = (const float*)gp; b.j = (const float*)jp; b.kappa = (const float*)kp;
+        b.dj = (float*)djp; b.dk = (float*)dkp;
+    }
+    // checkpoint stride: tuned once per shape class when the handle autotunes and leaves the stride
+    // automatic -- every K is timed on this call's own inputs (the full reverse march with its own
+    // forward sweep, best of two runs; its gradients are discarded) and the fastest kept
+    const rt_grid::TuneKey kkey{n_freq, num_sources, num_rays, ns};
+    bool tuned_now = false;
+    g->last_k_ms = -1.0f;
+    for (const auto& e : g->tuned_k)
+        if (e.first == kkey) g->last_k_ms = e.second.second;
+    if (g->opt.autotune && g->opt.ckpt_stride <= 0 && g->last_k_ms < 0.0f) {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        cudaError_t ce = cudaEventCreate(&e[0]);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&e[1]);
+        int best_k = 16;
+        float best_ms = 3.0e38f;
+        for (int K : {4, 8, 16, 32}) {
+            if (ce != cudaSuccess) break;
+            rt::BackArgs t = b;
+            t.stride = K;
+            t.have_ckpt = 0;
+            t.hash_rec = t.hash_now = nullptr;
+            void* ck = nullptr;
+            if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(t, W), &ck)) != RT_OK) break;
+            t.ckpt = (float*)ck;
+            float kms = 3.0e38f;
+            for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+                ce = cudaEventRecord(e[0], a.st);
+                if (ce == cudaSuccess) ce = rt::launch_march_bwd(W, t, a.st);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e[1], a.st);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
+                float ms = 0.0f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[0], e[1]);
+                if (ce == cudaSuccess && ms < kms) kms = ms;
+            }
+            if (ce == cudaSuccess && kms < best_ms) { best_ms = kms; best_k = K; }
+        }
+        for (auto ev : e)
+            if (ev) cudaEventDestroy(ev);
+        if (st != RT_OK) return st;
+        if (ce != cudaSuccess) return cuda_fail(ce, "checkpoint-stride tuning");
+        if (g->tuned_k.size() >= 64) g->tuned_k.erase(g->tuned_k.begin());
+        g->tuned_k.push_back({kkey, {best_k, best_ms}});
+        g->last_k_ms = best_ms;
+        tuned_now = true;
+        g->rec.valid = false;   // the tuning runs overwrote the checkpoint slot
+    }
+    b.stride = ckpt_stride(g, n_freq, num_sources, num_rays, ns);
+    g->last_k = b.stride;
     // checkpoints recorded by the forward march of exactly this problem: skip the forward sweep
     const auto& r = g->rec;
-    b.have_ckpt = r.valid && r.j == j_map && r.kappa == kappa_map && r.src == source_pos &&
+    b.have_ckpt = !tuned_now && r.valid && r.j == j_map && r.kappa == kappa_map && r.src == source_pos &&
                   r.nsrc == num_sources && r.rays == num_rays && r.ns == ns && r.n_freq == n_freq &&
                   r.stride == b.stride && r.W == W && r.kappa_mode == g->opt.kappa_mode && r.ds == step_size;
     if (!b.have_ckpt) g->rec.valid = false;   // this reverse march rewrites the checkpoint slot
@@ -1128,29 +1213,18 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
     void* ck;
     if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(b, W), &ck)) != RT_OK) return st;
     b.ckpt = (float*)ck;
+    // the gradients are sums: clear them (again, after tuning runs) just before the launch
+    if (tuned_now && grad_src && num_sources > 0)
+        RT_CUDA(cudaMemsetAsync(grad_src, 0, sizeof(float) * 3 * (size_t)num_sources, a.st), "cudaMemsetAsync(grad_src)");
     if (W == 1) {
-        b.grad = grad_out; b.j = j_map; b.kappa = kappa_map;
-        b.dj = grad_j; b.dk = grad_kappa;
         if (grad_j) RT_CUDA(cudaMemsetAsync(grad_j, 0, field_bytes, a.st), "cudaMemsetAsync(grad_j)");
         if (grad_kappa) RT_CUDA(cudaMemsetAsync(grad_kappa, 0, field_bytes, a.st), "cudaMemsetAsync(grad_kappa)");
         if ((st = g->mark(0, a.st)) != RT_OK) return st;
         RT_CUDA(rt::launch_march_bwd(1, b, a.st), "adjoint kernel launch");
         return g->mark(1, a.st);
     }
-    const size_t packed = sizeof(float) * (size_t)groups * ncell * W;
-    void *jp = nullptr, *kp = nullptr, *gp = nullptr, *djp = nullptr, *dkp = nullptr;
-    if ((st = g->ensure(rt_grid::JP, packed, &jp)) != RT_OK) return st;
-    if ((st = g->ensure(rt_grid::KP, packed, &kp)) != RT_OK) return st;
-    if ((st = g->ensure(rt_grid::GP, packed, &gp)) != RT_OK) return st;
-    if (grad_j && (st = g->ensure(rt_grid::DJ, packed, &djp)) != RT_OK) return st;
-    if (grad_kappa && (st = g->ensure(rt_grid::DK, packed, &dkp)) != RT_OK) return st;
-    RT_CUDA(rt::launch_pack(j_map, (float*)jp, n_freq, W, groups, ncell, a.st), "pack(j) launch");
-    RT_CUDA(rt::launch_pack(kappa_map, (float*)kp, n_freq, W, groups, ncell, a.st), "pack(kappa) launch");
-    RT_CUDA(rt::launch_pack(grad_out, (float*)gp, n_freq, W, groups, ncell, a.st), "pack(grad) launch");
     if (djp) RT_CUDA(cudaMemsetAsync(djp, 0, packed, a.st), "cudaMemsetAsync(dj)");
     if (dkp) RT_CUDA(cudaMemsetAsync(dkp, 0, packed, a.st), "cudaMemsetAsync(dkappa)");
-    b.grad = (const float*)gp; b.j = (const float*)jp; b.kappa = (const float*)kp;
-    b.dj = (float*)djp; b.dk = (float*)dkp;
     if ((st = g->mark(0, a.st)) != RT_OK) return st;
     RT_CUDA(rt::launch_march_bwd(W, b, a.st), "adjoint kernel launch");
     if ((st = g->mark(1, a.st)) != RT_OK) return st;

@@ -139,7 +139,7 @@ struct BackArgs {
 };
 // Checkpoint scratch (floats) for bin-group width W and stride a.stride.
 size_t backward_ckpt_floats(const BackArgs& a, int W);
-// W in {1, 2, 4}, a.stride in {8, 16, 32}.
+// W in {1, 2, 4}, a.stride in {4, 8, 16, 32}.
 cudaError_t launch_march_bwd(int W, const BackArgs& a, cudaStream_t st);
 
 // One instance of a batched launch (device-resident table entry).

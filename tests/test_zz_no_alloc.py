@@ -96,3 +96,32 @@ def test_noalloc_single_bin_and_rejects_oversize(env):
     out = torch.empty(many_rays.j.shape, device="cuda")
     st, keep = noalloc(torch, lib, many_rays, out)
     assert st == 1 and b"rays" in lib.rt_last_error()
+
+
+def test_noalloc_matches_oracle_and_allocates_nothing(env):
+    """Directly against the FP64 oracle (not only through rt_advance), and the property the entry
+    point exists for: after a warm-up call on this device (which commits the static array and
+    loads the kernels), further calls leave the device's free memory unchanged -- nothing is
+    allocated, by the library or by the CUDA runtime on its behalf."""
+    import oracle
+    torch, lib = env
+    p = inputs.random_small(73, shape=(20, 18, 22), n_freq=4, n_src=4, num_rays=500, horizon=16.0)
+    out = torch.empty(p.j.shape, device="cuda")
+    st, keep = noalloc(torch, lib, p, out)                 # warm-up: commits the scratch, loads kernels
+    assert st == 0, lib.rt_last_error().decode()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    j, k, s = keep
+    n0, n1, n2 = p.shape
+    for _ in range(3):
+        st = lib.rt_advance_noalloc(j.data_ptr(), k.data_ptr(), s.data_ptr(), s.shape[0], n0, n1, n2, p.num_rays,
+                                    p.step_size, p.radiation_velocity, p.time_step, p.n_freq, out.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+        assert st == 0, lib.rt_last_error().decode()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    R = oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size,
+                       oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step))
+    close(out.cpu().numpy().astype(np.float64), R)
