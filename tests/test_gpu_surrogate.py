@@ -81,21 +81,46 @@ def test_network_gradients_match_fp64_reference(env):
             g = bf16(np.where(acts[l] > 0, gx, S.SLOPE * gx))
 
 
-def test_training_reduces_loss_and_fallback_is_the_march(env):
+def test_training_gains_over_the_constant_predictor_and_fallback_is_the_march(env):
+    """What the trained network gains: on held-out fields its standardised log-field loss falls
+    well below that of the constant prediction (the training mean of the log field) and below the
+    untrained network's. The error estimate is fitted on a calibration split held out from
+    training, and its threshold is calibrated there: among the calibration fields it accepts, at
+    least 99 % meet the bound (none accepted: the threshold is -inf). Every held-out field it
+    rejects is re-solved by the plain march, and evaluate() reports the fallback."""
     torch = env
     from paper_2511_09389_gb300 import surrogate as S
     from paper_2511_09389_gb300.api import Grid
     grid = Grid((64, 64, 64), 1)
-    train = S.Dataset(range(48), grid, num_rays=768)
+    train = S.Dataset(range(256), grid, num_rays=768)
+    calib = S.Dataset(range(2000, 2032), grid, num_rays=768)
+    held = S.Dataset(range(1000, 1032), grid, num_rays=768)
     model = S.Surrogate(seed=1)
-    losses = S.train(model, train, epochs=4, batch=16, lr=3e-3)
+    model.mu, model.sigma = S.target_stats(train)
+    untrained = S.heldout_loss(model, held, batch=16)
+    constant = S.heldout_loss(model, held, batch=16, constant=True)
+    # the first ~100 steps only learn the mean of the log field (loss ~ the constant's); beyond
+    # the constant it takes a few hundred steps (on the 4096-field bench set: 1.02 after 128
+    # steps, 0.67 after 256)
+    losses = S.train(model, train, epochs=50, batch=32, lr=3e-3)    # 400 Adam steps
     assert all(math.isfinite(x) for x in losses)
-    assert losses[-1] < 0.7 * losses[0], losses
-    errs, est = S.fit_estimator(model, train, batch=16)
-    assert np.all(np.isfinite(est)) and errs.shape == (48,)
-    # with no field inside the bound the threshold is -inf: everything falls back to the march
-    held = S.Dataset(range(1000, 1016), grid, num_rays=768)
-    model.est_threshold = -math.inf
+    trained = S.heldout_loss(model, held, batch=16)
+    print(f"held-out loss: constant {constant:.4f}, untrained {untrained:.4f}, trained {trained:.4f}")
+    assert trained < 0.8 * constant and trained < untrained
+    errs, est = S.fit_estimator(model, calib, batch=16)
+    assert np.all(np.isfinite(est)) and errs.shape == (32,)
+    accepted = est <= model.est_threshold
+    if accepted.any():
+        assert np.mean(errs[accepted] <= 1e-2) >= 0.99
+    else:
+        assert model.est_threshold == -math.inf
     out = S.evaluate(model, grid, held, batch=16)
-    assert out["fallback_fraction"] == 1.0
-    assert out["fields"] == 16 and out["plain_fields_per_s"] > 0
+    assert out["fields"] == 32 and out["plain_fields_per_s"] > 0
+    assert out["heldout_loss"] < 0.8 * out["constant_heldout_loss"]
+    assert out["fallback_fraction"] == 1.0 - out["accepted_fraction"]
+    # the fields it falls back on are the plain march's
+    k, jj = held.kappa[:16], held.j[:16]
+    fields, acc = S.solve(model, grid, k, jj, held.sources[:16], num_rays=768)
+    for b in np.nonzero(~acc)[0]:
+        Fb = fields[b].double()
+        assert float((Fb - held.field[b].double()).norm() / held.field[b].double().norm()) <= 1e-5
