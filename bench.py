@@ -434,6 +434,65 @@ def surrogate_leg(args, dev):
     return res
 
 
+def sharded_tail(args, p, g, j, k, s, out, hj, hk, hs, hout, stream, step_ms, kern_ms, wall, clocks, U, world,
+                 rank, dev, sources):
+    """The rest of the N > 1 run: e2e through host buffers (copy j, kappa and the sources in,
+    march this rank's shard, all-reduce, copy the field out, per step), the max over ranks, and
+    rank 0's JSON line. The single-GPU legs are not run."""
+    import torch
+    import torch.distributed as dist
+    from paper_2511_09389_gb300 import sharding
+
+    def e2e_step():
+        j.copy_(hj, non_blocking=True)
+        k.copy_(hk, non_blocking=True)
+        s.copy_(hs, non_blocking=True)
+        sharding.advance_distributed(g, j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out)
+        hout.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i in range(args.steps):
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    t = torch.tensor([statistics.mean(step_ms), statistics.mean(kern_ms), statistics.mean(e2e_ms)],
+                     dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, kms, ems = t.tolist()
+    h2d = p.j.nbytes + p.kappa.nbytes + sources.nbytes
+    line = {
+        "metric": METRIC, "value": world * U / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + f"; {16 * world} sources in all, 16 per rank",
+                   "updates_per_step": world * U, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"(source, ray) shards x{world} (rt_shard_plan), one NCCL all-reduce of the "
+                                  f"{p.j.nbytes >> 20} MiB field per step",
+                   "kernel_ms": kms, "wall_s": wall, "launch_plan": g.last_plan(),
+                   "accumulation": g.last_accumulation(),
+                   "timing": "max over ranks of the mean over the K timed steps"},
+        "e2e": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": p.j.nbytes, "ms_per_step": ems,
+                "api": "per step: pinned inputs copied in, sharding.advance_distributed, field copied out"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def native_arm(args):
     import numpy as np
     import torch
@@ -452,22 +511,36 @@ def native_arm(args):
         dist.barrier()
     from paper_2511_09389_gb300.api import Grid
 
+    from paper_2511_09389_gb300 import sharding
     from paper_2511_09389_gb300.api import num_substeps
     p = inputs.turbulent()
-    U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
+    sources = p.sources
+    if world > 1:
+        # weak scaling over the sharded data path: the job is one advance with 16 sources per
+        # rank (rank 0's are the single-GPU workload's, the others drawn uniformly in the box
+        # from seeded generators); each rank marches its planned shard of the (source, ray)
+        # pairs and one all-reduce sums the partial fields
+        extra = [np.random.Generator(np.random.PCG64(2100 + r)).uniform(0.0, p.shape[0] - 1.0, size=(16, 3))
+                 for r in range(1, world)]
+        sources = np.concatenate([p.sources] + [e.astype(np.float32) for e in extra])
+    ns_ = num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    U = len(p.sources) * p.num_rays * ns_ * p.n_freq          # updates per rank and step
     if args.plan:
         g = Grid(p.shape, 8, profile=True, plan=tuple(int(x) for x in args.plan.split(",")))
     else:
         g = Grid(p.shape, 8, profile=True, autotune=True)   # tuned during the warm-up calls
     j = torch.from_numpy(p.j).to(dev)
     k = torch.from_numpy(p.kappa).to(dev)
-    s = torch.from_numpy(p.sources).to(dev)
+    s = torch.from_numpy(sources).to(dev)
     out = torch.empty_like(j)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
+        if world > 1:
+            sharding.advance_distributed(g, j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out)
+        else:
+            g.advance(j, k, s, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=out)
 
     visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     clocks = ClockSampler(visible[local].strip() if local < len(visible) else local)
@@ -496,8 +569,11 @@ def native_arm(args):
 
     # end to end through the host entry point: pinned inputs in, field back to the host
     pin = lambda a: torch.from_numpy(a).pin_memory()
-    hj, hk, hs = pin(p.j), pin(p.kappa), pin(p.sources)
+    hj, hk, hs = pin(p.j), pin(p.kappa), pin(sources)
     hout = torch.empty(p.j.shape, dtype=torch.float32).pin_memory()
+    if world > 1:
+        return sharded_tail(args, p, g, j, k, s, out, hj, hk, hs, hout, stream, step_ms, kern_ms, wall, clocks,
+                            U, world, rank, dev, sources)
     for _ in range(max(1, args.warmup)):
         g.advance_host(hj, hk, hs, p.num_rays, p.step_size, p.radiation_velocity, p.time_step, out=hout)
     e2e_ms = []

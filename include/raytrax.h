@@ -458,6 +458,20 @@ rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int e
 rt_status rt_last_plan(rt_grid* grid, int* width, int* block, int* prefetch, int* lanes_per_ray, int* tile,
                        float* tuned_ms);
 
+/* Multi-device partition of one advance (Sec. 2: the directions are sharded across devices,
+   each device sums its part, and one reduction across devices combines them; here the
+   (source, ray) pairs are split, which removes the paper's need for N_Omega divisible by the
+   device count). Host only, no device call. Shard `shard` of `n_shards` owns a contiguous range
+   of the source-major (source, ray) pairs; range sizes differ by at most one pair. The range is
+   written as *n_pieces <= 3 pieces to HOST pieces[4 * i + 0..3] = (source_begin, source_end,
+   ray_begin, ray_end): march each with rt_advance_rays on sources [source_begin, source_end)
+   (pointer source_pos + 3 * source_begin) and rays [ray_begin, ray_end) of the num_rays lattice,
+   the first piece overwriting the shard's partial field and the others accumulating; the sum of
+   all shards' partial fields is rt_advance's field. An empty shard (fewer pairs than shards)
+   has no piece. RT_ERR_INVALID_ARG for num_sources < 0, num_rays < 1 or shard outside
+   [0, n_shards). */
+rt_status rt_shard_plan(int num_sources, int num_rays, int n_shards, int shard, int* pieces, int* n_pieces);
+
 /* Checkpoint stride K of the last rt_backward* on this handle, and the reverse-march time in ms
    the stride tuner measured for it (-1 when it was not tuned). Either pointer may be NULL. */
 rt_status rt_last_ckpt_stride(rt_grid* grid, int* stride, float* tuned_ms);

@@ -20,7 +20,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_continue", "rt_advance_host",
            "rt_advance_host_async", "rt_host_wait", "rt_host_join", "rt_backward", "rt_backward_sources",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
-           "rt_tuning_report", "rt_last_accumulation", "rt_last_ckpt_stride", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
+           "rt_tuning_report", "rt_last_accumulation", "rt_last_ckpt_stride", "rt_shard_plan", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_info",
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
         lib.rt_backward_sources.restype = i
         lib.rt_trace_cells.argtypes = [vp, fp, i, i, f, i, llp, llp]
         lib.rt_trace_cells.restype = i
+        lib.rt_shard_plan.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        lib.rt_shard_plan.restype = i
         lib.rt_last_ckpt_stride.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         lib.rt_last_ckpt_stride.restype = i
         lib.rt_last_accumulation.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]

@@ -1053,6 +1053,34 @@ rt_status rt_last_plan(rt_grid* g, int* width, int* block, int* prefetch, int* l
     return RT_OK;
 }
 
+rt_status rt_shard_plan(int num_sources, int num_rays, int n_shards, int shard, int* pieces, int* n_pieces) {
+    if (!pieces || !n_pieces) return fail(RT_ERR_INVALID_ARG, "rt_shard_plan: NULL output");
+    *n_pieces = 0;
+    if (num_sources < 0 || num_rays < 1 || n_shards < 1 || shard < 0 || shard >= n_shards)
+        return fail(RT_ERR_INVALID_ARG, "rt_shard_plan: need num_sources >= 0, num_rays >= 1, 0 <= shard < n_shards");
+    // shard s owns pairs [p0, p1) of the source-major (source, ray) order: sizes differ by at most one
+    const long long total = (long long)num_sources * num_rays;
+    const long long base = total / n_shards, rem = total % n_shards;
+    const long long p0 = shard * base + std::min<long long>(shard, rem);
+    const long long p1 = p0 + base + (shard < rem ? 1 : 0);
+    long long p = p0;
+    while (p < p1) {
+        const int s0 = (int)(p / num_rays), r0 = (int)(p % num_rays);
+        int* q = pieces + 4 * (*n_pieces);
+        if (r0 != 0 || p1 - p < num_rays) {   // part of one source's rays
+            const long long end = std::min<long long>(p1, (long long)(s0 + 1) * num_rays);
+            q[0] = s0; q[1] = s0 + 1; q[2] = r0; q[3] = (int)(end - (long long)s0 * num_rays);
+            p = end;
+        } else {                               // whole sources
+            const int s1 = (int)(p1 / num_rays);
+            q[0] = s0; q[1] = s1; q[2] = 0; q[3] = num_rays;
+            p = (long long)s1 * num_rays;
+        }
+        ++*n_pieces;
+    }
+    return RT_OK;
+}
+
 rt_status rt_last_ckpt_stride(rt_grid* g, int* stride, float* tuned_ms) {
     if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
     if (stride) *stride = g->last_k;
