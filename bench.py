@@ -424,6 +424,8 @@ def surrogate_leg(args, dev):
     peak_tf = float(peaks.get("bf16_tflops", 1900.0))
     conv["roofline"] = {"bound": "tensor", "achieved": conv["forward_tflops"], "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": conv["forward_tflops"] / peak_tf,
+                        "data_grad_frac": conv["data_grad_tflops"] / peak_tf,
+                        "weight_grad_frac": conv["weight_grad_tflops"] / peak_tf,
                         "peak_kind": "measured" if "bf16_tflops" in peaks else "fallback"}
     res["conv_layer"] = conv
     res.update({"train_fields": len(train), "calibration_fields": len(calib), "epochs": args.surrogate_epochs,

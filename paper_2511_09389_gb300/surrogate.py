@@ -403,9 +403,9 @@ def evaluate(model, grid, ds, batch=32, bound=1e-2):
 
 def time_conv_layer(batch=8, edge=64, dilation=2, reps=5, seed=0):
     """CUDA-event time of one 32 -> 32 channel tensor-core convolution layer on a batch of
-    edge^3 volumes of random bf16 activations: the forward (bias + LeakyReLU) and the weight +
-    bias gradient, each averaged over `reps` calls after one warm-up call. A call does
-    2 * voxels * 32 * 32 * 27 flops."""
+    edge^3 volumes of random bf16 activations: the forward (bias + LeakyReLU), the data gradient
+    (transposed weights, LeakyReLU-derivative mask) and the weight + bias gradient, each averaged
+    over `reps` calls after one warm-up call. A call does 2 * voxels * 32 * 32 * 27 flops."""
     lib = _native.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     vox = edge ** 3
@@ -416,21 +416,30 @@ def time_conv_layer(batch=8, edge=64, dilation=2, reps=5, seed=0):
     w = torch.randn(32 * 32 * 27, device=dev, generator=g) / math.sqrt(27 * 32)
     bias = torch.zeros(32, device=dev)
     packed = torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device=dev)
+    packed_t = torch.empty(27 * 32 * 32, dtype=torch.bfloat16, device=dev)
+    dx = torch.empty_like(x)
     dw = torch.zeros(32 * 32 * 27, device=dev)
     db = torch.zeros(32, device=dev)
     st = torch.cuda.current_stream(dev).cuda_stream
     check(lib.rt_conv3d_pack_weights(_p(w), 32, 32, 0, _p(packed), st))
+    check(lib.rt_conv3d_pack_weights(_p(w), 32, 32, 1, _p(packed_t), st))
 
     def fwd():
         check(lib.rt_conv3d_forward(_p(x), batch, edge, edge, edge, 32, _p(packed), _p(bias), 32, dilation, 1, SLOPE,
                                     None, _p(y), None, st))
+
+    def dgrad():
+        # the data gradient as training runs it: the convolution with flipped, transposed
+        # weights, times the LeakyReLU derivative of the layer below (mask = its activation)
+        check(lib.rt_conv3d_forward(_p(y), batch, edge, edge, edge, 32, _p(packed_t), None, 32, dilation, 0, SLOPE,
+                                    _p(x), _p(dx), None, st))
 
     def wgrad():
         check(lib.rt_conv3d_weight_grad(_p(x), _p(y), batch, edge, edge, edge, 32, 32, dilation, _p(dw), _p(db), st))
 
     flop = 2.0 * batch * vox * 32 * 32 * 27
     out = {"batch": batch, "edge": edge, "dilation": dilation, "flop_per_call": flop}
-    for name, fn in (("forward", fwd), ("weight_grad", wgrad)):
+    for name, fn in (("forward", fwd), ("data_grad", dgrad), ("weight_grad", wgrad)):
         fn()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
