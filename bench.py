@@ -324,7 +324,7 @@ def paper_workload(args, dev, flush, stream):
 def _batch_vs_one_by_one(probs, args, dev, stream):
     """One autotuned batch (dedicated launches for instances that fill the GPU, persistent
     kernels for the rest) replayed from a CUDA graph, against the same instances advanced one
-    autotuned rt_advance call at a time (mean ms of each)."""
+    autotuned rt_advance call at a time with the batch's FP32 sums (mean ms of each)."""
     import statistics as st
     import torch
     from paper_2511_09389_gb300.api import Batch, Grid
@@ -346,7 +346,9 @@ def _batch_vs_one_by_one(probs, args, dev, stream):
         e1.record(stream)
         e1.synchronize()
         tb.append(e0.elapsed_time(e1))
-    grids = [Grid(p.shape, 8, autotune=True) for p in probs]
+    # the same arithmetic as the batch, which sums in FP32: single calls would pick fixed-point
+    # sums for the dense instances (automatic accumulation) and not be the same computation
+    grids = [Grid(p.shape, 8, autotune=True, accumulation="fp32") for p in probs]
     outs = [torch.empty_like(d["j"]) for d in dev_in]
 
     def one_by_one():
