@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     int g0 = -1, g7 = -1;
     Vec<W> jr[8];                     // SG: j at the corners of the current substep
     int jr0 = -1, jr7 = -1;
-    // per-thread segment record (local memory): x, I_k, E_k, a_k, e_k
+    // per-thread segment record: x, I_k, E_k, a_k, e_k. For strides up to 8 the segment loops
+    // are unrolled with constant indices, so the record lives in registers; longer records go
+    // to local memory
     float rx[K], ry[K], rz[K], rI[K][W], rE[K][W], ra[K][W], re[K][W];
     const int nseg = (a.ns + K - 1) / K;
 #pragma unroll 1
@@ -131,8 +133,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
         // replay the segment exactly as the forward sweep ran it
         Vec<W> jc[8], kc;
         int c0 = -1, c7 = -1, cn = -1;
-#pragma unroll 1
-        for (int q = 0; q < len; ++q) {
+        auto replay = [&](const int q) {
             Sample sm;
             make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
             if (sm.cell[0] != c0 || sm.cell[7] != c7) {
@@ -157,10 +158,17 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
             x = __fadd_rn(x, dx);
             y = __fadd_rn(y, dy);
             z = __fadd_rn(z, dz);
+        };
+        if constexpr (K <= 8) {   // constant indices: the record stays in registers
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (q < len) replay(q);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < len; ++q) replay(q);
         }
         // walk the segment backwards
-#pragma unroll 1
-        for (int q = len - 1; q >= 0; --q) {
+        auto walk = [&](const int q) {
             Sample sm;
             make_sample(rx[q], ry[q], rz[q], a.n0, a.n1, a.n2, a.kappa_mode, sm);
             if (sm.cell[0] != g0 || sm.cell[7] != g7) {
@@ -242,6 +250,14 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
                     for (int b = 0; b < W; ++b) pdk[b] += ddk[b];
                 }
             }
+        };
+        if constexpr (K <= 8) {
+#pragma unroll
+            for (int q = K - 1; q >= 0; --q)
+                if (q < len) walk(q);
+        } else {
+#pragma unroll 1
+            for (int q = len - 1; q >= 0; --q) walk(q);
         }
     }
     if (djg && pc[0] >= 0) {

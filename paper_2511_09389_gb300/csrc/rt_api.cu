@@ -498,7 +498,6 @@ rt_status prepare(rt_grid* g, const Call& a, int ns, const Plan& plan, const flo
     return RT_OK;
 }
 
-// Adjoint checkpoint stride: the option, rounded to a supported value; automatic = 16.
 // Adjoint checkpoint stride K in {4, 8, 16, 32}: the option rounded to the nearest supported
 // value; automatic: the stride the reverse-march tuner picked for this shape class (n_freq,
 // sources, rays, N_s) when the handle autotunes and has tuned it, else 16.

@@ -44,7 +44,7 @@ def oracle_backward(p, G, kappa_mode=0):
     return oracle.backward(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G, kappa_mode=kappa_mode)
 
 
-@pytest.mark.parametrize("n_freq,stride", [(1, 8), (1, 16), (2, 16), (3, 32), (4, 8), (5, 16)])
+@pytest.mark.parametrize("n_freq,stride", [(1, 4), (1, 8), (1, 16), (2, 4), (2, 16), (3, 32), (4, 4), (4, 8), (5, 16)])
 def test_adjoint_matches_oracle(torch_cuda, n_freq, stride):
     p = inputs.random_small(100 + n_freq, shape=(14, 11, 17), n_freq=n_freq, n_src=4, num_rays=97,
                             step_size=0.6, horizon=15.0)   # N_s = 25: ragged last segment
@@ -166,7 +166,7 @@ def gpu_backward_sources(torch, p, G, **opts):
     return gj.cpu().numpy(), gk.cpu().numpy(), gs.cpu().numpy()
 
 
-@pytest.mark.parametrize("n_freq,stride", [(1, 16), (2, 8), (3, 32), (5, 16)])
+@pytest.mark.parametrize("n_freq,stride", [(1, 4), (1, 16), (2, 8), (3, 32), (4, 4), (5, 16)])
 def test_source_gradient_matches_oracle(torch_cuda, n_freq, stride):
     p = inputs.random_small(200 + n_freq, shape=(14, 11, 17), n_freq=n_freq, n_src=4, num_rays=97,
                             step_size=0.6, horizon=15.0)
