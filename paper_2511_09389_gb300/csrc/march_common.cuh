@@ -117,6 +117,30 @@ __device__ __forceinline__ Vec<4> ldg_vec<4>(const float* __restrict__ p, int ce
     Vec<4> r; r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w; return r;
 }
 
+// Predicated gather (no branch): v is loaded from cell when p is true and left as it was
+// otherwise. The inputs are read-only for the whole kernel, so the load may be scheduled freely
+// (non-volatile asm); the index must be a valid cell either way (callers clamp it).
+template <int W>
+__device__ __forceinline__ void ldg_vec_if(bool p, const float* __restrict__ base, int cell, Vec<W>& v);
+template <>
+__device__ __forceinline__ void ldg_vec_if<1>(bool p, const float* __restrict__ base, int cell, Vec<1>& v) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t@q ld.global.nc.f32 %0, [%2];\n\t}"
+        : "+f"(v.v[0])
+        : "r"((int)p), "l"(base + cell));
+}
+template <>
+__device__ __forceinline__ void ldg_vec_if<2>(bool p, const float* __restrict__ base, int cell, Vec<2>& v) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.global.nc.v2.f32 {%0, %1}, [%3];\n\t}"
+        : "+f"(v.v[0]), "+f"(v.v[1])
+        : "r"((int)p), "l"(base + 2 * (size_t)cell));
+}
+template <>
+__device__ __forceinline__ void ldg_vec_if<4>(bool p, const float* __restrict__ base, int cell, Vec<4>& v) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%5];\n\t}"
+        : "+f"(v.v[0]), "+f"(v.v[1]), "+f"(v.v[2]), "+f"(v.v[3])
+        : "r"((int)p), "l"(base + 4 * (size_t)cell));
+}
+
 // Fire-and-forget global reductions (no return value): one L2 atomic per W-vector. They carry
 // no "memory" clobber: the accumulators they target are never read by the kernels that issue
 // them, so loads of the read-only inputs may be scheduled across them; kernel completion

@@ -561,8 +561,7 @@ __device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W
         const int s10 = (e01 * n1 + e10) * n2, s11 = (e01 * n1 + e11) * n2;
         const int ncell[8] = {s00 + e20, s00 + e21, s01 + e20, s01 + e21, s10 + e20, s10 + e21, s11 + e20, s11 + e21};
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if ((mask >> c) & 1u) gj[c] = ldg_vec<W>(jg, ncell[c]);
+        for (int c = 0; c < 8; ++c) ldg_vec_if<W>((mask >> c) & 1u, jg, ncell[c], gj[c]);
         // Eq. 2 with kappa(x_k); then kappa(x_{k+1}) is gathered
         float dep[W];
         if constexpr (W % 2 == 0) {
@@ -591,7 +590,7 @@ __device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W
             }
         }
         const int nnn = kappa_cell(b0, b1, b2, xn, yn, zn);
-        if (more && nnn != gnn) gk = ldg_vec<W>(kg, nnn);
+        ldg_vec_if<W>(more && nnn != gnn, kg, nnn, gk);
         gnn = nnn;
         // deposits of substep k into the current slots
 #pragma unroll
@@ -610,8 +609,9 @@ __device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W
         }
 
         // ---- the slots that leave at k+1: flush their sums (this substep included) and start the
-        // entering corners' sums from zero ----
-        if (mask) {
+        // entering corners' sums from zero (predicated, no branch: some lane of a warp almost
+        // always has a slot to change) ----
+        {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const bool f = (mask >> c) & 1u;
