@@ -84,7 +84,7 @@ typedef struct {
        whole corner set while it is unchanged and flushes and re-gathers all 8 corners when it
        changes, and mode 4 is mode 0 with the corners that enter at substep k+1 gathered before
        the update of substep k (no tiles, no checkpoint recording). plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
-       the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 only). plan_tile: source deposit tiles (1: off, 2: on): each
+       the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 or 4). plan_tile: source deposit tiles (1: off, 2: on): each
        block sums the deposits of its rays in the 8^3 cells around its source in shared memory
        and adds them to the field once (not in deterministic mode). */
     int plan_width;

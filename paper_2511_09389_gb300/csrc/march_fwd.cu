@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF
 }
 
 // Lanes per ray = 2: adjacent lanes (sub = threadIdx.x & 1) share one (ray, source, bin group),
-// each with half of its corner slots (march_lane_pair). REC: also the reverse march's checkpoints.
-// DET: the accumulation (flush() in march_lane.cuh).
-template <int W, bool REC = false, int DET = 0>
+// each with half of its corner slots (march_lane_pair; gathers mode PF = 4: march_lane_pair_ahead).
+// REC: also the reverse march's checkpoints. DET: the accumulation (flush() in march_lane.cuh).
+template <int W, bool REC = false, int DET = 0, int PF = 0>
 __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     const int rays_per_block = blockDim.x / 2;
     const int rblocks = (a.ray_count + rays_per_block - 1) / rays_per_block;
@@ -158,15 +158,19 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
         L.ck = a.ckpt + ((long long)g * a.nsrc + s) * a.ray_count + r;
         L.ck_stride = a.ck_stride;
     }
-    march_lane_pair<W, REC, DET>(L, sub, pmask);
+    if constexpr (PF == 4)
+        march_lane_pair_ahead<W, REC, DET>(L, sub, pmask);
+    else
+        march_lane_pair<W, REC, DET>(L, sub, pmask);
 }
 
 // ---- kernel table ------------------------------------------------------------------------
 // The compiled (W, gathers mode, accumulation, tiles, checkpoints, lanes per ray) combinations:
 //   FP32: every W and gathers mode with and without tiles (mode 4: without); recording with
-//         gathers mode 0 (and 1 or 3 for one bin); two lanes per ray for every W.
+//         gathers mode 0 (and 1 or 3 for one bin); two lanes per ray for every W with gathers
+//         mode 0 or 4 (recording: mode 0, and mode 4 for one bin).
 //   fixed point: corner slots and gathers mode 4 for every W; for one bin also recording and two
-//         lanes per ray.
+//         lanes per ray; two lanes per ray with gathers mode 4 for one and four bins.
 //   FP64: corner slots for every W, with and without recording; two lanes per ray for one bin.
 using MarchKernel = void (*)(MarchArgs);
 
@@ -205,7 +209,17 @@ MarchKernel pick_one_lane(int pf, int acc, bool tile, bool rec) {
     return rec ? k_march_fwd<W, 0, 2, false, true> : k_march_fwd<W, 0, 2, false>;
 }
 
-MarchKernel pick_pair(int W, int acc, bool rec) {
+MarchKernel pick_pair(int W, int pf, int acc, bool rec) {
+    if (pf == 4) {   // gathers one substep ahead: FP32 (recording for one bin) and fixed point
+        if (acc == 0 && !rec)
+            return W == 1 ? k_march_fwd_pair<1, false, 0, 4> : (W == 2 ? k_march_fwd_pair<2, false, 0, 4>
+                                                                     : k_march_fwd_pair<4, false, 0, 4>);
+        if (acc == 0 && W == 1) return k_march_fwd_pair<1, true, 0, 4>;
+        if (acc == 1 && !rec && (W == 1 || W == 4))
+            return W == 1 ? k_march_fwd_pair<1, false, 1, 4> : k_march_fwd_pair<4, false, 1, 4>;
+        return nullptr;
+    }
+    if (pf != 0) return nullptr;
     if (acc == 0) {
         switch (W * 2 + (rec ? 1 : 0)) {
             case 2: return k_march_fwd_pair<1>;
@@ -224,7 +238,7 @@ MarchKernel pick_pair(int W, int acc, bool rec) {
 
 MarchKernel pick_march(int W, int pf, int acc, bool tile, bool rec, int lpr) {
     if (pf < 0 || pf > 4 || acc < 0 || acc > 2) return nullptr;
-    if (lpr == 2) return pf == 0 && !tile ? pick_pair(W, acc, rec) : nullptr;
+    if (lpr == 2) return !tile && (W == 1 || W == 2 || W == 4) ? pick_pair(W, pf, acc, rec) : nullptr;
     if (lpr != 1) return nullptr;
     switch (W) {
         case 1: return pick_one_lane<1>(pf, acc, tile, rec);

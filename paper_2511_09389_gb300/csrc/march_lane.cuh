@@ -641,6 +641,180 @@ __device__ __forceinline__ void march_lane_slots_ahead(const Lane& L, RayState<W
     for (int b = 0; b < W; ++b) { R.I[b] = I[b]; R.tau[b] = tau[b]; }
 }
 
+// Two lanes per ray with gathers mode 4: the slots of march_lane_pair (lane `sub` keeps the four
+// slots whose axis-2 bit is `sub`) updated as in march_lane_slots_ahead -- the transition
+// k -> k+1 is classified during substep k, the corners that enter at k+1 are gathered into the
+// slots they replace right after substep k's partial trilinear sum has read them, kappa(x_{k+1})
+// right after kappa(x_k) is used -- and every gather, flush and slot change is predicated, so the
+// loop has no branch. Both lanes compute the same geometry, transitions and radiometry (the two
+// partial sums are exchanged with one shuffle per bin; a + b and b + a are the same FP32
+// number). REC: lane 0 of the pair stores the checkpoints (x_k, I_k, tau_k).
+template <int W, bool REC, int DET>
+__device__ __forceinline__ void march_lane_pair_ahead(const Lane& L, int sub, unsigned pmask) {
+    const float* __restrict__ jg = L.jg;
+    const float* __restrict__ kg = L.kg;
+    const float dx = __fmul_rn(L.n.x, L.ds), dy = __fmul_rn(L.n.y, L.ds), dz = __fmul_rn(L.n.z, L.ds);
+    float x = L.sx, y = L.sy, z = L.sz;
+    float I[W], tau[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) { I[b] = 0.0f; tau[b] = 0.0f; }
+    const float ds = L.ds, scale = L.scale;
+    const int n1 = L.n1, n2 = L.n2;
+    auto kappa_cell = [&](const Axis& a0, const Axis& a1, const Axis& a2, float px, float py, float pz) {
+        return L.kappa_mode == 0 ? (a0.lo * n1 + a1.lo) * n2 + a2.lo
+                                 : (nearest_round(px, L.n0) * n1 + nearest_round(py, n1)) * n2 + nearest_round(pz, n2);
+    };
+
+    // slot i of this lane is slot c = 2 i + sub of the ray: bits (c >> 2, c >> 1, c) & 1 =
+    // (i >> 1, i & 1, sub) along axes 0, 1, 2; with roles P_a the bit selects lo (bit == P_a) or hi
+    Axis a0 = axis_sample(x, L.n0), a1 = axis_sample(y, n1), a2 = axis_sample(z, n2);
+    int P0 = 0, P1 = 0, P2 = 0;
+    int pc[4];
+    float pend[4][W];
+    Vec<W> gj[4];
+    {
+        const int c2 = sub ? a2.hi : a2.lo;
+        const int r0 = a0.lo * n1, r1 = a0.hi * n1;
+        const int cell[4] = {(r0 + a1.lo) * n2 + c2, (r0 + a1.hi) * n2 + c2, (r1 + a1.lo) * n2 + c2,
+                             (r1 + a1.hi) * n2 + c2};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            pc[i] = cell[i];
+            gj[i] = ldg_vec<W>(jg, cell[i]);
+#pragma unroll
+            for (int b = 0; b < W; ++b) pend[i][b] = 0.0f;
+        }
+    }
+    int gnn = kappa_cell(a0, a1, a2, x, y, z);
+    Vec<W> gk = ldg_vec<W>(kg, gnn);
+
+    int ck_left = 0;     // REC: substeps until the next checkpoint
+    float* ckp = L.ck;   // REC: this lane's next checkpoint
+#pragma unroll 1
+    for (int k = 0; k < L.ns; ++k) {
+        if (REC) {
+            if (ck_left == 0) {
+                if (sub == 0) {
+                    ckp[0] = x; ckp[L.ck_lanes] = y; ckp[2 * L.ck_lanes] = z;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        ckp[(3 + b) * L.ck_lanes] = I[b];
+                        ckp[(3 + W + b) * L.ck_lanes] = tau[b];
+                    }
+                }
+                ckp += (3 + 2 * W) * L.ck_lanes;
+                ck_left = L.ck_stride;
+            }
+            --ck_left;
+        }
+        // ---- x_{k+1} and the slots that change (classification as in march_lane_slots_ahead) ----
+        const float xn = __fadd_rn(x, dx), yn = __fadd_rn(y, dy), zn = __fadd_rn(z, dz);   // Eq. 2: x_{k+1}
+        const Axis b0 = axis_sample(xn, L.n0), b1 = axis_sample(yn, n1), b2 = axis_sample(zn, n2);
+        const bool more = k + 1 < L.ns;
+        const int d0 = L.n0 > 1 ? b0.f - a0.f : 0, d1 = n1 > 1 ? b1.f - a1.f : 0, d2 = n2 > 1 ? b2.f - a2.f : 0;
+        const bool up0 = d0 == 1, up1 = d1 == 1, up2 = d2 == 1;
+        const bool dn0 = d0 == -1, dn1 = d1 == -1, dn2 = d2 == -1;
+        const bool other = (unsigned)(d0 + 1) > 2u || (unsigned)(d1 + 1) > 2u || (unsigned)(d2 + 1) > 2u;
+        const bool sh0 = up0 || dn0, sh1 = up1 || dn1, sh2 = up2 || dn2;
+        const int q0 = P0 ^ (dn0 ? 1 : 0), q1 = P1 ^ (dn1 ? 1 : 0), q2 = P2 ^ (dn2 ? 1 : 0);
+        // leaving slots of this lane, bit i = slot i: axis 0 bit is i >> 1, axis 1 bit is i & 1
+        unsigned mask = other ? 0xFu : 0u;
+        mask |= sh0 ? (q0 ? 0xCu : 0x3u) : 0u;
+        mask |= sh1 ? (q1 ? 0xAu : 0x5u) : 0u;
+        mask |= (sh2 && q2 == sub) ? 0xFu : 0u;
+        if (!more) mask = 0u;
+        const int Q0 = P0 ^ (sh0 ? 1 : 0), Q1 = P1 ^ (sh1 ? 1 : 0), Q2 = P2 ^ (sh2 ? 1 : 0);   // roles at k+1
+
+        // ---- substep k: weights of x_k in this lane's slot order ----
+        const float u0 = 1.0f - a0.t, u1 = 1.0f - a1.t, u2 = 1.0f - a2.t;
+        const float f00 = P0 ? a0.t : u0, f01 = P0 ? u0 : a0.t;
+        const float f10 = P1 ? a1.t : u1, f11 = P1 ? u1 : a1.t;
+        const float f2 = (P2 ^ sub) ? a2.t : u2;
+        float w[4];
+        w[0] = (f00 * f10) * f2; w[1] = (f00 * f11) * f2; w[2] = (f01 * f10) * f2; w[3] = (f01 * f11) * f2;
+        float part[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) part[b] = 0.0f;
+        if constexpr (W % 2 == 0) {
+#pragma unroll
+            for (int h = 0; h < W; h += 2) {
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    acc = __ffma2_rn(make_float2(w[i], w[i]), make_float2(gj[i].v[h], gj[i].v[h + 1]), acc);
+                part[h] = acc.x; part[h + 1] = acc.y;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) part[b] = fmaf(w[i], gj[i].v[b], part[b]);
+            }
+        }
+        // the slots are read: gather the corners entering at k+1 into the slots they replace
+        const int e00 = Q0 ? b0.hi : b0.lo, e01 = Q0 ? b0.lo : b0.hi;
+        const int e10 = Q1 ? b1.hi : b1.lo, e11 = Q1 ? b1.lo : b1.hi;
+        const int e2 = (Q2 ^ sub) ? b2.hi : b2.lo;
+        const int s0 = e00 * n1, s1 = e01 * n1;
+        const int ncell[4] = {(s0 + e10) * n2 + e2, (s0 + e11) * n2 + e2, (s1 + e10) * n2 + e2, (s1 + e11) * n2 + e2};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ldg_vec_if<W>((mask >> i) & 1u, jg, ncell[i], gj[i]);
+        // Eq. 2 with kappa(x_k) and the whole trilinear sum of j(x_k)
+        float dep[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float jk = part[b] + __shfl_xor_sync(pmask, part[b], 1);
+            const float kds = gk.v[b] * ds;
+            const float att = neg_exp(kds);               // exp(-kappa(x_k) ds)
+            const float em = neg_exp(tau[b]);             // exp(-tau_k)
+            I[b] = fmaf(I[b], att, jk * em * ds);         // Eq. 2: I_{k+1}
+            tau[b] += kds;                                // Eq. 2: tau_{k+1}
+            dep[b] = I[b] * scale;
+        }
+        const int nnn = kappa_cell(b0, b1, b2, xn, yn, zn);
+        ldg_vec_if<W>(more && nnn != gnn, kg, nnn, gk);
+        gnn = nnn;
+        // deposits of substep k into this lane's slots
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if constexpr (W % 2 == 0) {
+#pragma unroll
+                for (int h = 0; h < W; h += 2) {
+                    const float2 v = __ffma2_rn(make_float2(w[i], w[i]), make_float2(dep[h], dep[h + 1]),
+                                                make_float2(pend[i][h], pend[i][h + 1]));
+                    pend[i][h] = v.x; pend[i][h + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[i][b] = fmaf(w[i], dep[b], pend[i][b]);
+            }
+        }
+        // the leaving slots: flush their sums (this substep included), start the entering ones
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool f = (mask >> i) & 1u;
+            flush_if<W, DET>(f, L, pc[i], pend[i]);
+            if constexpr (W % 2 == 0) {
+                const float keep = f ? 0.0f : 1.0f;
+#pragma unroll
+                for (int h = 0; h < W; h += 2) {
+                    const float2 v = __fmul2_rn(make_float2(pend[i][h], pend[i][h + 1]), make_float2(keep, keep));
+                    pend[i][h] = v.x; pend[i][h + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < W; ++b) pend[i][b] = f ? 0.0f : pend[i][b];
+            }
+            pc[i] = f ? ncell[i] : pc[i];
+        }
+        P0 = Q0; P1 = Q1; P2 = Q2;
+        a0 = b0; a1 = b1; a2 = b2;
+        x = xn; y = yn; z = zn;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) flush<W, DET>(L, pc[i], pend[i]);
+}
+
 // Gathers modes 1 and 3, the corner set as one unit: deposits are merged in registers while the
 // set is unchanged and all eight corners are flushed when it changes. AHEAD (mode 1): the gathers
 // of substep k+1 are issued before the update of substep k, every substep. Otherwise (mode 3)

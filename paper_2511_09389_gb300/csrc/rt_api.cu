@@ -265,7 +265,7 @@ int num_substeps(float ds, float c, float dt, int cap) { return rt::substeps(ds,
 }  // namespace
 
 // Widths W in {the default, 2, 1} that fit n_freq; 32, 64, 128, 256 threads per block; gather
-// modes 0, 1, 2, 3 with and without source tiles, mode 0 with two lanes per ray, and mode 4.
+// modes 0, 1, 2, 3 with and without source tiles, mode 4, and modes 0 and 4 with two lanes per ray.
 int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int widths[3], nw = 0;
     widths[nw++] = n_freq == 1 ? 1 : (n_freq == 2 ? 2 : 4);
@@ -274,13 +274,13 @@ int rt::march_plan_candidates(int n_freq, MarchPlan* out) {
     int n = 0;
     for (int wi = 0; wi < nw; ++wi)
         for (int b : {32, 64, 128, 256})
-            for (int cand = 0; cand < 10; ++cand) {
+            for (int cand = 0; cand < 11; ++cand) {
                 MarchPlan p;
                 p.W = widths[wi];
                 p.block = b;
                 p.prefetch = cand < 8 ? cand >> 1 : (cand == 8 ? 0 : 4);
                 p.tile = cand < 8 ? (cand & 1) : 0;
-                p.lpr = cand == 8 ? 2 : 1;
+                p.lpr = cand == 8 || cand == 10 ? 2 : 1;
                 out[n++] = p;
             }
     return n;
@@ -622,28 +622,27 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if ((st = g->table(a.num_rays, a.ray_begin, a.ray_end, &dirs)) != RT_OK) return st;
     const float scale = (float)(4.0 * 3.14159265358979323846 / (double)a.num_rays);
 
-    // default plan (measured on GB300): 32-thread blocks. Summing in FP32: gather prefetch and
-    // source deposit tiles for one bin per thread, corner slots with the gathers a substep ahead
-    // (gathers mode 4) for wider groups (a tiled 4-bin deposit is 32 shared-memory atomics).
-    // Summing in 8-byte words (no tiles): gathers mode 4, or for one bin two lanes per ray while the
-    // call has too few lanes to fill the GPU (twice as fast on 64^3 with 8 sources, slower on 2,097
-    // sources)
+    // default plan (measured on GB300): 32-thread blocks, corner slots with the gathers a substep
+    // ahead (gathers mode 4). One bin per thread: two lanes per ray while the call has too few
+    // lanes to fill the GPU (64^3, 8 sources, 3,072 rays: 0.09 ms against 0.15 ms for tiles with
+    // prefetch); otherwise, summing in FP32, gather prefetch with source deposit tiles. Wider
+    // groups: one lane per ray (four bins on 128^3 with 16 sources: 0.25 ms against 0.37 ms with
+    // two lanes, which repeat the geometry; a tiled 4-bin deposit is 32 shared-memory atomics).
+    // Summing in 8-byte words (no tiles): gathers mode 4.
     const bool det = g->opt.deterministic != 0;
     Plan plan;
     plan.W = pick_width(a.n_freq);
     plan.block = 32;
-    plan.prefetch = plan.W == 1 ? 1 : 4;
     if (g->opt.plan_width) plan.W = g->opt.plan_width;
-    plan.tile = plan.W == 1 ? 1 : 0;
-    if (plan.W > 1) plan.prefetch = 4;
     {
-        Plan untiled = plan;
-        untiled.tile = 0;
-        if (acc_mode_for(g, untiled, a, ns) != 0) {
-            const double lanes = (double)a.nsrc * (a.ray_end - a.ray_begin) * ((a.n_freq + plan.W - 1) / plan.W);
-            plan.tile = 0;
-            plan.lpr = plan.W == 1 && lanes < 152.0 * 1024.0 ? 2 : 1;
-            plan.prefetch = plan.lpr == 2 ? 0 : 4;
+        const double lanes = (double)a.nsrc * (a.ray_end - a.ray_begin) * ((a.n_freq + plan.W - 1) / plan.W);
+        plan.prefetch = 4;
+        plan.tile = 0;
+        if (plan.W == 1 && lanes < 152.0 * 1024.0) {
+            plan.lpr = 2;
+        } else if (plan.W == 1 && acc_mode_for(g, plan, a, ns) == 0) {   // FP32 sums: tiles
+            plan.prefetch = 1;
+            plan.tile = 1;
         }
     }
     if (det) {   // deterministic mode: corner slots, one lane per ray (validated at creation)
@@ -656,8 +655,11 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (g->opt.plan_prefetch) plan.prefetch = g->opt.plan_prefetch - 1;
     if (g->opt.plan_lanes) plan.lpr = g->opt.plan_lanes;
     if (g->opt.plan_tile) plan.tile = g->opt.plan_tile - 1;
-    if (plan.lpr != 1 && (plan.lpr != 2 || plan.prefetch))
-        return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 1, or 2 with gathers mode 0");
+    // a pinned gathers mode or tile that two lanes per ray do not have: one lane (unless pinned)
+    if (!g->opt.plan_lanes && plan.lpr == 2 && ((plan.prefetch != 0 && plan.prefetch != 4) || plan.tile))
+        plan.lpr = 1;
+    if (plan.lpr != 1 && (plan.lpr != 2 || (plan.prefetch != 0 && plan.prefetch != 4)))
+        return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 1, or 2 with gathers mode 0 or 4");
     g->last_plan_ms = -1.0f;
     if (g->opt.autotune && !det && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
     if (a.st_I && plan.lpr > 1) {   // the stateful march runs one lane per (ray, source, bin group)
@@ -665,9 +667,9 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         plan.prefetch = 0;
     }
     // record the reverse march's checkpoints with the adjoint's bin grouping: gathers mode 0 with
-    // one lane per ray, or for one bin per thread two lanes per ray (measured on GB300, 64^3 with
-    // 24,576 lanes: 0.12 ms against 0.16 for mode 3, 0.16 for mode 1 and 0.24 for mode 0 with one
-    // lane), unless a plan with gathers mode 0, 1 or 3 was pinned or tuned
+    // one lane per ray, or for one bin per thread two lanes per ray with gathers mode 4 (measured
+    // on GB300, 64^3 with 24,576 lanes: 0.087 ms against 0.12 for two lanes with mode 0, 0.155 for
+    // mode 3 and 0.17 for mode 1 with one lane), unless a plan was pinned or tuned
     bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
     if (record) {
         const int w = pick_width(a.n_freq);
@@ -676,13 +678,18 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
             plan.block = 32;
             plan.tile = 0;
             plan.lpr = w == 1 && !det ? 2 : 1;
+            if (plan.lpr == 2) plan.prefetch = 4;
         }
         plan.W = w;
-        if (plan.lpr == 2 || w != 1) plan.prefetch = 0;   // corner slots
-        else if (plan.prefetch == 2) plan.prefetch = 3;   // (recording has no gathers mode 2)
+        if (w != 1) plan.prefetch = 0;                               // corner slots
+        else if (plan.lpr == 2) plan.prefetch = plan.prefetch == 4 ? 4 : 0;
+        else if (plan.prefetch == 2) plan.prefetch = 3;              // (recording has no gathers mode 2)
     }
     const int acc = acc_mode_for(g, plan, a, ns);
     if (acc != 0) plan.tile = 0;
+    // a default tile that the (pinned) gathers mode has no kernel for is dropped
+    if (plan.tile && !g->opt.plan_tile && !rt::march_fwd_available(plan.W, plan.prefetch, acc, 1, record, plan.lpr, plan.block))
+        plan.tile = 0;
     // a plan that this accumulation has no kernel for falls back to corner slots (every mode has
     // them); recording stays off where no recording kernel exists (the reverse march then makes
     // its own forward sweep)

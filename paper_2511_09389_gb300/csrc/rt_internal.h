@@ -74,7 +74,7 @@ struct MarchPlan {
 };
 // The plans the autotuners time for n_freq bins (rt_api.cu for single calls, rt_batch.cu for the
 // batch's dedicated instances), at most kMaxMarchPlans; returns how many were written to out.
-constexpr int kMaxMarchPlans = 120;
+constexpr int kMaxMarchPlans = 132;
 int march_plan_candidates(int n_freq, MarchPlan* out);
 
 // [n_freq][ncell] -> [groups][ncell][W] (bins >= n_freq padded with zero).

@@ -222,7 +222,8 @@ def test_deterministic_mode_full_size(torch_cuda):
                                   (1, 32, 0, 1), (4, 32, 0, 1, 1), (2, 128, 1, 1, 1), (1, 64, 1, 1, 1),
                                   (1, 32, 2, 1, 1), (1, 256, 0, 1, 1), (1, 64, 1, 1, 0), (4, 32, 3, 1),
                                   (2, 64, 3, 1, 0), (1, 64, 3, 1, 1), (4, 64, 3, 1, 1),
-                                  (4, 32, 4, 1), (2, 64, 4, 1), (1, 128, 4, 1)])
+                                  (4, 32, 4, 1), (2, 64, 4, 1), (1, 128, 4, 1),
+                                  (4, 64, 4, 2), (4, 32, 4, 2), (2, 32, 4, 2), (1, 128, 4, 2)])
 def test_every_launch_plan_meets_parity(torch_cuda, plan):
     """Each launch plan the autotuner may pick (bins per group, block, prefetch, lanes per ray,
     source deposit tiles) on a ragged multi-bin problem."""
@@ -256,7 +257,7 @@ def test_source_tiles_with_clustered_and_face_sources(torch_cuda, plan):
 
 @pytest.mark.parametrize("step_size", [0.13, 0.5, 1.0, 1.7, 3.2])
 @pytest.mark.parametrize("plan", [(4, 32, 0), (1, 64, 0, 1, 1), (2, 32, 0, 1, 0), (4, 64, 3), (4, 32, 0, 2), (1, 64, 0, 2),
-                                  (4, 32, 4), (1, 64, 4), (2, 32, 4)])
+                                  (4, 32, 4), (1, 64, 4, 1), (2, 32, 4), (4, 32, 4, 2), (1, 64, 4, 2)])
 def test_corner_slots_across_step_sizes(torch_cuda, plan, step_size):
     """Gathers mode 0 keeps a face shared by consecutive corner sets (a step of one cell along an
     axis) and flushes everything else. Steps much shorter than a cell (long runs in one set), of
@@ -277,7 +278,8 @@ def test_corner_slots_across_step_sizes(torch_cuda, plan, step_size):
     ("auto", (4, 32, 0, 1), 40, "fixed"), ("auto", None, 4, "fp32"), ("auto", (4, 32, 0, 1), 4, "fp32"),
     ("fp32", (1, 64, 0, 2), 40, "fp32"), ("fp32", None, 40, "fp32"), ("fp64", None, 4, "fp64"),
     ("fp64", (1, 32, 0, 1), 4, "fp64"), ("fp64", (4, 32, 0, 1), 4, "fp64"), ("fp64", (2, 64, 0, 1), 4, "fp64"),
-    ("fp64", (1, 64, 1, 1, 1), 4, "fp64"), ("fixed", (4, 64, 0, 1), 4, "fixed"), ("fixed", (1, 64, 0, 2), 4, "fixed")])
+    ("fp64", (1, 64, 1, 1, 1), 4, "fp64"), ("fixed", (4, 64, 0, 1), 4, "fixed"), ("fixed", (1, 64, 0, 2), 4, "fixed"),
+    ("fixed", (4, 64, 4, 2), 4, "fixed"), ("auto", (1, 64, 4, 2), 40, "fixed"), ("fp32", (4, 32, 4, 2), 40, "fp32")])
 def test_accumulation_modes_meet_parity(torch_cuda, accumulation, plan, n_src, expect):
     """rt_options.accumulation on a ragged problem with sources on and outside the faces: FP32, FP64
     and 64-bit fixed-point sums all meet the bar against the oracle. The automatic mode sums in
@@ -341,3 +343,21 @@ def test_gathers_ahead_sums_equal_corner_slots(torch_cuda, width, shape, step_si
          for mode in (0, 4)]
     assert np.array_equal(F[0].view(np.uint32), F[1].view(np.uint32))
     assert_parity(F[1], run_oracle(p))
+
+
+@pytest.mark.parametrize("shape,step_size", [((17, 13, 21), 0.5), ((9, 1, 12), 1.7), ((14, 11, 17), 0.13),
+                                             ((14, 11, 17), 3.2)])
+def test_pair_gathers_ahead_sums_equal_pair_slots(torch_cuda, shape, step_size):
+    """Two lanes per ray with gathers mode 4 flush the same per-lane slot sums at the same points
+    as two lanes per ray with corner slots (mode 0): one bin summed in fixed point gives bitwise
+    equal fields; four bins per lane meet the oracle (short steps, steps over a cell, a box with a
+    single-cell axis)."""
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.random_small(97, shape=shape, n_freq=1, n_src=4, num_rays=201, step_size=step_size, horizon=14.0)
+    F = [run_gpu(torch_cuda, p, grid=Grid(p.shape, 8, plan=(1, 64, mode, 2), accumulation="fixed"))
+         for mode in (0, 4)]
+    assert np.array_equal(F[0].view(np.uint32), F[1].view(np.uint32))
+    assert_parity(F[1], run_oracle(p))
+    p = inputs.random_small(98, shape=shape, n_freq=4, n_src=4, num_rays=201, step_size=step_size, horizon=14.0)
+    assert_parity(run_gpu(torch_cuda, p, grid=Grid(p.shape, 8, plan=(4, 64, 4, 2), accumulation="fixed")),
+                  run_oracle(p))
