@@ -449,6 +449,14 @@ rt_status rt_sync_status(void* cuda_stream);
 rt_status rt_microbench(int kind, int vec, void* buf, long long buf_bytes, int edge, int iters, float* ms,
                         double* ops);
 
+/* The attenuation factor exp(-x) exactly as every march kernel computes it (2^(-x log2 e) on
+   the device's base-2 exponential, subnormal results flushed to zero), for n device values:
+   y[i] = exp(-x[i]). x and y are device arrays of n floats (caller-owned, may not overlap
+   partially; y = x is allowed), enqueued on `stream` (NULL: legacy default stream), no
+   synchronisation. For checking the factor's accuracy. Errors: RT_ERR_INVALID_ARG for n < 0 or
+   a NULL array with n > 0; RT_ERR_CUDA if the launch fails. */
+rt_status rt_neg_exp(const float* x, float* y, long long n, void* stream);
+
 /* Launch plan of the last forward call on this handle: bin-group width (1, 2 or 4 bins per
    group), threads per block, gather mode (0: reuse, 1: ahead, 2: both), lanes per ray, source
    deposit tiles (0 / 1), and the march time the autotuner measured for it in ms (-1 when

@@ -25,7 +25,7 @@ EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error"
            "rt_batch_destroy", "rt_c32_from_f32", "rt_c32_to_f32", "rt_conv3d_pack_weights",
            "rt_conv3d_forward", "rt_device_status", "rt_conv3d_weight_grad",
            "rt_surrogate_features", "rt_field_max", "rt_log_field_loss", "rt_field_error", "rt_c32_channel_mean",
-           "rt_adam_step", "rt_microbench", "rt_advance_batch", "rt_sync_status")
+           "rt_adam_step", "rt_microbench", "rt_neg_exp", "rt_advance_batch", "rt_sync_status")
 
 
 class RTError(RuntimeError):
@@ -149,6 +149,8 @@ def load(path: str = LIB_PATH):
         lib.rt_microbench.argtypes = [i, i, vp, ll, i, i, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_double)]
         lib.rt_microbench.restype = i
+        lib.rt_neg_exp.argtypes = [fp, fp, ll, vp]
+        lib.rt_neg_exp.restype = i
         lib.rt_advance_batch.argtypes = [vp, vp, i, vp]
         lib.rt_advance_batch.restype = i
         lib.rt_sync_status.argtypes = [vp]

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256, 2) k_march_batch(const BatchInst* __restr
             L.jg = B.jp + off;
             L.kg = B.kp + off;
             L.og = B.acc + off;
+            L.pol = red_policy(4LL * B.groups * ncell * W);
             L.n = B.dirs[r];
             L.sx = B.src[3 * item.y + 0]; L.sy = B.src[3 * item.y + 1]; L.sz = B.src[3 * item.y + 2];
             L.n0 = B.n0; L.n1 = B.n1; L.n2 = B.n2;

@@ -46,6 +46,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     const float* __restrict__ Gg = a.grad + (size_t)g * ncell * W;
     float* __restrict__ djg = a.dj ? a.dj + (size_t)g * ncell * W : nullptr;
     float* __restrict__ dkg = a.dk ? a.dk + (size_t)g * ncell * W : nullptr;
+    // dL/dj and dL/dkappa together: kept in L2 while they fit (red_policy)
+    const int bwd_groups = (a.n_freq + W - 1) / W;
+    const unsigned long long pol = red_policy(8LL * bwd_groups * ncell * W);
 
     const float4 n = a.dirs[r];
     const float ds = a.ds;
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
                 if (sm.cell[0] != pc[0] || sm.cell[7] != pc[7]) {
                     if (pc[0] >= 0) {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c]);
+                        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c], pol);
                     }
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
             }
             if (dkg) {
                 if (sm.nn != pnn) {
-                    if (pnn >= 0) red_vec<W>(dkg, pnn, pdk);
+                    if (pnn >= 0) red_vec<W>(dkg, pnn, pdk, pol);
                     pnn = sm.nn;
 #pragma unroll
                     for (int b = 0; b < W; ++b) pdk[b] = ddk[b];
@@ -262,9 +265,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     }
     if (djg && pc[0] >= 0) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c]);
+        for (int c = 0; c < 8; ++c) red_vec<W>(djg, pc[c], pdj[c], pol);
     }
-    if (dkg && pnn >= 0) red_vec<W>(dkg, pnn, pdk);
+    if (dkg && pnn >= 0) red_vec<W>(dkg, pnn, pdk, pol);
     }   // r < ray_count
     if (SG) {
         // every thread of the block reaches here (blocks are whole warps; lanes past the last ray

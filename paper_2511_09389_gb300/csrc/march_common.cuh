@@ -85,13 +85,21 @@ __device__ __forceinline__ constexpr int tile_offset(int c) {
     return ((c >> 2) & 1) * kTile * kTile + ((c >> 1) & 1) * kTile + (c & 1);
 }
 
-// exp(-x) for the march's attenuation factors (x = kappa ds >= 0, or tau >= 0): CUDA's fast
-// exponential intrinsic, a few ulp in FP32 for the arguments of the march (its error grows
-// with |x|, where exp(-x) itself is negligible), far inside the relative 1e-5 the march is held
-// to against the FP64 oracle, at a fraction of the instructions of expf. Every kernel of the
-// library (forward, adjoint replay, batch) uses this one function, so a replayed march repeats
-// the forward's intensities exactly.
-__device__ __forceinline__ float neg_exp(float x) { return __expf(-x); }
+// exp(-x) for the march's attenuation factors (x = kappa ds >= 0, or tau >= 0), from the
+// identity exp(-x) = 2^(-x log2(e)): one FP32 multiply by the constant log2(e) and the PTX
+// base-2 exponential ex2.approx.ftz.f32 (results below the smallest normal FP32 number, i.e.
+// x > 87.3, flush to zero, far below any deposit that matters). Its relative error is a few
+// ulp plus the rounding of the product, which grows with x: about |x| log2(e) ln(2) 2^-24 --
+// checked against FP64 exp in the tests through rt_neg_exp, and far inside the relative 1e-5
+// the march is held to against the FP64 oracle. Every kernel of the library (forward, adjoint
+// replay, batch) uses this one function, so a replayed march repeats the forward's intensities
+// exactly.
+__device__ __forceinline__ float neg_exp(float x) {
+    constexpr float kLog2e = 1.4426950408889634f;   // log2(e)
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * -kLog2e));
+    return r;
+}
 
 // ---- W-wide bin vectors -----------------------------------------------------------------
 template <int W> struct Vec;
@@ -144,51 +152,71 @@ __device__ __forceinline__ void ldg_vec_if<4>(bool p, const float* __restrict__ 
 // Fire-and-forget global reductions (no return value): one L2 atomic per W-vector. They carry
 // no "memory" clobber: the accumulators they target are never read by the kernels that issue
 // them, so loads of the read-only inputs may be scheduled across them; kernel completion
-// orders them before any later reader.
-__device__ __forceinline__ void red_add(float* p, float a) {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a));
+// orders them before any later reader. Each carries an L2 eviction policy (red_policy).
+//
+// An accumulator that fits in L2 with room for the packed inputs beside it (at most 64 MiB of
+// the 126 MB L2) is marked evict-last, so the reductions keep finding its lines there while the
+// gathers stream the inputs through; a larger one is marked evict-normal (measured on GB300, 4
+// bins on 128^3 with 16 sources, a 32 MiB accumulator: 3 % less march time with evict-last).
+constexpr long long kL2KeepBytes = 64ll << 20;
+__device__ __forceinline__ unsigned long long red_policy(long long acc_bytes) {
+    unsigned long long p;
+    if (acc_bytes <= kL2KeepBytes)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
-__device__ __forceinline__ void red_add2(float* p, float a, float b) {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b));
+
+__device__ __forceinline__ void red_add(float* p, float a, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(a), "l"(pol));
 }
-__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-                 "f"(d));
+__device__ __forceinline__ void red_add2(float* p, float a, float b, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(a), "f"(b), "l"(pol));
+}
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a), "f"(b),
+                 "f"(c), "f"(d), "l"(pol));
 }
 
 template <int W>
-__device__ __forceinline__ void red_vec(float* __restrict__ base, int cell, const float* v);
+__device__ __forceinline__ void red_vec(float* __restrict__ base, int cell, const float* v, unsigned long long pol);
 template <>
-__device__ __forceinline__ void red_vec<1>(float* __restrict__ base, int cell, const float* v) {
-    red_add(base + cell, v[0]);
+__device__ __forceinline__ void red_vec<1>(float* __restrict__ base, int cell, const float* v, unsigned long long pol) {
+    red_add(base + cell, v[0], pol);
 }
 template <>
-__device__ __forceinline__ void red_vec<2>(float* __restrict__ base, int cell, const float* v) {
-    red_add2(base + 2 * (size_t)cell, v[0], v[1]);
+__device__ __forceinline__ void red_vec<2>(float* __restrict__ base, int cell, const float* v, unsigned long long pol) {
+    red_add2(base + 2 * (size_t)cell, v[0], v[1], pol);
 }
 template <>
-__device__ __forceinline__ void red_vec<4>(float* __restrict__ base, int cell, const float* v) {
-    red_add4(base + 4 * (size_t)cell, v[0], v[1], v[2], v[3]);
+__device__ __forceinline__ void red_vec<4>(float* __restrict__ base, int cell, const float* v, unsigned long long pol) {
+    red_add4(base + 4 * (size_t)cell, v[0], v[1], v[2], v[3], pol);
 }
 
-// Predicated form (no branch): the reduction happens only when p is true; the index must be a
-// valid cell either way (callers clamp it), so no address outside the grid is formed.
+// Predicated form: the reduction happens only when p is true; the index must be a valid cell
+// either way (callers clamp it), so no address outside the grid is formed. (The compiler still
+// places each predicated reduction in a short branch of its own.)
 template <int W>
-__device__ __forceinline__ void red_vec_if(bool p, float* __restrict__ base, int cell, const float* v);
+__device__ __forceinline__ void red_vec_if(bool p, float* __restrict__ base, int cell, const float* v,
+                                           unsigned long long pol);
 template <>
-__device__ __forceinline__ void red_vec_if<1>(bool p, float* __restrict__ base, int cell, const float* v) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f32 [%1], %2;\n\t}"
-                 ::"r"((int)p), "l"(base + cell), "f"(v[0]));
+__device__ __forceinline__ void red_vec_if<1>(bool p, float* __restrict__ base, int cell, const float* v,
+                                              unsigned long long pol) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.L2::cache_hint.f32 [%1], %2, %3;\n\t}"
+                 ::"r"((int)p), "l"(base + cell), "f"(v[0]), "l"(pol));
 }
 template <>
-__device__ __forceinline__ void red_vec_if<2>(bool p, float* __restrict__ base, int cell, const float* v) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.v2.f32 [%1], {%2, %3};\n\t}"
-                 ::"r"((int)p), "l"(base + 2 * (size_t)cell), "f"(v[0]), "f"(v[1]));
+__device__ __forceinline__ void red_vec_if<2>(bool p, float* __restrict__ base, int cell, const float* v,
+                                              unsigned long long pol) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.L2::cache_hint.v2.f32 [%1], {%2, %3}, %4;\n\t}"
+                 ::"r"((int)p), "l"(base + 2 * (size_t)cell), "f"(v[0]), "f"(v[1]), "l"(pol));
 }
 template <>
-__device__ __forceinline__ void red_vec_if<4>(bool p, float* __restrict__ base, int cell, const float* v) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
-                 ::"r"((int)p), "l"(base + 4 * (size_t)cell), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
+__device__ __forceinline__ void red_vec_if<4>(bool p, float* __restrict__ base, int cell, const float* v,
+                                              unsigned long long pol) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.L2::cache_hint.v4.f32 [%1], {%2, %3, %4, %5}, %6;\n\t}"
+                 ::"r"((int)p), "l"(base + 4 * (size_t)cell), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "l"(pol));
 }
 
 // FP64 reductions for the wide accumulation mode. The deposit is an FP32 number; it is widened

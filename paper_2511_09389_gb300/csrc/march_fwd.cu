@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF
     L.jg = a.jp + (size_t)g * ncell * W;
     L.kg = a.kp + (size_t)g * ncell * W;
     L.og = og;
+    L.pol = red_policy(4LL * a.groups * ncell * W);
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF
             if (any) {
                 const int u0 = i / (kTile * kTile), u1 = (i / kTile) % kTile, u2 = i % kTile;
                 const int cell = ((to0 + u0) * a.n1 + (to1 + u1)) * a.n2 + (to2 + u2);
-                red_vec<W>(og, cell, v);
+                red_vec<W>(og, cell, v, red_policy(4LL * a.groups * a.n0 * a.n1 * a.n2 * W));
             }
         }
     }
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     L.jg = a.jp + (size_t)g * ncell * W;
     L.kg = a.kp + (size_t)g * ncell * W;
     L.og = a.acc + (size_t)g * ncell * W;
+    L.pol = red_policy(4LL * a.groups * ncell * W);
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;

@@ -51,6 +51,7 @@ struct Lane {
     float ds;
     float scale;              // factor of every deposit
     int kappa_mode;
+    unsigned long long pol = 0;   // L2 policy of the FP32 field reductions (red_policy)
     float* tile = nullptr;    // the block's shared-memory deposit tile ([kTile^3][W]) or NULL
     int to0 = 0, to1 = 0, to2 = 0;   // its origin cell
     // REC: adjoint checkpoints written during the march, in the reverse march's layout: the
@@ -91,7 +92,7 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
             if (b < L.nbins)
                 red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * f));
     } else {
-        red_vec<W>(L.og, cell, v);
+        red_vec<W>(L.og, cell, v, L.pol);
     }
 }
 
@@ -109,7 +110,7 @@ __device__ __forceinline__ void flush_if(bool p, const Lane& L, int cell, const 
             red_add_u64_if(p && b < L.nbins, L.og64 + (size_t)cell * W + b,
                            (unsigned long long)__float2ll_rn(v[b] * f));
     } else {
-        red_vec_if<W>(p, L.og, cell, v);
+        red_vec_if<W>(p, L.og, cell, v, L.pol);
     }
 }
 

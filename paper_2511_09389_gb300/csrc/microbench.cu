@@ -9,9 +9,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "march_common.cuh"
 #include "rt_internal.h"
 
 namespace rt {
+
+// The march's attenuation factor exp(-x) (neg_exp), element by element, so its accuracy can be
+// checked against a reference exponential.
+__global__ void k_neg_exp(const float* __restrict__ x, float* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = neg_exp(x[i]);
+}
 
 namespace {
 
@@ -187,4 +195,13 @@ extern "C" rt_status rt_microbench(int kind, int vec, void* buf, long long buf_b
     if (e != cudaSuccess) return rt::set_error(RT_ERR_CUDA, cudaGetErrorString(e));
     *ops = (double)grid * block * iters * (stencil ? 8.0 : 1.0);
     return RT_OK;
+}
+
+extern "C" rt_status rt_neg_exp(const float* x, float* y, long long n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return rt::set_error(RT_ERR_INVALID_ARG, "rt_neg_exp: need n >= 0 and device x, y");
+    if (n == 0) return RT_OK;
+    const long long blocks = (n + 255) / 256;
+    rt::k_neg_exp<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RT_OK : rt::set_error(RT_ERR_CUDA, cudaGetErrorString(e));
 }

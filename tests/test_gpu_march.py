@@ -361,3 +361,33 @@ def test_pair_gathers_ahead_sums_equal_pair_slots(torch_cuda, shape, step_size):
     p = inputs.random_small(98, shape=shape, n_freq=4, n_src=4, num_rays=201, step_size=step_size, horizon=14.0)
     assert_parity(run_gpu(torch_cuda, p, grid=Grid(p.shape, 8, plan=(4, 64, 4, 2), accumulation="fixed")),
                   run_oracle(p))
+
+
+def test_attenuation_factor_accuracy(torch_cuda):
+    """exp(-x) as every march kernel computes it (rt_neg_exp: 2^(-x log2 e)) against FP64 exp:
+    the relative error is at most 2^-21 (the base-2 exponential) plus 1.25 |x| 2^-24 wherever
+    exp(-x) is a normal FP32 number (x <= 87); beyond that the factor is flushed to zero. The
+    second term: the FP32 product y = x log2 e carries the rounding of the product (at most
+    |y| 2^-24) and of the constant (FP32 log2 e is off by a relative 1.3e-8 = 0.23 x 2^-24), and
+    2^y turns an error e in y into a relative error ln(2) e, with ln(2) log2(e) = 1."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300 import _native
+    lib = _native.load()
+    gen = torch.Generator().manual_seed(5)
+    x = torch.cat([torch.linspace(0.0, 87.0, 400001, dtype=torch.float64),
+                   torch.rand(200000, generator=gen, dtype=torch.float64) * 4.0,
+                   torch.tensor([0.0, 1e-30, 1e-7, 0.5, 1.0, 88.0, 100.0, 1e4], dtype=torch.float64)]).float()
+    xd = x.cuda()
+    yd = torch.empty_like(xd)
+    assert lib.rt_neg_exp(xd.data_ptr(), yd.data_ptr(), xd.numel(), None) == 0
+    torch.cuda.synchronize()
+    y, xx = yd.cpu().double(), x.double()
+    ref = torch.exp(-xx)
+    normal = xx <= 87.0
+    rel = (y[normal] - ref[normal]).abs() / ref[normal]
+    bound = 2.0 ** -21 + 1.25 * xx[normal] * 2.0 ** -24
+    print(f"neg_exp: max relative error / bound {float((rel / bound).max()):.3f}, "
+          f"max relative error {float(rel.max()):.2e}")
+    assert bool((rel <= bound).all())
+    assert bool((y[xx >= 88.0] == 0).all())
+    assert lib.rt_neg_exp(xd.data_ptr(), yd.data_ptr(), -1, None) == 1
