@@ -99,8 +99,10 @@ typedef struct {
                            synchronises the stream (one pass over the inputs). 0: no scan. */
     int record_checkpoints; /* 1: every full-range rt_advance also stores the reverse march's
                            checkpoints (every ckpt_stride substeps) in the handle, marching
-                           with the adjoint's bin grouping (gathers mode 0; for one bin, two
-                           lanes per ray unless a plan is pinned or tuned); a following
+                           with the adjoint's bin grouping (one bin: two lanes per ray with
+                           gathers mode 4; wider groups: gathers mode 0; unless a plan is
+                           pinned; with autotune = 1 the fastest plan that records, timed with
+                           its checkpoint stores, tuned apart from non-recording calls); a following
                            rt_backward / rt_backward_sources with the same j_map, kappa_map and
                            source_pos pointers and the same scalars uses them instead of
                            repeating the forward sweep -- but only if a 64-bit content hash of
@@ -263,6 +265,27 @@ rt_status rt_backward_sources(rt_grid* grid, const float* grad_out, const float*
                               int num_rays, float step_size, float radiation_velocity, float time_step,
                               int n_freq, float* grad_j, float* grad_kappa, float* grad_src,
                               void* cuda_stream);
+
+/* Emissivity inversion (Sec. 4, gradient-based inversion, with every voxel of j free instead of
+   one amplitude): starting from the j in j_map, `iterations` projected Adam steps (beta1 0.9,
+   beta2 0.999, epsilon 1e-8, learning rate lr; after each step j = max(j, 0)) on
+       L(j) = mean over the n_freq * n0 n1 n2 values of (log(F(j) + eps) - log(target + eps))^2,
+       eps = eps_rel * max(target),
+   where F(j) = rt_advance(j, kappa_map, source_pos, ...) with this call's scalars and dL/dj comes
+   from rt_backward. target, kappa_map, j_map: device [n_freq][n0][n1][n2] (target >= 0, the
+   field to match); j_map is overwritten with the recovered j. losses: device float
+   [iterations + 1], overwritten: losses[i] = L before step i + 1, losses[iterations] = L of the
+   result. Everything is enqueued on cuda_stream (NULL: legacy default stream) with no host
+   synchronisation after the grid's first call of this shape class (autotuning, when on, times
+   its plans then); a grid created with record_checkpoints = 1 lets each reverse march reuse the
+   forward's checkpoints. Workspace: 6 n floats held by the grid. Errors: RT_ERR_INVALID_ARG for
+   a NULL array, iterations < 0, lr or eps_rel not finite and positive, n_freq outside
+   [1, max_freq], j_map aliasing an input or losses overlapping an array, and whatever
+   rt_advance / rt_backward return for the problem's arguments. */
+rt_status rt_invert_emissivity(rt_grid* grid, const float* target, const float* kappa_map,
+                               const float* source_pos, int num_sources, int num_rays, float step_size,
+                               float radiation_velocity, float time_step, int n_freq, int iterations,
+                               float lr, float eps_rel, float* j_map, float* losses, void* cuda_stream);
 
 /* Duration in ms of the march kernel(s) of the last rt_advance / rt_backward call on this
    handle (forward: the march kernel only, without packing or zeroing; backward: the adjoint

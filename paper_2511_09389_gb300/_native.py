@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ER
 # every symbol include/raytrax.h declares
 EXPORTS = ("rt_default_options", "rt_create_grid", "rt_destroy", "rt_last_error", "rt_num_substeps",
            "rt_direction_table", "rt_advance", "rt_advance_rays", "rt_advance_continue", "rt_advance_host",
-           "rt_advance_host_async", "rt_host_wait", "rt_host_join", "rt_backward", "rt_backward_sources",
+           "rt_advance_host_async", "rt_host_wait", "rt_host_join", "rt_backward", "rt_backward_sources", "rt_invert_emissivity",
            "rt_trace_cells", "rt_kernel_ms", "rt_last_plan",
            "rt_tuning_report", "rt_last_accumulation", "rt_last_ckpt_stride", "rt_shard_plan", "rt_advance_noalloc", "rt_batch_create", "rt_batch_run", "rt_batch_updates",
            "rt_batch_info",
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
         lib.rt_backward.restype = i
         lib.rt_backward_sources.argtypes = [vp, fp, fp, fp, fp, i, i, f, f, f, i, fp, fp, fp, vp]
         lib.rt_backward_sources.restype = i
+        lib.rt_invert_emissivity.argtypes = [vp, fp, fp, fp, i, i, f, f, f, i, i, f, f, fp, fp, vp]
+        lib.rt_invert_emissivity.restype = i
         lib.rt_trace_cells.argtypes = [vp, fp, i, i, f, i, llp, llp]
         lib.rt_trace_cells.restype = i
         lib.rt_shard_plan.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]

@@ -261,6 +261,26 @@ class Grid:
         check(st)
         return (gj, gk, gs) if need_sources else (gj, gk)
 
+    def invert_emissivity(self, target, kappa, sources, num_rays: int, step_size: float,
+                          radiation_velocity: float = 1.0, time_step: float = 1.0, *, iterations: int = 200,
+                          lr: float = 1e-2, eps_rel: float = 1e-2, j=None, stream=None):
+        """rt_invert_emissivity: `iterations` projected Adam steps on the log-field misfit to
+        `target`, from j (default zero). Returns (the recovered j, the device tensor of the
+        iterations + 1 losses); nothing is synchronised."""
+        t = _grid_tensor(target, "target")
+        j = torch.zeros_like(t) if j is None else _grid_tensor(j, "j").clone()
+        j, kappa, src = self._inputs(j, kappa, sources)
+        if t.shape != j.shape:
+            raise ValueError("target must be shaped like kappa")
+        losses = torch.empty(int(iterations) + 1, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            check(self._lib.rt_invert_emissivity(self._h, t.data_ptr(), kappa.data_ptr(), src.data_ptr(), src.shape[0],
+                                                 int(num_rays), float(step_size), float(radiation_velocity),
+                                                 float(time_step), j.shape[0], int(iterations), float(lr),
+                                                 float(eps_rel), j.data_ptr(), losses.data_ptr(),
+                                                 _stream_ptr(stream, self.device)))
+        return j, losses
+
     def kernel_ms(self) -> float:
         """Duration of the last call's march kernel (needs profile=True)."""
         ms = ctypes.c_float()

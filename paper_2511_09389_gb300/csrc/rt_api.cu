@@ -134,7 +134,7 @@ struct rt_grid {
     std::vector<DirTable> dirs;
     // scratch slots
     enum Slot { JP, KP, ACC, ACC64, HJ, HK, HOUT, HSRC, TRACE, CKPT, GP, DJ, DK, DETS, STPOS, STI, STTAU, CHK,
-                AJ0, AK0, AOUT0, ASRC0, AJ1, AK1, AOUT1, ASRC1, HASH, NSLOT };
+                AJ0, AK0, AOUT0, ASRC0, AJ1, AK1, AOUT1, ASRC1, HASH, INV, NSLOT };
     void* buf[NSLOT] = {};
     size_t cap[NSLOT] = {};
     // profiling events around the last march kernel
@@ -143,8 +143,9 @@ struct rt_grid {
     // autotuning cache: shape class -> fastest launch plan
     struct TuneKey {
         int n_freq, nsrc, rays, ns;
+        int rec = 0;   // forward plans: tuned for a recording call (checkpoint stores included)
         bool operator==(const TuneKey& o) const {
-            return n_freq == o.n_freq && nsrc == o.nsrc && rays == o.rays && ns == o.ns;
+            return n_freq == o.n_freq && nsrc == o.nsrc && rays == o.rays && ns == o.ns && rec == o.rec;
         }
     };
     std::vector<std::pair<TuneKey, std::pair<Plan, float>>> tuned;
@@ -518,9 +519,12 @@ size_t acc_bytes(const rt_grid* g, const Call& a, const Plan& plan) {
 }
 
 // Autotuner: on the first call of a shape class, time every candidate plan's march kernel on
-// the call's own inputs (into scratch; best of two runs each) and keep the fastest.
-rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scale, Plan* best) {
-    const rt_grid::TuneKey key{a.n_freq, a.nsrc, a.ray_end - a.ray_begin, ns};
+// the call's own inputs (into scratch; best of two runs each) and keep the fastest. A call that
+// records the reverse march's checkpoints is tuned apart, over the plans with a recording kernel
+// at the adjoint's bin grouping, each timed with its checkpoint stores.
+rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scale, Plan* best, bool record) {
+    rt_grid::TuneKey key{a.n_freq, a.nsrc, a.ray_end - a.ray_begin, ns};
+    key.rec = record ? 1 : 0;
     for (const auto& e : g->tuned)
         if (e.first == key) {
             *best = e.second.first;
@@ -548,9 +552,20 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
         if (p.lpr == 1 && p.tile && g->opt.accumulation == 0 && auto_accumulation(g, a, ns) != 0) continue;
         const int acc = acc_mode_for(g, p, a, ns);
         if (acc != 0 && p.lpr == 1 && p.tile) continue;
-        if (!rt::march_fwd_available(W, p.prefetch, acc, p.tile, 0, p.lpr, p.block)) continue;
+        if (record && W != pick_width(a.n_freq)) continue;
+        if (!rt::march_fwd_available(W, p.prefetch, acc, p.tile, record, p.lpr, p.block)) continue;
         rt::MarchArgs m;
         if ((st = prepare(g, a, ns, p, dirs, scale, nullptr, &m)) != RT_OK) break;
+        if (record) {   // the checkpoint stores into the CKPT slot (the call then records anew)
+            rt::BackArgs sz{};
+            sz.ray_count = a.num_rays; sz.nsrc = a.nsrc; sz.n_freq = a.n_freq; sz.ns = ns;
+            sz.stride = ckpt_stride(g, a.n_freq, a.nsrc, a.num_rays, ns);
+            void* ck;
+            g->rec.valid = false;
+            if ((st = g->ensure(rt_grid::CKPT, sizeof(float) * rt::backward_ckpt_floats(sz, W), &ck)) != RT_OK) break;
+            m.ckpt = (float*)ck;
+            m.ck_stride = sz.stride;
+        }
         float cand_ms = 3.0e38f;
         for (int rep = 0; rep < 2; ++rep) {
             if (acc != 0) {
@@ -571,8 +586,9 @@ rt_status tune(rt_grid* g, const Call& a, int ns, const float4* dirs, float scal
         }
         if (st == RT_OK) {
             char line[128];
-            snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d acc=%s %.4f ms\n", W, b,
-                     p.prefetch, p.lpr, p.tile, acc == 2 ? "fp64" : (acc == 1 ? "fixed" : "fp32"), cand_ms);
+            snprintf(line, sizeof line, "W=%d block=%d prefetch=%d lanes=%d tile=%d acc=%s%s %.4f ms\n", W, b,
+                     p.prefetch, p.lpr, p.tile, acc == 2 ? "fp64" : (acc == 1 ? "fixed" : "fp32"),
+                     record ? " recording" : "", cand_ms);
             g->tune_report += line;
         }
     }
@@ -661,7 +677,8 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     if (plan.lpr != 1 && (plan.lpr != 2 || (plan.prefetch != 0 && plan.prefetch != 4)))
         return fail(RT_ERR_INVALID_ARG, "plan_lanes must be 1, or 2 with gathers mode 0 or 4");
     g->last_plan_ms = -1.0f;
-    if (g->opt.autotune && !det && (st = tune(g, a, ns, dirs, scale, &plan)) != RT_OK) return st;
+    bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
+    if (g->opt.autotune && !det && (st = tune(g, a, ns, dirs, scale, &plan, record)) != RT_OK) return st;
     if (a.st_I && plan.lpr > 1) {   // the stateful march runs one lane per (ray, source, bin group)
         plan.lpr = 1;
         plan.prefetch = 0;
@@ -670,7 +687,6 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
     // one lane per ray, or for one bin per thread two lanes per ray with gathers mode 4 (measured
     // on GB300, 64^3 with 24,576 lanes: 0.087 ms against 0.12 for two lanes with mode 0, 0.155 for
     // mode 3 and 0.17 for mode 1 with one lane), unless a plan was pinned or tuned
-    bool record = g->opt.record_checkpoints && !a.st_I && a.ray_begin == 0 && a.ray_end == a.num_rays;
     if (record) {
         const int w = pick_width(a.n_freq);
         const bool keep = plan.W == w && (g->opt.plan_prefetch || g->opt.plan_lanes || g->opt.autotune);
@@ -1280,6 +1296,58 @@ rt_status rt_backward(rt_grid* g, const float* grad_out, const float* j_map, con
                       void* cuda_stream) {
     return backward_impl(g, grad_out, j_map, kappa_map, source_pos, num_sources, num_rays, step_size,
                          radiation_velocity, time_step, n_freq, grad_j, grad_kappa, nullptr, cuda_stream);
+}
+
+// Emissivity inversion (Sec. 4): per iteration one recording rt_advance of j, the log-field
+// misfit and its gradient dL/dF, one rt_backward for dL/dj, and a projected Adam step, all
+// enqueued on the caller's stream. Workspace (INV slot): F, log target, dL/dF, dL/dj, the two
+// Adam moments (n floats each) and the target's maximum.
+rt_status rt_invert_emissivity(rt_grid* g, const float* target, const float* kappa_map, const float* source_pos,
+                               int num_sources, int num_rays, float step_size, float radiation_velocity,
+                               float time_step, int n_freq, int iterations, float lr, float eps_rel, float* j_map,
+                               float* losses, void* cuda_stream) {
+    if (!g) return fail(RT_ERR_INVALID_ARG, "grid handle is NULL");
+    if (!target || !kappa_map || !j_map || !losses) return fail(RT_ERR_INVALID_ARG, "a NULL array");
+    if (iterations < 0 || !(lr > 0.0f) || !std::isfinite(lr) || !(eps_rel > 0.0f) || !std::isfinite(eps_rel))
+        return fail(RT_ERR_INVALID_ARG, "need iterations >= 0, finite lr > 0 and eps_rel > 0");
+    if (n_freq < 1 || n_freq > g->max_freq) return fail(RT_ERR_INVALID_ARG, "n_freq must be in [1, max_freq]");
+    if (j_map == target || j_map == kappa_map || j_map == source_pos)
+        return fail(RT_ERR_INVALID_ARG, "j_map aliases an input");
+    const long long n = (long long)n_freq * g->ncell();
+    const float* lo = losses;
+    for (const float* a : {target, kappa_map, (const float*)j_map})
+        if (lo < a + n && a < lo + iterations + 1) return fail(RT_ERR_INVALID_ARG, "losses overlaps an array");
+    rt_status st = check_device(g);
+    if (st != RT_OK) return st;
+    const cudaStream_t cs = (cudaStream_t)cuda_stream;
+    void* w = nullptr;
+    if ((st = g->ensure(rt_grid::INV, sizeof(float) * (6 * (size_t)n + 4), &w)) != RT_OK) return st;
+    float* F = (float*)w;
+    float* log_t = F + n;
+    float* grad = log_t + n;
+    float* dj = grad + n;
+    float* m = dj + n;
+    float* v = m + n;
+    float* fmax = v + n;
+    RT_CUDA(cudaMemsetAsync(m, 0, sizeof(float) * 2 * (size_t)n, cs), "cudaMemsetAsync(Adam moments)");
+    RT_CUDA(cudaMemsetAsync(losses, 0, sizeof(float) * ((size_t)iterations + 1), cs), "cudaMemsetAsync(losses)");
+    RT_CUDA(rt::launch_field_max(target, 1, n, fmax, cs), "target maximum");
+    RT_CUDA(rt::launch_log_target(target, n, fmax, eps_rel, log_t, cs), "log target");
+    for (int it = 1; it <= iterations; ++it) {
+        if ((st = rt_advance(g, j_map, kappa_map, source_pos, num_sources, num_rays, step_size, radiation_velocity,
+                             time_step, n_freq, F, 0, cuda_stream)) != RT_OK)
+            return st;
+        RT_CUDA(rt::launch_log_misfit(F, log_t, n, fmax, eps_rel, grad, losses + it - 1, cs), "log misfit");
+        if ((st = rt_backward(g, grad, j_map, kappa_map, source_pos, num_sources, num_rays, step_size,
+                              radiation_velocity, time_step, n_freq, dj, nullptr, cuda_stream)) != RT_OK)
+            return st;
+        RT_CUDA(rt::launch_adam_projected(j_map, dj, m, v, n, lr, 0.9f, 0.999f, 1e-8f, it, 0.0f, cs), "Adam step");
+    }
+    if ((st = rt_advance(g, j_map, kappa_map, source_pos, num_sources, num_rays, step_size, radiation_velocity,
+                         time_step, n_freq, F, 0, cuda_stream)) != RT_OK)
+        return st;
+    RT_CUDA(rt::launch_log_misfit(F, log_t, n, fmax, eps_rel, nullptr, losses + iterations, cs), "log misfit");
+    return RT_OK;
 }
 
 rt_status rt_backward_sources(rt_grid* g, const float* grad_out, const float* j_map, const float* kappa_map,

@@ -209,6 +209,17 @@ cudaError_t launch_channel_mean(const void* x, int B, int C, long long vox, floa
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                         float eps, int step, cudaStream_t st);
 
+// Emissivity inversion (inversion.cu). fmax: device scalar, the target's maximum; eps =
+// eps_rel * fmax. log_t = log(target + eps); the misfit writes dL/dF to grad (if non-NULL) and
+// adds mean (log(F + eps) - log_t)^2 to *loss; the Adam step (bias corrections as launch_adam)
+// is followed by p = max(p, lower).
+cudaError_t launch_log_target(const float* target, long long n, const float* fmax, float eps_rel, float* log_t,
+                              cudaStream_t st);
+cudaError_t launch_log_misfit(const float* F, const float* log_t, long long n, const float* fmax, float eps_rel,
+                              float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_adam_projected(float* p, const float* g, float* m, float* v, long long n, float lr, float b1,
+                                  float b2, float eps, int step, float lower, cudaStream_t st);
+
 // FP32 [B][C][vox] <-> C32 bf16 [B][vox][32] (channels >= C are zero), C <= 32.
 cudaError_t launch_to_c32(const float* src, int B, int C, long long vox, void* dst, cudaStream_t st);
 cudaError_t launch_from_c32(const void* src, int B, int C, long long vox, float* dst, cudaStream_t st);

@@ -4,9 +4,10 @@ inversion", generalised from the paper's single amplitude to every voxel of j).
 The loss is the mean squared difference of log fields,
     L(j) = mean_v (log(F(j)_v + eps) - log(F_target_v + eps))^2,   eps = eps_rel * max F_target,
 (the field vanishes past the light-travel horizon, so eps keeps the logarithm finite). F(j) is
-one rt_advance through RTFunction, dL/dj the hand-written reverse march. j starts from zero and
-takes Adam steps (the library's rt_adam_step kernel), each followed by a projection onto j >= 0:
-a negative emissivity would make the field negative where the logarithm is undefined.
+one rt_advance, dL/dj the hand-written reverse march. j starts from zero and takes Adam steps,
+each followed by a projection onto j >= 0: a negative emissivity would make the field negative
+where the logarithm is undefined. The loop runs in the library (rt_invert_emissivity) with no
+host round trip per iteration; log_field_loss is the same loss in torch, for autograd use.
 
 The floor eps defaults to 1e-2 of the target's maximum. At j = 0 the field is zero and the
 gradient of the loss scales as 1/eps; with a floor of 1e-8 of the maximum that first gradient
@@ -22,8 +23,7 @@ import time
 
 import torch
 
-from .api import Grid, adam_step
-from .autograd import RTFunction
+from .api import Grid
 
 
 def log_field_loss(F: torch.Tensor, log_target: torch.Tensor, eps: float) -> torch.Tensor:
@@ -35,34 +35,25 @@ def recover_emissivity(target: torch.Tensor, kappa: torch.Tensor, sources: torch
                        step_size: float, radiation_velocity: float, time_step: float, *, iterations: int = 200,
                        lr: float = 1e-2, eps_rel: float = 1e-2, grid: Grid | None = None, j0=None) -> dict:
     """Recover j (same shape as kappa) whose field matches `target` (the field of the unknown
-    emissivity, same shape) in the log-MSE sense. Returns the recovered j, the loss before every
-    step and after the last, and the wall time of the iterations (synchronised at the end)."""
+    emissivity, same shape) in the log-MSE sense, with the library's native loop
+    (rt_invert_emissivity: every iteration a recording forward march, the fused misfit and its
+    gradient, the reverse march and a projected Adam step on one stream). Returns the recovered
+    j, the loss before every step and after the last, and the wall time of the iterations
+    (synchronised at both ends)."""
     dev = kappa.device
     if grid is None:
         shape = tuple(kappa.shape[-3:])
         nf = 1 if kappa.dim() == 3 else kappa.shape[0]
         grid = Grid(shape, nf, record_checkpoints=True, autotune=True, device=dev)
-    eps = eps_rel * float(target.max())
-    log_t = torch.log(target + eps)
-    j = torch.zeros_like(kappa) if j0 is None else j0.detach().clone().float()
-    m, v = torch.zeros_like(j), torch.zeros_like(j)
-    losses = []
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for it in range(1, iterations + 1):
-        jv = j.detach().requires_grad_(True)
-        F = RTFunction.apply(jv, kappa, sources, num_rays, step_size, radiation_velocity, time_step, grid)
-        loss = log_field_loss(F, log_t, eps)
-        loss.backward()
-        losses.append(loss.detach())
-        adam_step(j, jv.grad, m, v, lr=lr, step=it)
-        j.clamp_(min=0.0)
-    with torch.no_grad():
-        F = RTFunction.apply(j, kappa, sources, num_rays, step_size, radiation_velocity, time_step, grid)
-        losses.append(log_field_loss(F, log_t, eps))
+    j, losses = grid.invert_emissivity(target, kappa, sources, num_rays, step_size, radiation_velocity, time_step,
+                                       iterations=iterations, lr=lr, eps_rel=eps_rel, j=j0)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
-    return {"j": j, "losses": [float(x) for x in torch.stack(losses).cpu()], "wall_s": wall,
+    if kappa.dim() == 3:
+        j = j[0]
+    return {"j": j, "losses": [float(x) for x in losses.cpu()], "wall_s": wall,
             "iterations": iterations, "ckpt_stride": grid.last_ckpt_stride()}
 
 

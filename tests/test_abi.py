@@ -98,3 +98,12 @@ def test_deterministic_rejects_plans_it_cannot_run(lib, field, value):
     assert lib.rt_create_grid(ctypes.byref(h), 8, 8, 8, 1, ctypes.byref(opt)) == 1
     assert b"deterministic" in lib.rt_last_error()
     assert not h.value
+
+
+
+def test_invert_emissivity_rejects_a_null_grid(lib):
+    """rt_invert_emissivity checks the handle on the host before any device call (the other
+    argument checks need a device grid: tests/test_gpu_adjoint.py)."""
+    assert lib.rt_invert_emissivity(None, None, None, None, 1, 8, 0.5, 1.0, 1.0, 1, 1, 1e-2, 1e-2, None, None,
+                                    None) == 1
+    assert b"grid" in lib.rt_last_error()

@@ -380,3 +380,77 @@ def test_emissivity_inversion_reduced_size(torch_cuda):
     assert L[-1] < 0.05 * L[0]
     assert corr > 0.5          # FP64 oracle, same settings: loss x 7e-3, correlation 0.74
     assert float(res["j"].min()) >= 0.0
+
+
+def test_native_inversion_loop_matches_autograd_loop(torch_cuda):
+    """rt_invert_emissivity (the loop in the library: recording forward, fused log misfit and its
+    gradient, reverse march, Adam with the projection fused) against the same iterations written
+    with torch autograd: RTFunction for the march, the loss in torch ops, rt_adam_step, clamp.
+    Both sum their deposits with FP32 atomics in run-dependent order, so losses and the recovered
+    j agree to rounding-level tolerances, not bitwise. Also: the loss history has iterations + 1
+    entries, j stays >= 0, and zero iterations return the start's loss and leave j unchanged."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300 import inversion
+    from paper_2511_09389_gb300.api import Grid, adam_step
+    from paper_2511_09389_gb300.autograd import RTFunction
+    p = inputs.inverse_problem(n=24, n_blobs=3, num_rays=512, horizon=24.0, seed=4200)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    j_true, k, s = t(p.j), t(p.kappa), t(p.sources)
+    g = Grid(p.shape, 1, record_checkpoints=True)
+    target = g.advance(j_true, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
+    iters, lr, eps_rel = 25, 5e-2, 1e-2
+    res = inversion.recover_emissivity(target, k, s, p.num_rays, p.step_size, 1.0, p.time_step, iterations=iters,
+                                       lr=lr, eps_rel=eps_rel, grid=g)
+    # the same loop in torch
+    eps = eps_rel * float(target.max())
+    log_t = torch.log(target + eps)
+    j = torch.zeros_like(k)
+    m, v = torch.zeros_like(j), torch.zeros_like(j)
+    ref_losses = []
+    for it in range(1, iters + 1):
+        jv = j.detach().requires_grad_(True)
+        F = RTFunction.apply(jv, k, s, p.num_rays, p.step_size, 1.0, p.time_step, g)
+        loss = inversion.log_field_loss(F, log_t, eps)
+        loss.backward()
+        ref_losses.append(float(loss))
+        adam_step(j, jv.grad, m, v, lr=lr, step=it)
+        j.clamp_(min=0.0)
+    L = np.array(res["losses"])
+    assert L.shape == (iters + 1,)
+    rel_loss = np.abs(L[:iters] - ref_losses) / np.array(ref_losses)
+    rel_j = float((res["j"] - j).norm() / j.norm())
+    print(f"native vs autograd loop: max loss rel diff {rel_loss.max():.2e}, j rel-L2 {rel_j:.2e}, "
+          f"loss {L[0]:.3e} -> {L[-1]:.3e}")
+    assert rel_loss.max() < 1e-3 and rel_j < 1e-2
+    assert float(res["j"].min()) >= 0.0 and L[-1] < L[0]
+    res0 = inversion.recover_emissivity(target, k, s, p.num_rays, p.step_size, 1.0, p.time_step, iterations=0,
+                                        grid=g, j0=j)
+    F = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
+    assert len(res0["losses"]) == 1 and torch.equal(res0["j"], j)
+    assert abs(res0["losses"][0] - float(inversion.log_field_loss(F, log_t, eps))) <= 1e-5 * res0["losses"][0]
+
+
+def test_native_inversion_rejects_bad_arguments(torch_cuda):
+    """Scalars, NULL arrays, n_freq, aliasing and overlapping loss buffers are refused with
+    RT_ERR_INVALID_ARG before anything is enqueued (j is left as it was)."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300 import _native
+    from paper_2511_09389_gb300.api import Grid
+    lib = _native.load()
+    g = Grid((8, 8, 8), 1)
+    z = lambda: torch.rand(1, 8, 8, 8, device="cuda")
+    tgt, kap, jm = z(), z(), z()
+    j0 = jm.clone()
+    src = torch.full((1, 3), 3.5, device="cuda")
+    losses = torch.zeros(8, device="cuda")
+    P = lambda t: t.data_ptr() if t is not None else None
+    cases = [dict(tgt=None), dict(iters=-1), dict(lr=0.0), dict(lr=float("nan")), dict(eps_rel=0.0),
+             dict(eps_rel=float("inf")), dict(nf=2), dict(jm=tgt), dict(jm=kap), dict(losses=jm), dict(losses=None)]
+    for c in cases:
+        a = dict(tgt=tgt, kap=kap, nf=1, iters=3, lr=1e-2, eps_rel=1e-2, jm=jm, losses=losses)
+        a.update(c)
+        st = lib.rt_invert_emissivity(g._h, P(a["tgt"]), P(a["kap"]), P(src), 1, 16, 0.5, 1.0, 2.0, a["nf"], a["iters"],
+                                      a["lr"], a["eps_rel"], P(a["jm"]), P(a["losses"]), None)
+        assert st == 1, c
+    torch.cuda.synchronize()
+    assert torch.equal(jm, j0)
