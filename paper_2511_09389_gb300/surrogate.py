@@ -22,6 +22,7 @@ meet a 1e-2 bound against the march; the estimate and the fallback keep such fie
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import math
 
@@ -30,6 +31,7 @@ import torch
 
 from . import _native
 from ._native import check
+from .api import Batch
 
 LAYERS = [(2, 32, 1, 1), (32, 32, 2, 1), (32, 32, 4, 1), (32, 32, 8, 1), (32, 1, 16, 0)]  # c_in, c_out, dil, act
 SLOPE = 0.1
@@ -217,12 +219,47 @@ def field_max(lib, field, device):
     return out
 
 
-def march_fields(grid, kappa, j, sources, num_rays=3072, step_size=0.5, time_step=64.0, out=None):
-    """The plain march for a batch of one-bin problems (the surrogate's teacher and fallback)."""
+_BATCHES: "collections.OrderedDict" = collections.OrderedDict()
+_MAX_BATCHES = 48
+
+
+def clear_batches():
+    """Close the cached march batches (and release the buffers they hold)."""
+    while _BATCHES:
+        _BATCHES.popitem(last=False)[1].close()
+
+
+def march_fields(grid, kappa, j, sources, num_rays=3072, step_size=0.5, time_step=64.0, out=None, index=None,
+                 cache=True):
+    """The plain march for a batch of one-bin problems (the surrogate's teacher and fallback):
+    the fields b in `index` (default all) marched together by one rt_batch -- a field of 64^3
+    with a few sources is too small to fill the GPU alone, so the batch's persistent kernels run
+    them side by side -- into out[b]. With cache=True the batch is kept, keyed by its buffers
+    and scalars (it holds references to them), and a repeated call replays its CUDA graph;
+    cache=False marches once and frees the batch's scratch. `grid` is unused (kept for the
+    callers' signature)."""
     out = torch.empty_like(kappa) if out is None else out
-    for b in range(kappa.shape[0]):
-        grid.advance(j[b].unsqueeze(0), kappa[b].unsqueeze(0), sources[b], num_rays, step_size, 1.0, time_step,
-                     out=out[b].unsqueeze(0))
+    idx = list(range(kappa.shape[0])) if index is None else [int(b) for b in index]
+    if not idx:
+        return out
+    key = (int(num_rays), float(step_size), float(time_step)) + tuple(
+        (kappa[b].data_ptr(), j[b].data_ptr(), sources[b].data_ptr(), int(sources[b].shape[0]), out[b].data_ptr(),
+         tuple(kappa[b].shape)) for b in idx)
+    bt = _BATCHES.get(key) if cache else None
+    if bt is None:
+        bt = Batch([dict(j=j[b:b + 1], kappa=kappa[b:b + 1], sources=sources[b], num_rays=num_rays,
+                         step_size=step_size, radiation_velocity=1.0, time_step=time_step, out=out[b:b + 1])
+                    for b in idx])
+        if cache:
+            while len(_BATCHES) >= _MAX_BATCHES:
+                _BATCHES.popitem(last=False)[1].close()
+            _BATCHES[key] = bt
+    else:
+        _BATCHES.move_to_end(key)
+    bt.run()
+    if not cache:
+        torch.cuda.current_stream(out.device).synchronize()
+        bt.close()
     return out
 
 
@@ -244,7 +281,7 @@ class Dataset:
             self.kappa[a:a + len(src)] = k
             self.j[a:a + len(src)] = jj
             self.sources += src
-            march_fields(grid, k, jj, src, num_rays=num_rays, out=self.field[a:a + len(src)])
+            march_fields(grid, k, jj, src, num_rays=num_rays, out=self.field[a:a + len(src)], cache=False)
         self.fmax = field_max(_native.load(), self.field, dev)
 
     def __len__(self):
@@ -331,19 +368,20 @@ def fit_estimator(model, ds, batch=32, bound=1e-2, coverage=0.99):
     return e, est
 
 
-def solve(model, grid, kappa, j, sources, num_rays=3072, step_size=0.5, time_step=64.0):
+def solve(model, grid, kappa, j, sources, num_rays=3072, step_size=0.5, time_step=64.0, out=None):
     """Fields of a batch through the surrogate with its fallback: the network's field where the
     error estimate accepts it (exp of the de-standardised log prediction; the target's floor of
-    1e-8 of the peak is below FP32 resolution there), the plain march's elsewhere. Returns the
-    fields [B, D, H, W] and the accepted mask."""
+    1e-8 of the peak is below FP32 resolution there), the plain march's elsewhere -- the rejected
+    fields marched together in one batch (march_fields). Returns the fields [B, D, H, W] (in `out`
+    when given: a buffer reused across calls lets the fallback batch replay its graph) and the
+    accepted mask."""
     B, D, H, W = kappa.shape
     pred = model.forward(kappa, j, keep=True)
     est = model.estimate(model.features_for_estimate(B, D, H, W))
     acc = est <= model.est_threshold
-    out = torch.exp(pred * model.sigma + model.mu)
-    for b in np.nonzero(~acc)[0]:
-        grid.advance(j[b].unsqueeze(0), kappa[b].unsqueeze(0), sources[b], num_rays, step_size, 1.0, time_step,
-                     out=out[b].unsqueeze(0))
+    arg = pred * model.sigma + model.mu
+    out = torch.exp(arg) if out is None else torch.exp(arg, out=out)
+    march_fields(grid, kappa, j, sources, num_rays, step_size, time_step, out=out, index=np.nonzero(~acc)[0])
     return out, acc
 
 
@@ -352,6 +390,7 @@ def evaluate(model, grid, ds, batch=32, bound=1e-2):
     surrogate's true errors. Timed with CUDA events on the current stream."""
     st = torch.cuda.current_stream(grid.device)
     out = torch.empty_like(ds.kappa[:batch])
+    out2 = torch.empty_like(ds.kappa[:batch])
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -372,7 +411,8 @@ def evaluate(model, grid, ds, batch=32, bound=1e-2):
         n_fb = 0
         for a in range(0, len(ds), batch):
             sl = slice(a, min(a + batch, len(ds)))
-            _, acc = solve(model, grid, ds.kappa[sl], ds.j[sl], ds.sources[sl], num_rays=ds.num_rays)
+            _, acc = solve(model, grid, ds.kappa[sl], ds.j[sl], ds.sources[sl], num_rays=ds.num_rays,
+                           out=out2[: sl.stop - sl.start])
             n_fb += int(np.sum(~acc))
         return n_fb
 

@@ -95,6 +95,10 @@ def test_training_gains_over_the_constant_predictor_and_fallback_is_the_march(en
     train = S.Dataset(range(256), grid, num_rays=768)
     calib = S.Dataset(range(2000, 2032), grid, num_rays=768)
     held = S.Dataset(range(1000, 1032), grid, num_rays=768)
+    # the teacher marches fields side by side in one batch: each equals its own rt_advance
+    for b in (0, 17, 31):
+        Fb = grid.advance(held.j[b:b + 1], held.kappa[b:b + 1], held.sources[b], 768, 0.5, 1.0, 64.0)[0].double()
+        assert float((Fb - held.field[b].double()).norm() / Fb.norm()) <= 1e-5
     model = S.Surrogate(seed=1)
     model.mu, model.sigma = S.target_stats(train)
     untrained = S.heldout_loss(model, held, batch=16)
