@@ -74,6 +74,14 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Bring a box into L2 ahead of its load (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_5d(const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4) {
+    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -204,21 +212,24 @@ struct ChainItem {
 };
 
 // Items ordered (batch, segment, residue, y-pair), y-pair fastest: neighbouring items share halo rows.
-__device__ __forceinline__ bool chain_item(const ConvArgs& a, int item, int Q, ChainItem& it) {
-    const int half_h = a.H >> 1;
+__device__ __forceinline__ bool chain_item(int H, int D, int dil, int item, int Q, ChainItem& it) {
+    const int half_h = H >> 1;
     int t = item;
     const int p = t % half_h;
     t /= half_h;
-    const int r = t % a.dil;
-    t /= a.dil;
+    const int r = t % dil;
+    t /= dil;
     const int q = t % Q;
     it.b = t / Q;
     it.y0 = 2 * p;
     it.r = r;
-    const int lc = (a.D - r + a.dil - 1) / a.dil;   // outputs of residue r (0 when r >= D)
+    const int lc = (D - r + dil - 1) / dil;   // outputs of residue r (0 when r >= D)
     it.n0 = q * kChainMax;
     it.n1 = min(lc, it.n0 + kChainMax);
     return it.n0 < it.n1;
+}
+__device__ __forceinline__ bool chain_item(const ConvArgs& a, int item, int Q, ChainItem& it) {
+    return chain_item(a.H, a.D, a.dil, item, Q, it);
 }
 }  // namespace
 
@@ -449,32 +460,46 @@ __global__ void __launch_bounds__(kConvThreads, kChainCtas) k_conv3d_chain(const
     }
 }
 
-// ---- weight gradient ------------------------------------------------------------------------
+// ---- weight gradient, chained along z -------------------------------------------------------
 // dW[co][ci][tap] = sum over voxels v of dZ[v][co] * X[v + off(tap)][ci] (zero outside). As a
-// GEMM: M = (tap, ci) rows, N = co, K = voxels. Both operands are the boxes the forward kernel
-// loads, read MN-major (for a fixed voxel the 32 channels are one 64-byte swizzled row): A = four
-// taps' input boxes back to back (MN blocks of 32 channels 8 KB apart), B = the dZ box of the
-// tile. Each CTA accumulates its share of tiles in tensor memory (one 128 x 32 accumulator per
-// group of four taps, 7 groups) and adds the result to dW once, with FP32 atomics.
+// GEMM: M = (tap, ci) rows, N = co, K = voxels, both operands read MN-major from the boxes the
+// forward loads (for a fixed voxel the 32 channels are one 64-byte swizzled row). The work items
+// are the forward's chain segments: outputs z = r + n d (n in [n0, n1)) at a fixed batch and
+// y-pair. The input box of slice z' = r + i d and offset (dy, dx) pairs voxel for voxel with the
+// dZ box of output n = i - 1 + j for j = 0, 1, 2 (tap dz = 1 - j), so it is loaded once per
+// slice for the three outputs instead of once per (output, tap). A ring stage holds one group of
+// four input boxes (the nine (dy, dx) offsets make groups of 4, 4 and 1; the last group's other
+// three box slots hold stale data whose accumulator rows are never read); the segment's dZ boxes
+// pass through a ring of four slots, the boxes of slots 0 and 1 also written to mirror slots 4
+// and 5, so the (up to) three boxes a slice pairs with, starting at any slot, are consecutive in
+// shared memory: one MMA of N = 96 (64 or
+// 32 at the ends of a segment) per group and K step reads them all. Per (group, j) one 128 x 32
+// accumulator in tensor memory (9 of them, adjacent in j) sums over every item of the CTA; the
+// CTA adds them to dW once, with FP32 atomics. Per output tile ~12 boxes are loaded instead of 28.
 
 namespace {
-constexpr int kWgGroups = 7;               // ceil(27 / 4) groups of four taps
-constexpr int kWgGroupBytes = 4 * kBox;    // 32 KB
-constexpr int kWgBarOff = 2 * kWgGroupBytes + kBox;
-constexpr int kWgBytes = kWgBarOff + 7 * 8 + 16;
-constexpr int kWgCols = 256;               // 7 x 32 columns rounded up to a power of two
+constexpr int kWcStageBytes = 4 * kBox;    // one group of four input boxes, 32 KB
+constexpr int kWcStages = 5;
+constexpr int kWcZSlots = 4;               // ring positions, plus mirrors of slots 0 and 1
+constexpr int kWcZOff = kWcStages * kWcStageBytes;
+constexpr int kWcBarOff = kWcZOff + (kWcZSlots + 2) * kBox;
+constexpr int kWcBytes = kWcBarOff + (2 * kWcStages + 2 * kWcZSlots + 1) * 8 + 16;
+constexpr int kWcCols = 512;               // 9 accumulators x 32 columns, rounded up to a power of two
+static_assert(kWcBytes <= 227 * 1024, "weight-gradient shared memory");
 }  // namespace
 
 __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__ CUtensorMap tmap_x,
-                                                         const __grid_constant__ CUtensorMap tmap_dz, WgradArgs a) {
+                                                         const __grid_constant__ CUtensorMap tmap_dz, WgradArgs a,
+                                                         int n_items, int Q) {
+    constexpr int S = kWcStages, ZS = kWcZSlots;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sg = smem;                                   // two group buffers
-    unsigned char* sz = smem + 2 * kWgGroupBytes;               // dZ box
-    uint64_t* gfull = reinterpret_cast<uint64_t*>(smem + kWgBarOff);   // [2]
-    uint64_t* gempty = gfull + 2;                                       // [2]
-    uint64_t* zfull = gempty + 2;
-    uint64_t* zempty = zfull + 1;
-    uint64_t* mma_done = zempty + 1;
+    unsigned char* sa = smem;                                   // input stages
+    unsigned char* sz = smem + kWcZOff;                         // dZ slots and their mirrors
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kWcBarOff);
+    uint64_t* empty = full + S;
+    uint64_t* zfull = empty + S;
+    uint64_t* zempty = zfull + ZS;
+    uint64_t* mma_done = zempty + ZS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -482,18 +507,16 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
         if (tid == 0) atomicExch(a.err, 10);
         return;
     }
-
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { mbar_init(&gfull[i], 1); mbar_init(&gempty[i], 1); }
-        mbar_init(zfull, 1);
-        mbar_init(zempty, 1);
+        for (int i = 0; i < S; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < ZS; ++i) { mbar_init(&zfull[i], 1); mbar_init(&zempty[i], 1); }
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kWgCols)
+                     "r"(kWcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -501,81 +524,146 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = idesc_bf16(128, 32, 1);
+    {   // every MMA accumulates: clear the nine accumulators (each warp its 32 lanes)
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) tmem_zero32(tmem + lanes + (uint32_t)(c * 32));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
-    const int half_h = a.H >> 1;
-    const int tiles_per_b = a.D * half_h;
-    // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: at any time the blocks work on one window of
-    // neighbouring tiles, whose shifted boxes overlap and stay in L2 (a contiguous range per
-    // block re-read its halos from DRAM: 3.5x the input)
-    const int t_begin = blockIdx.x;
-    const int t_step = gridDim.x;
-    int done_tiles = 0;
     if (warp == 0 && lane == 0) {
-        int gq = 0, zq = 0;
-        for (int tile = t_begin; tile < a.n_tiles && !*abort_flag; tile += t_step, ++done_tiles) {
-            const int b = tile / tiles_per_b, rem = tile - b * tiles_per_b;
-            const int z = rem / half_h, y0 = 2 * (rem - (rem / half_h) * half_h);
-            if (!mbar_wait(zempty, ((uint32_t)done_tiles & 1u) ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 5); break; }
-            mbar_expect_tx(zfull, kBox);
-            tma_load_5d(sz, &tmap_dz, zfull, 0, 0, y0, z, b);
-            ++zq;
-            for (int g = 0; g < kWgGroups; ++g, ++gq) {
-                const int buf = gq & 1;
-                if (!mbar_wait(&gempty[buf], ((uint32_t)(gq >> 1) & 1u) ^ 1u)) { *abort_flag = 1; atomicExch(a.err, 6); break; }
-                const int ntap = min(4, 27 - g * 4);
-                mbar_expect_tx(&gfull[buf], ntap * kBox);
-                for (int t = 0; t < ntap; ++t) {
-                    const int tap = g * 4 + t;
-                    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                    tma_load_5d(sg + buf * kWgGroupBytes + t * kBox, &tmap_x, &gfull[buf], 0, dx * a.dil,
-                                y0 + dy * a.dil, z + dz * a.dil, b);
+        // producer: per input slice i, the dZ box of output i + 1 (its first use), then the
+        // slice's three groups of input boxes
+        int q = 0, zt = 0;
+        for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+            ChainItem it;
+            if (!chain_item(a.H, a.D, a.dil, item, Q, it)) continue;
+            for (int i = it.n0 - 1; i <= it.n1 && !*abort_flag; ++i) {
+                if (i + 1 >= it.n0 && i + 1 < it.n1) {
+                    const int slot = zt % ZS;
+                    if (!mbar_wait(&zempty[slot], ((uint32_t)(zt / ZS) & 1u) ^ 1u)) {
+                        *abort_flag = 1;
+                        atomicExch(a.err, 5);
+                        break;
+                    }
+                    mbar_expect_tx(&zfull[slot], (slot < 2 ? 2 : 1) * kBox);
+                    const int zo = it.r + (i + 1) * a.dil;
+                    tma_load_5d(sz + slot * kBox, &tmap_dz, &zfull[slot], 0, 0, it.y0, zo, it.b);
+                    if (slot < 2) tma_load_5d(sz + (slot + ZS) * kBox, &tmap_dz, &zfull[slot], 0, 0, it.y0, zo, it.b);
+                    ++zt;
+                }
+                // L2 prefetch two slices ahead (the three dy rows; dx only shifts x) and of the dZ
+                // box loaded then: their loads find them in L2 instead of waiting on DRAM
+                const int zp = it.r + (i + 2) * a.dil;
+                if (i + 2 <= it.n1 && zp < a.D) {
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int yp = it.y0 + dy * a.dil;   // whole boxes inside the volume only
+                        if (yp >= 0 && yp + 2 <= a.H) tma_prefetch_5d(&tmap_x, 0, 0, yp, zp, it.b);
+                    }
+                    if (i + 3 < it.n1) tma_prefetch_5d(&tmap_dz, 0, 0, it.y0, it.r + (i + 3) * a.dil, it.b);
+                }
+                const int zi = it.r + i * a.dil;
+                if (zi < 0 || zi >= a.D) continue;
+                for (int g = 0; g < 3; ++g, ++q) {
+                    const int st = q % S;
+                    if (!mbar_wait(&empty[st], ((uint32_t)(q / S) & 1u) ^ 1u)) {
+                        *abort_flag = 1;
+                        atomicExch(a.err, 6);
+                        break;
+                    }
+                    const int nb = g < 2 ? 4 : 1;
+                    mbar_expect_tx(&full[st], nb * kBox);
+                    for (int u = 0; u < nb; ++u) {
+                        const int p = 4 * g + u, dy = p / 3 - 1, dx = p % 3 - 1;
+                        tma_load_5d(sa + st * kWcStageBytes + u * kBox, &tmap_x, &full[st], 0, dx * a.dil,
+                                    it.y0 + dy * a.dil, zi, it.b);
+                    }
                 }
             }
         }
-        // let the last loads land before the block can exit (returns at once after normal use)
-        if (zq > 0) mbar_wait(zfull, (uint32_t)(zq - 1) & 1u);
-        for (int p = gq > 2 ? gq - 2 : 0; p < gq; ++p) mbar_wait(&gfull[p & 1], (uint32_t)(p >> 1) & 1u);
+        // let the last loads land before the block can exit
+        for (int p = q > S ? q - S : 0; p < q; ++p) mbar_wait(&full[p % S], (uint32_t)(p / S) & 1u);
+        for (int p = zt > ZS ? zt - ZS : 0; p < zt; ++p) mbar_wait(&zfull[p % ZS], (uint32_t)(p / ZS) & 1u);
     } else if (warp == 1 && lane == 0) {
-        int gq = 0;
-        for (int tile = t_begin; tile < a.n_tiles && !*abort_flag; tile += t_step, ++done_tiles) {
-            if (!mbar_wait(zfull, (uint32_t)done_tiles & 1u)) { *abort_flag = 1; atomicExch(a.err, 7); break; }
-            const uint32_t zb = smem_u32(sz);
-            for (int g = 0; g < kWgGroups; ++g, ++gq) {
-                const int buf = gq & 1;
-                if (!mbar_wait(&gfull[buf], (uint32_t)(gq >> 1) & 1u)) { *abort_flag = 1; atomicExch(a.err, 8); break; }
-                tc_fence_after();
-                const uint32_t ab = smem_u32(sg + buf * kWgGroupBytes);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    // MN-major SW64: K = 16 voxels = two 8-row blocks (1 KB); MN blocks 8 KB apart
-                    const uint64_t ad = sdesc_sw64(ab + (uint32_t)(k * 1024), kBox, 512);
-                    const uint64_t bd = sdesc_sw64(zb + (uint32_t)(k * 1024), kBox, 512);
-                    mma_bf16(tmem + (uint32_t)(g * 32), ad, bd, idesc, (tile != t_begin || k != 0) ? 1u : 0u);
+        // MMA issuer: for input slice i and group g, the outputs i - 1 + j (j = 0, 1, 2) of the
+        // segment, each into accumulator g * 3 + j; the dZ box of output n is released after
+        // slice n + 1, its last use
+        int q = 0, zt = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < n_items && ok && !*abort_flag; item += gridDim.x) {
+            ChainItem it;
+            if (!chain_item(a.H, a.D, a.dil, item, Q, it)) continue;
+            const int t0 = zt;   // ring index of output n0's dZ box
+            for (int i = it.n0 - 1; i <= it.n1 && ok; ++i) {
+                if (i + 1 >= it.n0 && i + 1 < it.n1) {
+                    const int t = t0 + (i + 1 - it.n0);
+                    if (!mbar_wait(&zfull[t % ZS], (uint32_t)(t / ZS) & 1u)) {
+                        *abort_flag = 1;
+                        atomicExch(a.err, 7);
+                        ok = false;
+                        break;
+                    }
                 }
-                mma_commit(&gempty[buf]);
+                const int zi = it.r + i * a.dil;
+                if (zi >= 0 && zi < a.D) {
+                    for (int g = 0; g < 3; ++g, ++q) {
+                        const int st = q % S;
+                        if (!mbar_wait(&full[st], (uint32_t)(q / S) & 1u)) {
+                            *abort_flag = 1;
+                            atomicExch(a.err, 8);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t ab = smem_u32(sa + st * kWcStageBytes);
+                        // outputs i - 1 + j, j in [jl, jh], within the segment
+                        const int jl = max(0, it.n0 - (i - 1)), jh = min(2, it.n1 - 1 - (i - 1));
+                        const int cnt = jh - jl + 1;
+                        const uint32_t idesc = cnt == 3 ? idesc_bf16(128, 96, 1)
+                                               : (cnt == 2 ? idesc_bf16(128, 64, 1) : idesc_bf16(128, 32, 1));
+                        const uint32_t zb = smem_u32(sz + ((t0 + (i - 1 + jl) - it.n0) % ZS) * kBox);
+                        const uint32_t d = tmem + (uint32_t)((g * 3 + jl) * 32);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            // MN-major SW64: K = 16 voxels = two 8-row blocks (1 KB); MN blocks 8 KB apart
+                            const uint64_t ad = sdesc_sw64(ab + (uint32_t)(k * 1024), kBox, 512);
+                            const uint64_t bd = sdesc_sw64(zb + (uint32_t)(k * 1024), kBox, 512);
+                            mma_bf16(d, ad, bd, idesc, 1u);
+                        }
+                        mma_commit(&empty[st]);
+                    }
+                    if (!ok) break;
+                }
+                if (i - 1 >= it.n0 && i - 1 < it.n1) mma_commit(&zempty[(t0 + i - 1 - it.n0) % ZS]);
             }
-            mma_commit(zempty);
+            zt = t0 + (it.n1 - it.n0);
         }
         mma_commit(mma_done);   // arrives once every MMA issued above has completed
     }
     __syncthreads();
-    const int ntile = t_begin < a.n_tiles ? (a.n_tiles - 1 - t_begin) / t_step + 1 : 0;
     const bool mma_ok = mbar_wait(mma_done, 0);
-    bool ok = mma_ok && !*abort_flag;
+    const bool ok = mma_ok && !*abort_flag;
     if (!mma_ok && tid == 0) atomicExch(a.err, 9);
     tc_fence_after();
-    if (ok && ntile > 0) {
-        // row m = warp * 32 + lane -> (tap within group = warp, input channel = lane)
+    if (ok && blockIdx.x < n_items) {
+        // lane m = warp * 32 + lane of group g's accumulators: input box 4 g + warp, channel lane
         const int ci = lane;
-        for (int g = 0; g < kWgGroups; ++g) {
-            float v[32];
-            tmem_load<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 32), v);
-            const int tap = g * 4 + warp;
-            if (tap < 27 && ci < a.c_in) {
+        for (int g = 0; g < 3; ++g) {
+            const int p = 4 * g + warp;
+            if (p >= 9) continue;   // warp-uniform: stale box slots of the last group
+            const int dy = p / 3 - 1, dx = p % 3 - 1;
+            for (int j = 0; j < 3; ++j) {
+                float v[32];
+                tmem_load<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((g * 3 + j) * 32), v);
+                const int tap = (2 - j) * 9 + (dy + 1) * 3 + (dx + 1);   // dz = 1 - j
+                if (ci < a.c_in) {
 #pragma unroll
-                for (int co = 0; co < 32; ++co)
-                    if (co < a.c_out) atomicAdd(a.dw + ((size_t)co * a.c_in + ci) * 27 + tap, v[co]);
+                    for (int co = 0; co < 32; ++co)
+                        if (co < a.c_out) atomicAdd(a.dw + ((size_t)co * a.c_in + ci) * 27 + tap, v[co]);
+                }
             }
         }
     }
@@ -583,7 +671,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(const __grid_constant__
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWcCols) : "memory");
     }
 }
 
@@ -657,13 +745,12 @@ cudaError_t launch_conv3d_tc(const ConvLaunch& c, cudaStream_t st) {
 }
 
 cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st) {
-    if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2) return cudaErrorInvalidValue;
+    if (c.W != 64 || c.H % 2 != 0 || c.B < 1 || c.D < 1 || c.H < 2 || c.dil < 1) return cudaErrorInvalidValue;
     CUtensorMap mx, mz;
     if (!make_map(&mx, c.x, c.B, c.D, c.H, c.W) || !make_map(&mz, c.dz, c.B, c.D, c.H, c.W))
         return cudaErrorInvalidValue;
-    // at most two CTAs per SM: each holds 256 tensor-memory columns of the SM's 512
-    const int bytes = kWgBytes < 100 * 1024 ? 100 * 1024 : kWgBytes;
-    cudaError_t ea = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // one CTA per SM: it holds 512 tensor-memory columns and 192 KB of rings
+    cudaError_t ea = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWcBytes);
     if (ea != cudaSuccess) return ea;
     WgradArgs a{};
     a.dw = c.dw;
@@ -671,10 +758,13 @@ cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st) {
     a.c_in = c.c_in; a.c_out = c.c_out; a.dil = c.dil;
     a.n_tiles = c.B * c.D * (c.H / 2);
     a.err = c.err;
-    int grid = 2 * sm_count();
-    if (grid > a.n_tiles) grid = a.n_tiles;
+    const int Q = ((c.D + c.dil - 1) / c.dil + kChainMax - 1) / kChainMax;
+    const long long items = (long long)c.B * Q * c.dil * (c.H / 2);
+    if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int grid = sm_count();
+    if (grid > items) grid = (int)items;
     if (grid < 1) return cudaSuccess;
-    k_conv3d_wgrad<<<grid, 128, bytes, st>>>(mx, mz, a);
+    k_conv3d_wgrad<<<grid, 128, kWcBytes, st>>>(mx, mz, a, (int)items, Q);
     return cudaGetLastError();
 }
 

@@ -154,3 +154,27 @@ def test_conv_weight_and_bias_gradients_match_oracle(env, c_in, c_out, dil):
     assert lib.rt_device_status(ctypes.byref(code)) == 0, code.value
     assert rel(dw.cpu().numpy().reshape(gw.shape), gw) <= 1e-4
     assert rel(db.cpu().numpy(), gb) <= 1e-4
+
+
+@pytest.mark.parametrize("shape,c_in,c_out,dil", [((3, 20, 4, 64), 32, 32, 1), ((2, 19, 6, 64), 32, 32, 2),
+                                                  ((1, 27, 2, 64), 7, 32, 3), ((2, 9, 8, 64), 32, 3, 4)])
+def test_conv_weight_gradient_across_chain_segments(env, shape, c_in, c_out, dil):
+    """The weight gradient walks chains of outputs along z in segments of at most eight: depths
+    with several segments per chain (and a ragged last one), every residue of the dilation, more
+    items than the dZ ring and input stages hold, against the FP64 oracle."""
+    torch, lib = env
+    B, D, H, W = shape
+    rng = np.random.default_rng(7 * D + dil)
+    x = bf16_round(rng.standard_normal((B, c_in, D, H, W)))
+    gy = bf16_round(rng.standard_normal((B, c_out, D, H, W)))
+    _, gw, gb = oracle.conv3d_bwd(x, np.zeros((c_out, c_in, 3, 3, 3)), gy, dil)
+    dw = torch.zeros(c_out * c_in * 27, dtype=torch.float32, device="cuda")
+    db = torch.zeros(c_out, dtype=torch.float32, device="cuda")
+    xc, gc = to_c32(torch, lib, x), to_c32(torch, lib, gy)
+    st = lib.rt_conv3d_weight_grad(xc.data_ptr(), gc.data_ptr(), B, D, H, W, c_in, c_out, dil, dw.data_ptr(),
+                                   db.data_ptr(), None)
+    assert st == 0, lib.rt_last_error()
+    code = ctypes.c_int()
+    assert lib.rt_device_status(ctypes.byref(code)) == 0, code.value
+    assert rel(dw.cpu().numpy().reshape(gw.shape), gw) <= 1e-4
+    assert rel(db.cpu().numpy(), gb) <= 1e-4
