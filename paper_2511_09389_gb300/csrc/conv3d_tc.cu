@@ -166,7 +166,6 @@ struct ConvArgs {
 struct WgradArgs {
     float* dw;                        // [c_out][c_in][27], accumulated
     int B, D, H, W, c_in, c_out, dil;
-    int n_tiles;
     int* err;
 };
 
@@ -756,7 +755,6 @@ cudaError_t launch_conv3d_wgrad(const WgradLaunch& c, cudaStream_t st) {
     a.dw = c.dw;
     a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
     a.c_in = c.c_in; a.c_out = c.c_out; a.dil = c.dil;
-    a.n_tiles = c.B * c.D * (c.H / 2);
     a.err = c.err;
     const int Q = ((c.D + c.dil - 1) / c.dil + kChainMax - 1) / kChainMax;
     const long long items = (long long)c.B * Q * c.dil * (c.H / 2);
