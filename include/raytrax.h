@@ -86,7 +86,7 @@ typedef struct {
        the update of substep k (no tiles, no checkpoint recording). plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
        the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 or 4). plan_tile: source deposit tiles (1: off, 2: on): each
        block sums the deposits of its rays in the 8^3 cells around its source in shared memory
-       and adds them to the field once (not in deterministic mode). */
+       and adds them to the field once (FP32 sums only; not in deterministic mode). */
     int plan_width;
     int plan_block;
     int plan_prefetch;
@@ -111,12 +111,11 @@ typedef struct {
                            synchronisation): buffers rewritten in place in between get the
                            gradients of their new contents. 0: off. */
     int accumulation;   /* how deposits are summed into the field (deterministic = 1 implies 3):
-                           0: automatic (default): 64-bit fixed point for groups of one bin,
-                              FP32 for wider groups. A one-bin FP32 reduction and an 8-byte one
-                              are one L2 operation each (the same march time was measured on
-                              GB300), a W-bin group's FP32 reduction is one vector operation
-                              against W 8-byte ones. One-bin groups sum in FP64 instead when the
-                              fixed-point unit would be coarse (num_sources * N_s (N_s + 1) / 2
+                           0: automatic (default): FP32 while the call deposits fewer than 32
+                              updates per cell and bin on average (num_sources * num_rays * N_s
+                              < 32 * n0 n1 n2); denser calls, where FP32 sums lose the small
+                              deposits to rounding, sum in 64-bit fixed point -- or in FP64 where
+                              the fixed-point unit would be coarse (num_sources * N_s (N_s + 1) / 2
                               above 2^32) and in rt_advance_continue.
                            1: FP32 reductions (W-wide vectors). A cell that takes very many
                               small deposits on top of a large sum -- next to many clustered
