@@ -486,7 +486,8 @@ def sharded_tail(args, p, g, j, k, s, out, hj, hk, hs, hout, stream, step_ms, ke
         "e2e": {"value": world * U / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": p.j.nbytes, "ms_per_step": ems,
                 "api": "per step: pinned inputs copied in, sharding.advance_distributed, field copied out"},
-        "gpu_launches": 3 * args.steps,
+        # per step, each of this rank's planned pieces is one pack, one march and one unpack
+        "gpu_launches": 3 * len(sharding.plan(len(sources), p.num_rays, world, rank)) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
     }
