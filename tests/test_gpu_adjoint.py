@@ -382,13 +382,16 @@ def test_emissivity_inversion_reduced_size(torch_cuda):
     assert float(res["j"].min()) >= 0.0
 
 
-def test_native_inversion_loop_matches_autograd_loop(torch_cuda):
+@pytest.mark.parametrize("n_freq,record", [(1, True), (2, False)])
+def test_native_inversion_loop_matches_autograd_loop(torch_cuda, n_freq, record):
     """rt_invert_emissivity (the loop in the library: recording forward, fused log misfit and its
     gradient, reverse march, Adam with the projection fused) against the same iterations written
     with torch autograd: RTFunction for the march, the loss in torch ops, rt_adam_step, clamp.
     Both sum their deposits with FP32 atomics in run-dependent order, so losses and the recovered
     j agree to rounding-level tolerances, not bitwise. Also: the loss history has iterations + 1
-    entries, j stays >= 0, and zero iterations return the start's loss and leave j unchanged."""
+    entries, j stays >= 0, and zero iterations return the start's loss and leave j unchanged. Two
+    bins: one loss over both; without recorded checkpoints every reverse march runs its own
+    forward sweep."""
     torch = torch_cuda
     from paper_2511_09389_gb300 import inversion
     from paper_2511_09389_gb300.api import Grid, adam_step
@@ -396,7 +399,10 @@ def test_native_inversion_loop_matches_autograd_loop(torch_cuda):
     p = inputs.inverse_problem(n=24, n_blobs=3, num_rays=512, horizon=24.0, seed=4200)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     j_true, k, s = t(p.j), t(p.kappa), t(p.sources)
-    g = Grid(p.shape, 1, record_checkpoints=True)
+    if n_freq == 2:   # a second bin with more opaque kappa and a dimmer emissivity
+        j_true = torch.cat([j_true, 0.5 * j_true])
+        k = torch.cat([k, 1.8 * k])
+    g = Grid(p.shape, n_freq, record_checkpoints=record)
     target = g.advance(j_true, k, s, p.num_rays, p.step_size, 1.0, p.time_step)
     iters, lr, eps_rel = 25, 5e-2, 1e-2
     res = inversion.recover_emissivity(target, k, s, p.num_rays, p.step_size, 1.0, p.time_step, iterations=iters,
@@ -412,7 +418,7 @@ def test_native_inversion_loop_matches_autograd_loop(torch_cuda):
         F = RTFunction.apply(jv, k, s, p.num_rays, p.step_size, 1.0, p.time_step, g)
         loss = inversion.log_field_loss(F, log_t, eps)
         loss.backward()
-        ref_losses.append(float(loss))
+        ref_losses.append(float(loss.detach()))
         adam_step(j, jv.grad, m, v, lr=lr, step=it)
         j.clamp_(min=0.0)
     L = np.array(res["losses"])
