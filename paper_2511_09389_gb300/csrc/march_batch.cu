@@ -48,7 +48,10 @@ __global__ void __launch_bounds__(256, 2) k_march_batch(const BatchInst* __restr
             rs.x = L.sx; rs.y = L.sy; rs.z = L.sz;
 #pragma unroll
             for (int b = 0; b < W; ++b) { rs.I[b] = 0.0f; rs.tau[b] = 0.0f; }
-            march_lane<W, 0>(L, rs);
+            // corner slots with the entering corners gathered a substep ahead (gathers mode 4)
+            // where the lane fits the 128-register cap; the four-bin lane needs ~160 registers
+            // for that and keeps the slots of mode 0
+            march_lane<W, W == 4 ? 0 : 4>(L, rs);
         }
         __syncwarp();
     }
