@@ -99,9 +99,8 @@ typedef struct {
                            synchronises the stream (one pass over the inputs). 0: no scan. */
     int record_checkpoints; /* 1: every full-range rt_advance also stores the reverse march's
                            checkpoints (every ckpt_stride substeps) in the handle, marching
-                           with the adjoint's bin grouping (one bin: two lanes per ray with
-                           gathers mode 4; wider groups: gathers mode 0; unless a plan is
-                           pinned; with autotune = 1 the fastest plan that records, timed with
+                           with the adjoint's bin grouping (one bin: two lanes per ray; wider
+                           groups: one lane; both with gathers mode 4; unless a plan is pinned; with autotune = 1 the fastest plan that records, timed with
                            its checkpoint stores, tuned apart from non-recording calls); a following
                            rt_backward / rt_backward_sources with the same j_map, kappa_map and
                            source_pos pointers and the same scalars uses them instead of

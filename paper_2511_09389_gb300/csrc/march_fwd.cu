@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
 // ---- kernel table ------------------------------------------------------------------------
 // The compiled (W, gathers mode, accumulation, tiles, checkpoints, lanes per ray) combinations:
 //   FP32: every W and gathers mode with and without tiles (mode 4: without); recording with
-//         gathers mode 0 (and 1 or 3 for one bin); two lanes per ray for every W with gathers
-//         mode 0 or 4 (recording: mode 0, and mode 4 for one bin).
+//         gathers modes 0 and 4 (and 1 or 3 for one bin); two lanes per ray for every W with
+//         gathers mode 0 or 4, recording or not.
 //   fixed point: corner slots and gathers mode 4 for every W; for one bin also recording and two
 //         lanes per ray; two lanes per ray with gathers mode 4 for one and four bins.
 //   FP64: corner slots for every W, with and without recording; two lanes per ray for one bin.
@@ -178,8 +178,9 @@ using MarchKernel = void (*)(MarchArgs);
 
 template <int W>
 MarchKernel pick_one_lane(int pf, int acc, bool tile, bool rec) {
-    if (pf == 4) {   // corner slots with the gathers one substep ahead: no tiles, no recording
-        if (tile || rec) return nullptr;
+    if (pf == 4) {   // corner slots with the gathers one substep ahead: no tiles
+        if (tile) return nullptr;
+        if (rec) return acc == 0 ? k_march_fwd<W, 4, 0, false, true> : nullptr;
         if (acc == 0) return k_march_fwd<W, 4, 0, false>;
         if (acc == 1) return k_march_fwd<W, 4, 1, false>;
         return nullptr;
@@ -216,7 +217,9 @@ MarchKernel pick_pair(int W, int pf, int acc, bool rec) {
         if (acc == 0 && !rec)
             return W == 1 ? k_march_fwd_pair<1, false, 0, 4> : (W == 2 ? k_march_fwd_pair<2, false, 0, 4>
                                                                      : k_march_fwd_pair<4, false, 0, 4>);
-        if (acc == 0 && W == 1) return k_march_fwd_pair<1, true, 0, 4>;
+        if (acc == 0)   // recording
+            return W == 1 ? k_march_fwd_pair<1, true, 0, 4> : (W == 2 ? k_march_fwd_pair<2, true, 0, 4>
+                                                                  : k_march_fwd_pair<4, true, 0, 4>);
         if (acc == 1 && !rec && (W == 1 || W == 4))
             return W == 1 ? k_march_fwd_pair<1, false, 1, 4> : k_march_fwd_pair<4, false, 1, 4>;
         return nullptr;

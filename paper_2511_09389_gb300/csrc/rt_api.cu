@@ -683,10 +683,11 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
         plan.lpr = 1;
         plan.prefetch = 0;
     }
-    // record the reverse march's checkpoints with the adjoint's bin grouping: gathers mode 0 with
-    // one lane per ray, or for one bin per thread two lanes per ray with gathers mode 4 (measured
-    // on GB300, 64^3 with 24,576 lanes: 0.087 ms against 0.12 for two lanes with mode 0, 0.155 for
-    // mode 3 and 0.17 for mode 1 with one lane), unless a plan was pinned or tuned
+    // record the reverse march's checkpoints with the adjoint's bin grouping and gathers mode 4:
+    // two lanes per ray for one bin per thread, one lane for wider groups (measured on GB300, 64^3
+    // with 8 sources and 3,072 rays: one bin 0.087 ms against 0.12 for two lanes with mode 0,
+    // 0.155 for mode 3 and 0.17 for mode 1 with one lane; four bins 0.094 ms against 0.124 for two
+    // lanes and 0.131 for one lane with mode 0), unless a plan was pinned or tuned
     if (record) {
         const int w = pick_width(a.n_freq);
         const bool keep = plan.W == w && (g->opt.plan_prefetch || g->opt.plan_lanes || g->opt.autotune);
@@ -697,9 +698,10 @@ rt_status advance_impl(rt_grid* g, const Call& a) {
             if (plan.lpr == 2) plan.prefetch = 4;
         }
         plan.W = w;
-        if (w != 1) plan.prefetch = 0;                               // corner slots
-        else if (plan.lpr == 2) plan.prefetch = plan.prefetch == 4 ? 4 : 0;
-        else if (plan.prefetch == 2) plan.prefetch = 3;              // (recording has no gathers mode 2)
+        if (plan.prefetch != 4) {
+            if (w != 1 || plan.lpr == 2) plan.prefetch = 0;          // corner slots
+            else if (plan.prefetch == 2) plan.prefetch = 3;          // (recording has no gathers mode 2)
+        }
     }
     const int acc = acc_mode_for(g, plan, a, ns);
     if (acc != 0) plan.tile = 0;

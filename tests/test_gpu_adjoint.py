@@ -233,7 +233,8 @@ def test_autograd_sources_kappa_scale_and_amplitudes(torch_cuda):
 
 
 @pytest.mark.parametrize("n_freq,stride,plan", [(1, 16, None), (3, 8, None), (5, 32, (4, 64, 0, 2, 1)), (2, 16, None),
-                                                 (1, 16, (1, 32, 0, 2)), (2, 8, (2, 64, 0, 2))])
+                                                 (1, 16, (1, 32, 0, 2)), (2, 8, (2, 64, 0, 2)), (4, 8, (4, 32, 4, 1)),
+                                                 (3, 16, (4, 64, 4, 2)), (2, 4, (2, 32, 4, 2)), (2, 8, (2, 32, 4, 1))])
 def test_recorded_checkpoints_give_the_same_gradients(torch_cuda, n_freq, stride, plan):
     """record_checkpoints: the forward march stores the reverse march's checkpoints and the
     adjoint skips its forward sweep; gradients as without it. A backward whose arguments
@@ -247,6 +248,8 @@ def test_recorded_checkpoints_give_the_same_gradients(torch_cuda, n_freq, stride
     j, k, s, Gt = t(p.j), t(p.kappa), t(p.sources), t(G)
     g = Grid(p.shape, 8, ckpt_stride=stride, record_checkpoints=True, plan=plan)
     F = g.advance(j, k, s, p.num_rays, p.step_size, 1.0, p.time_step).cpu().numpy()
+    if plan is not None and plan[2] == 4:   # recorded with the gathers a substep ahead
+        assert g.last_plan()["prefetch"] == 4 and g.last_plan()["lanes_per_ray"] == plan[3]
     gj, gk, gs = g.backward(Gt, j, k, s, p.num_rays, p.step_size, 1.0, p.time_step, need_sources=True)
     rj, rk = oracle_backward(p, G)
     ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
