@@ -12,7 +12,9 @@
 // per-thread record (x_k, I_k, E_k, a_k, e_k) and then walks it backwards, so the forward state
 // is recomputed exactly and never reconstructed by dividing out exp(-kappa ds). Scatters into
 // dj / dkappa are merged in registers while the corner set (or kappa cell) is unchanged, and
-// gathers are skipped while it is unchanged (the registers still hold those corner values).
+// gathers are skipped while it is unchanged (the registers still hold those corner values). With
+// one bin and K = 4 a segment's four samples are formed from its checkpoint first and all their
+// gathers (j, kappa, G) issued together, so the replay and the walk run on registers.
 #include "march_common.cuh"
 #include "rt_internal.h"
 
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
     // are unrolled with constant indices, so the record lives in registers; longer records go
     // to local memory
     float rx[K], ry[K], rz[K], rI[K][W], rE[K][W], ra[K][W], re[K][W];
+    // one bin with K = 4: the segment's gathers are issued together (below)
+    constexpr bool kBatch = K == 4 && W == 1;
     const int nseg = (a.ns + K - 1) / K;
 #pragma unroll 1
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -133,58 +137,34 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
         float I[W], tau[W];
 #pragma unroll
         for (int b = 0; b < W; ++b) { I[b] = ck_at(seg, 3 + b); tau[b] = ck_at(seg, 3 + W + b); }
-        // replay the segment exactly as the forward sweep ran it
-        Vec<W> jc[8], kc;
-        int c0 = -1, c7 = -1, cn = -1;
-        auto replay = [&](const int q) {
-            Sample sm;
-            make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
-            if (sm.cell[0] != c0 || sm.cell[7] != c7) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
-                c0 = sm.cell[0]; c7 = sm.cell[7];
-            }
-            if (sm.nn != cn) { kc = ldg_vec<W>(kg, sm.nn); cn = sm.nn; }
-            rx[q] = x; ry[q] = y; rz[q] = z;
+        // One replay step (the forward sweep's Eq. 2 exactly as it ran it) for sample sm with the j
+        // values jv of its corners and kappa kv at its cell: fills the record at q, advances I, tau.
+        auto replay_step = [&](const int q, const Sample& sm, const Vec<W>* jv, const Vec<W>& kv, float px,
+                               float py, float pz) {
+            rx[q] = px; ry[q] = py; rz[q] = pz;
 #pragma unroll
             for (int b = 0; b < W; ++b) {
                 float jk = 0.0f;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jc[c].v[b], jk);
-                const float kds = kc.v[b] * ds;
+                for (int c = 0; c < 8; ++c) jk = fmaf(sm.w[c], jv[c].v[b], jk);
+                const float kds = kv.v[b] * ds;
                 const float att = neg_exp(kds), em = neg_exp(tau[b]);
                 const float emis = jk * em * ds;
                 rI[q][b] = I[b]; rE[q][b] = em; ra[q][b] = att; re[q][b] = emis;
                 I[b] = fmaf(I[b], att, emis);
                 tau[b] += kds;
             }
-            x = __fadd_rn(x, dx);
-            y = __fadd_rn(y, dy);
-            z = __fadd_rn(z, dz);
         };
-        if constexpr (K <= 8) {   // constant indices: the record stays in registers
-#pragma unroll
-            for (int q = 0; q < K; ++q)
-                if (q < len) replay(q);
-        } else {
-#pragma unroll 1
-            for (int q = 0; q < len; ++q) replay(q);
-        }
-        // walk the segment backwards
-        auto walk = [&](const int q) {
-            Sample sm;
-            make_sample(rx[q], ry[q], rz[q], a.n0, a.n1, a.n2, a.kappa_mode, sm);
-            if (sm.cell[0] != g0 || sm.cell[7] != g7) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) gc[c] = ldg_vec<W>(Gg, sm.cell[c]);
-                g0 = sm.cell[0]; g7 = sm.cell[7];
-            }
+        // One reverse step at record q for sample sm, with G (gv) and, for the source gradient,
+        // j (jv) at its corners: lam, mu, the dj / dkappa contributions (merged while the corner
+        // set / kappa cell is unchanged) and dL/dx_q.
+        auto walk_step = [&](const int q, const Sample& sm, const Vec<W>* gv, const Vec<W>* jv) {
             float ddj[W], ddk[W];
 #pragma unroll
             for (int b = 0; b < W; ++b) {
                 float gk = 0.0f;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) gk = fmaf(sm.w[c], gc[c].v[b], gk);
+                for (int c = 0; c < 8; ++c) gk = fmaf(sm.w[c], gv[c].v[b], gk);
                 const float lam = fmaf(a_next[b], lam_next[b], gk * a.scale);      // lam_{k+1}
                 ddj[b] = lam * rE[q][b] * ds;
                 ddk[b] = -ds * fmaf(lam * rI[q][b], ra[q][b], mu[b]);              // uses mu_{k+1}
@@ -193,11 +173,6 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
                 a_next[b] = ra[q][b];
             }
             if (SG) {
-                if (sm.cell[0] != jr0 || sm.cell[7] != jr7) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) jr[c] = ldg_vec<W>(jg, sm.cell[c]);
-                    jr0 = sm.cell[0]; jr7 = sm.cell[7];
-                }
                 float V[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -205,8 +180,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
 #pragma unroll
                     for (int b = 0; b < W; ++b) {
                         const float In = fmaf(rI[q][b], ra[q][b], re[q][b]);     // I_{k+1}
-                        v = fmaf(a.scale * In, gc[c].v[b], v);
-                        v = fmaf(ddj[b], jr[c].v[b], v);
+                        v = fmaf(a.scale * In, gv[c].v[b], v);
+                        v = fmaf(ddj[b], jv[c].v[b], v);
                     }
                     V[c] = v;
                 }
@@ -254,13 +229,89 @@ __global__ void __launch_bounds__(256) k_march_bwd(BackArgs a) {
                 }
             }
         };
-        if constexpr (K <= 8) {
+        if constexpr (!kBatch) {
+            // replay the segment exactly as the forward sweep ran it, gathering the corner set
+            // when it changes; then walk it backwards, gathering G (and j) likewise
+            Vec<W> jc[8], kc;
+            int c0 = -1, c7 = -1, cn = -1;
+            auto replay = [&](const int q) {
+                Sample sm;
+                make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, sm);
+                if (sm.cell[0] != c0 || sm.cell[7] != c7) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) jc[c] = ldg_vec<W>(jg, sm.cell[c]);
+                    c0 = sm.cell[0]; c7 = sm.cell[7];
+                }
+                if (sm.nn != cn) { kc = ldg_vec<W>(kg, sm.nn); cn = sm.nn; }
+                replay_step(q, sm, jc, kc, x, y, z);
+                x = __fadd_rn(x, dx);
+                y = __fadd_rn(y, dy);
+                z = __fadd_rn(z, dz);
+            };
+            if constexpr (K <= 8) {   // constant indices: the record stays in registers
+#pragma unroll
+                for (int q = 0; q < K; ++q)
+                    if (q < len) replay(q);
+            } else {
+#pragma unroll 1
+                for (int q = 0; q < len; ++q) replay(q);
+            }
+            auto walk = [&](const int q) {
+                Sample sm;
+                make_sample(rx[q], ry[q], rz[q], a.n0, a.n1, a.n2, a.kappa_mode, sm);
+                if (sm.cell[0] != g0 || sm.cell[7] != g7) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) gc[c] = ldg_vec<W>(Gg, sm.cell[c]);
+                    g0 = sm.cell[0]; g7 = sm.cell[7];
+                }
+                if (SG && (sm.cell[0] != jr0 || sm.cell[7] != jr7)) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) jr[c] = ldg_vec<W>(jg, sm.cell[c]);
+                    jr0 = sm.cell[0]; jr7 = sm.cell[7];
+                }
+                walk_step(q, sm, gc, jr);
+            };
+            if constexpr (K <= 8) {
+#pragma unroll
+                for (int q = K - 1; q >= 0; --q)
+                    if (q < len) walk(q);
+            } else {
+#pragma unroll 1
+                for (int q = len - 1; q >= 0; --q) walk(q);
+            }
+        } else {
+            // one bin, K = 4: every position of the segment follows from its checkpoint, so its
+            // samples are formed first and all their gathers (j and kappa for the replay, G for
+            // the walk) are issued together -- one L2 round trip per segment instead of one per
+            // corner-set change -- and both passes then run on registers
+            Sample smq[K];
+            float px[K], py[K], pz[K];
+            Vec<W> jq[K][8], kq[K], gq[K][8];
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                px[q] = x; py[q] = y; pz[q] = z;
+                make_sample(x, y, z, a.n0, a.n1, a.n2, a.kappa_mode, smq[q]);
+                x = __fadd_rn(x, dx);
+                y = __fadd_rn(y, dy);
+                z = __fadd_rn(z, dz);
+            }
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                if (q < len) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        jq[q][c] = ldg_vec<W>(jg, smq[q].cell[c]);
+                        gq[q][c] = ldg_vec<W>(Gg, smq[q].cell[c]);
+                    }
+                    kq[q] = ldg_vec<W>(kg, smq[q].nn);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (q < len) replay_step(q, smq[q], jq[q], kq[q], px[q], py[q], pz[q]);
 #pragma unroll
             for (int q = K - 1; q >= 0; --q)
-                if (q < len) walk(q);
-        } else {
-#pragma unroll 1
-            for (int q = len - 1; q >= 0; --q) walk(q);
+                if (q < len) walk_step(q, smq[q], gq[q], jq[q]);
         }
     }
     if (djg && pc[0] >= 0) {
