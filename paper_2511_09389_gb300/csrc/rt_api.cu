@@ -1202,9 +1202,9 @@ rt_status backward_impl(rt_grid* g, const float* grad_out, const float* j_map, c
     // checkpoint stride: tuned once per shape class when the handle autotunes and leaves the stride
     // automatic -- every K is timed on this call's own inputs (the full reverse march with its own
     // forward sweep, best of two runs; its gradients are discarded) and the fastest kept. The own
-    // sweep also stands for what a recording forward pays to write that K's checkpoints: timing
-    // the reverse march alone on recorded checkpoints picked K = 4 on the 64^3 inverse workload,
-    // whose recording forward then took 0.11 ms instead of 0.088 ms (measured on GB300)
+    // sweep also stands for what a recording forward pays to write that K's checkpoints (timing
+    // the reverse march alone on recorded checkpoints gave a slower forward + adjoint step on the
+    // 64^3 inverse workload: 8.5 against 8.9 x 10^9 updates/s, measured on GB300)
     const rt_grid::TuneKey kkey{n_freq, num_sources, num_rays, ns};
     bool tuned_now = false;
     g->last_k_ms = -1.0f;
