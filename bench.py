@@ -229,7 +229,7 @@ def fwd_adjoint(args, dev, flush, stream):
     from paper_2511_09389_gb300.api import Grid, num_substeps
     p = inputs.inverse_problem()
     U = len(p.sources) * p.num_rays * num_substeps(p.step_size, p.radiation_velocity, p.time_step) * p.n_freq
-    g = Grid(p.shape, 1, profile=True, record_checkpoints=True, autotune=True)
+    g = Grid(p.shape, 1, profile=True, record_checkpoints=True, autotune=True, ckpt_stride=args.ckpt_stride)
     j, k, s = (torch.from_numpy(a).to(dev) for a in (p.j, p.kappa, p.sources))
     G = torch.randn(p.j.shape, device=dev)
     out = torch.empty_like(j)
@@ -711,6 +711,8 @@ def main():
     ap.add_argument("--surrogate-epochs", type=int, default=8)
     ap.add_argument("--plan", default="", help="pin the launch plan 'bins_per_group,block,prefetch[,lanes_per_ray]' "
                                                "instead of autotuning (for reproducible profiles)")
+    ap.add_argument("--ckpt-stride", type=int, default=0,
+                    help="pin the adjoint checkpoint stride K (4, 8, 16 or 32) instead of tuning it (0)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
