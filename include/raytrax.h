@@ -83,8 +83,9 @@ typedef struct {
        substep's gathers before the current update, mode 2 does both, mode 3 reuses the
        whole corner set while it is unchanged and flushes and re-gathers all 8 corners when it
        changes, and mode 4 is mode 0 with the corners that enter at substep k+1 gathered before
-       the update of substep k (no tiles, no checkpoint recording). plan_lanes: lanes per ray (1, or 2 adjacent lanes sharing one ray, each keeping
-       the four corner slots on its side of axis 2, for twice the warps; gathers mode 0 or 4). plan_tile: source deposit tiles (1: off, 2: on): each
+       the update of substep k (no tiles). plan_lanes: lanes per ray (1, or 2 adjacent lanes
+       sharing one ray, each keeping the four corner slots on its side of axis 2, for twice the
+       warps; gathers mode 0 or 4). plan_tile: source deposit tiles (1: off, 2: on): each
        block sums the deposits of its rays in the 8^3 cells around its source in shared memory
        and adds them to the field once (FP32 sums only; not in deterministic mode). */
     int plan_width;
@@ -100,8 +101,9 @@ typedef struct {
     int record_checkpoints; /* 1: every full-range rt_advance also stores the reverse march's
                            checkpoints (every ckpt_stride substeps) in the handle, marching
                            with the adjoint's bin grouping (one bin: two lanes per ray; wider
-                           groups: one lane; both with gathers mode 4; unless a plan is pinned; with autotune = 1 the fastest plan that records, timed with
-                           its checkpoint stores, tuned apart from non-recording calls); a following
+                           groups: one lane; both with gathers mode 4) unless a plan is pinned
+                           (with autotune = 1: the fastest plan that records, timed with its
+                           checkpoint stores, tuned apart from non-recording calls); a following
                            rt_backward / rt_backward_sources with the same j_map, kappa_map and
                            source_pos pointers and the same scalars uses them instead of
                            repeating the forward sweep -- but only if a 64-bit content hash of
@@ -250,9 +252,10 @@ rt_status rt_backward(rt_grid* grid, const float* grad_out, const float* j_map,
 
 /* rt_backward plus the gradient with respect to the source positions: grad_src (device
    [num_sources][3], overwritten, or NULL). Sec. 4 notes that the march is built from smooth
-   interpolation and deposition primitives; source positions enter only through them. Every position of a ray is x_k = src + k n ds, so dL/dsrc sums dL/dx_k over the
-   source's rays and substeps with everything else fixed, where x_k enters the deposit of
-   I_{k+1} and the gather of j:
+   interpolation and deposition primitives; source positions enter only through them. Every
+   position of a ray is x_k = src + k n ds, so dL/dsrc sums dL/dx_k over the source's rays
+   and substeps with everything else fixed, where x_k enters the deposit of I_{k+1} and the
+   gather of j:
      dL/dx_k = grad_x [ sum_c w_c(x) (s I_{k+1} G[c] + lam_{k+1} E_k ds j[c]) ] at x = x_k,
    the corner values held fixed. The nearest-cell kappa read is piecewise constant and adds
    nothing (the gradient is that of the almost-everywhere derivative); a clamped axis adds
