@@ -53,15 +53,17 @@ def direction_table(num_rays: int) -> np.ndarray:
 class Grid:
     """A library handle for one grid shape (owns its scratch on one device).
 
-    accumulation: "auto" (64-bit fixed point for one-bin groups, FP32 for wider ones), "fp32",
-    "fp64" or "fixed"; deterministic=True also sums in fixed point, with one launch plan.
+    accumulation: "auto" (FP32 while a call deposits fewer than 32 updates per cell and bin on
+    average, else 64-bit fixed point, or FP64 where the fixed-point unit would be coarse and in
+    continued marches), "fp32", "fp64" or "fixed"; deterministic=True also sums in fixed point,
+    with one launch plan.
 
     plan=(bins_per_group, block, gathers[, lanes_per_ray[, tile]]) pins the forward launch plan,
     gathers 0 = corner slots (a shared face keeps its gathers and sums), 1 = one step ahead,
-    2 = both, 3 = the whole corner set reused while unchanged; tile 0 / 1 = source deposit tiles
-    off / on
-    (the library's default when not given; ignored when autotune=True, which times the
-    candidates on the first call of each shape class)."""
+    2 = both, 3 = the whole corner set reused while unchanged, 4 = corner slots with the entering
+    corners gathered a substep ahead; lanes_per_ray 1 or 2 (2: gathers 0 or 4); tile 0 / 1 =
+    source deposit tiles off / on (the library's default when not given; ignored when
+    autotune=True, which times the candidates on the first call of each shape class)."""
 
     ACCUMULATION = {"auto": 0, "fp32": 1, "fp64": 2, "fixed": 3}
 
