@@ -58,10 +58,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_counter(src_hash, key="dram_bytes_per_launch"):
-    """A per-launch counter of the march kernel (DRAM bytes, L2 red sectors) from the committed
-    ncu summary, or None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "march_fwd_turbulent128.md")
+def profiled_counter(src_hash, key="dram_bytes_per_launch", summary="march_fwd_turbulent128.md"):
+    """A counter of the march kernel (DRAM bytes, L2 red sectors) from a committed ncu summary in
+    profiles/, or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
     except OSError:
@@ -273,7 +273,30 @@ def fwd_adjoint(args, dev, flush, stream):
                           "optimiser": "Adam (rt_adam_step), projected onto j >= 0, j = 0 at the start"}}
 
 
-def paper_workload(args, dev, flush, stream):
+def paper_roofline(plan, acc, U, kms, peaks):
+    """The paper workload's march kernel against the L2 reductions of its accumulation: issued
+    L2 red sectors per update counted by ncu on the first 256 of its sources with the same plan
+    (the committed summary, hash-checked), times this run's updates, over its CUDA-event time."""
+    summary = "march_fwd_paper_timing.md"
+    src_hash = kernel_source_hash()
+    per_update = profiled_counter(src_hash, "l2_red_sectors_per_update", summary)
+    text = open(os.path.join(ROOT, "profiles", summary)).read() if per_update is not None else ""
+    m = re.search(r"profiled_plan:\s*([0-9,]+)\s+(\w+)", text)
+    same = (m is not None and plan is not None and acc == m.group(2) and
+            m.group(1) == f"{plan['width']},{plan['prefetch']},{plan['lanes_per_ray']},{plan['tile']}")
+    peak_key = {"fixed": "red_stencil_u64", "fp64": "red_stencil_f64"}.get(acc, "red_stencil_v1")
+    peak = (peaks or {}).get(peak_key)
+    if per_update is None or not same or not peak:
+        return {"bound": "l2_red", "frac": None,
+                "note": "no ncu count for this kernel source, plan and accumulation" if peak else "no peak"}
+    rate = per_update * U / (kms * 1e-3)
+    return {"bound": "l2_red", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "Gop/s", "frac": rate / peak,
+            "peak_kind": f"measured here ({peak_key}: reductions into the 8 corners of random cells of a 128^3 grid)",
+            "basis": f"issued L2 red sectors per update ({per_update:.4f}, ncu on the first 256 sources, "
+                     f"profiles/{summary}) x {U} updates / march-kernel CUDA-event time"}
+
+
+def paper_workload(args, dev, flush, stream, peaks=None):
     """The paper's timing run on a synthetic medium (128^3 lognormal kappa, 2097 sources at the
     0.1 % highest-kappa cells, N_Omega 4096, ds 0.5, one bin; c dt 128 assumed, N_s 256): one
     rt_advance per step, autotuned during the warm-up, L2 flushed before each timed step. The
@@ -305,6 +328,7 @@ def paper_workload(args, dev, flush, stream):
     t = st.mean(steps)
     res = {"value": U / (t * 1e-3), "unit": "updates/s", "updates_per_step": U, "ms_per_step": t,
            "kernel_ms": st.mean(kern), "launch_plan": plan, "accumulation": acc,
+           "roofline": paper_roofline(plan, acc, U, st.mean(kern), peaks),
            "workload": f"128^3 lognormal kappa, {len(p.sources)} sources at the 0.1 % highest-kappa cells, "
                        f"N_Omega {p.num_rays}, ds {p.step_size}, N_s {ns} (c dt 128 assumed), 1 bin",
            "paper": {"seconds": 4.49, "hardware": "1x H200 (JAX)", "speedup_context": 4.49 / (t * 1e-3),
@@ -666,7 +690,7 @@ def native_arm(args):
                              "ms_per_step": statistics.mean(tdet), "note": "64-bit fixed-point deposits, bitwise reproducible"}
     line["fwd_adjoint"] = fwd_adjoint(args, dev, flush, stream)
     if not args.no_paper:
-        line["paper_workload"] = paper_workload(args, dev, flush, stream)
+        line["paper_workload"] = paper_workload(args, dev, flush, stream, line["roofline"].get("peaks"))
     if not args.no_batch:
         line["batched"] = batched(args, dev, stream)
     if args.surrogate_train > 0:

@@ -40,3 +40,30 @@ def test_warmup_floor_is_enforced():
     r = run_bench("--impl", "reference", "--steps", "1", "--warmup", "2", timeout=120)
     assert r.returncode != 0
     assert "--warmup must be >= 3" in r.stderr
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_profile_counters_are_current_and_read_back():
+    """The ncu counts the benchmark divides by its own kernel time come from summaries captured
+    on the current march sources: the hash check passes, and the paper leg's L2 fraction is the
+    summary's reductions per update x updates / time over the peak, null for another plan."""
+    b = _bench_module()
+    h = b.kernel_source_hash()
+    assert b.profiled_counter(h, "l2_red_sectors_per_launch") > 0
+    assert b.profiled_counter(h, "l2_read_sectors_per_launch") > 0
+    per_update = b.profiled_counter(h, "l2_red_sectors_per_update", "march_fwd_paper_timing.md")
+    assert per_update is not None and 1.0 < per_update < 8.0
+    assert b.profiled_counter("0" * 16, "l2_red_sectors_per_launch") is None
+    plan = {"width": 1, "block": 32, "prefetch": 4, "lanes_per_ray": 2, "tile": 0}
+    U, kms, peak = 2_198_863_872, 31.3, 195e9
+    r = b.paper_roofline(plan, "fixed", U, kms, {"red_stencil_u64": peak})
+    assert r["frac"] == pytest.approx(per_update * U / (kms * 1e-3) / peak, rel=1e-12)
+    assert b.paper_roofline(dict(plan, lanes_per_ray=1), "fixed", U, kms, {"red_stencil_u64": peak})["frac"] is None
+    assert b.paper_roofline(plan, "fp32", U, kms, {"red_stencil_v1": peak})["frac"] is None
