@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF
     L.jg = a.jp + (size_t)g * ncell * W;
     L.kg = a.kp + (size_t)g * ncell * W;
     L.og = og;
-    L.pol = red_policy(4LL * a.groups * ncell * W);
+    L.pol = red_policy((DET ? 8LL : 4LL) * a.groups * ncell * W);   // bytes of the accumulator
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(fwd_max_threads<W, PF>(), fwd_min_blocks<W, PF
     L.og64 = a.acc64 ? a.acc64 + (size_t)g * ncell * W : nullptr;
     L.ncell = ncell;
     L.nbins = min(W, a.n_freq - g * W);
-    L.fix = a.fix;
+    if (DET == 1) L.fix = __ldg(a.fix);   // the fixed-point unit, read once per lane
     L.tile = TILE ? tile : nullptr;
     L.to0 = to0; L.to1 = to1; L.to2 = to2;
     // start at the source with I = tau = 0, or (stateful advance) where the previous call left
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     L.jg = a.jp + (size_t)g * ncell * W;
     L.kg = a.kp + (size_t)g * ncell * W;
     L.og = a.acc + (size_t)g * ncell * W;
-    L.pol = red_policy(4LL * a.groups * ncell * W);
+    L.pol = red_policy((DET ? 8LL : 4LL) * a.groups * ncell * W);   // bytes of the accumulator
     L.n = a.dirs[r];
     L.sx = a.src[3 * s + 0]; L.sy = a.src[3 * s + 1]; L.sz = a.src[3 * s + 2];
     L.n0 = a.n0; L.n1 = a.n1; L.n2 = a.n2;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_pair(MarchArgs a) {
     L.og64 = a.acc64 ? a.acc64 + (size_t)g * ncell * W : nullptr;
     L.ncell = ncell;
     L.nbins = min(W, a.n_freq - g * W);
-    L.fix = a.fix;
+    if (DET == 1) L.fix = __ldg(a.fix);   // the fixed-point unit, read once per lane
     if (REC) {
         L.ck_lanes = (long long)a.ray_count * a.nsrc * a.groups;
         L.ck = a.ckpt + ((long long)g * a.nsrc + s) * a.ray_count + r;

@@ -43,7 +43,7 @@ struct Lane {
                                               //   FP64 (the wide accumulation), see flush()
     long long ncell;
     int nbins;                                //   real bins in this group (the rest are padding)
-    const float* fix;                         //   units per unit deposit, a power of two (device)
+    float fix = 0.0f;                         //   fixed point: units per unit deposit, a power of two
     float4 n;                 // direction
     float sx, sy, sz;         // source position
     int n0, n1, n2;
@@ -83,14 +83,13 @@ __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
         double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
 #pragma unroll
         for (int b = 0; b < W; ++b)
-            if (b < L.nbins) red_add_f64(o + b, v[b]);
+            if (W == 1 || b < L.nbins) red_add_f64(o + b, v[b]);
     } else if (DET) {
         // v * 2^k is exact in FP32; its rounding to an integer is the fixed-point quantisation
-        const float f = __ldg(L.fix);
 #pragma unroll
         for (int b = 0; b < W; ++b)
-            if (b < L.nbins)
-                red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * f));
+            if (W == 1 || b < L.nbins)
+                red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
     } else {
         red_vec<W>(L.og, cell, v, L.pol);
     }
@@ -102,13 +101,12 @@ __device__ __forceinline__ void flush_if(bool p, const Lane& L, int cell, const 
     if (DET == 2) {
         double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
 #pragma unroll
-        for (int b = 0; b < W; ++b) red_add_f64_if(p && b < L.nbins, o + b, v[b]);
+        for (int b = 0; b < W; ++b) red_add_f64_if(p && (W == 1 || b < L.nbins), o + b, v[b]);
     } else if (DET) {
-        const float f = __ldg(L.fix);
 #pragma unroll
         for (int b = 0; b < W; ++b)
-            red_add_u64_if(p && b < L.nbins, L.og64 + (size_t)cell * W + b,
-                           (unsigned long long)__float2ll_rn(v[b] * f));
+            red_add_u64_if(p && (W == 1 || b < L.nbins), L.og64 + (size_t)cell * W + b,
+                           (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
     } else {
         red_vec_if<W>(p, L.og, cell, v, L.pol);
     }
