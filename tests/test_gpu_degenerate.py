@@ -1,0 +1,125 @@
+"""GPU parity on degenerate grids: extents of one or two cells (slabs, lines, a single cell),
+through the C ABI, against the FP64 oracle (itself pinned on these shapes in
+test_oracle_degenerate.py). Every launch plan family, every accumulation, the reverse march
+and the batched persistent kernel meet the same bars as on regular grids.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09389_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_ABS_REL = 1e-4
+GRAD_REL = 1e-3
+
+SHAPES = [(1, 1, 1), (1, 9, 11), (9, 1, 11), (9, 11, 1), (2, 7, 5), (7, 2, 1), (1, 2, 2), (2, 2, 2)]
+PLANS = [None, (4, 32, 4), (4, 32, 0), (4, 32, 4, 2), (1, 64, 4, 2), (2, 64, 3), (1, 64, 1), (2, 32, 0, 2),
+         (1, 32, 4)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2511_09389_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def problem(shape, seed, n_freq=4):
+    return inputs.random_small(seed, shape=shape, n_freq=n_freq, n_src=3, num_rays=37, step_size=0.6,
+                               horizon=9.0)
+
+
+def oracle_field(p):
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    return oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns)
+
+
+def assert_parity(F, R):
+    F = np.asarray(F, np.float64).reshape(R.shape)
+    for b in range(R.shape[0]):
+        d = F[b] - R[b]
+        e2 = np.linalg.norm(d) / np.linalg.norm(R[b])
+        emax = np.abs(d).max() / np.abs(R[b]).max()
+        assert e2 <= REL_L2 and emax <= MAX_ABS_REL, f"bin {b}: rel-L2 {e2:.3e}, max-abs-rel {emax:.3e}"
+
+
+def advance(torch, p, **opts):
+    from paper_2511_09389_gb300.api import Grid
+    g = Grid(p.shape, 8, **opts)
+    t = lambda a: torch.from_numpy(a).cuda()
+    out = g.advance(t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size, p.radiation_velocity, p.time_step)
+    torch.cuda.synchronize()
+    F = out.cpu().numpy()
+    g.close()
+    return F
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_plan_family_on_degenerate_extents(torch_cuda, shape):
+    p = problem(shape, 700 + sum(shape))
+    R = oracle_field(p)
+    for plan in PLANS:
+        F = advance(torch_cuda, p, plan=plan)
+        try:
+            assert_parity(F, R)
+        except AssertionError as e:
+            raise AssertionError(f"plan {plan}: {e}") from None
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 11), (7, 2, 1), (2, 2, 2)])
+def test_every_accumulation_on_degenerate_extents(torch_cuda, shape):
+    p = problem(shape, 720 + sum(shape), n_freq=3)
+    R = oracle_field(p)
+    for opts in ({"accumulation": "fp32"}, {"accumulation": "fp64"}, {"accumulation": "fixed"},
+                 {"deterministic": True}, {"kappa_mode": 0, "accumulation": "auto"}):
+        assert_parity(advance(torch_cuda, p, **opts), R)
+    # deterministic mode is bitwise reproducible here too
+    a = advance(torch_cuda, p, deterministic=True)
+    b = advance(torch_cuda, p, deterministic=True)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape,n_freq,stride", [((1, 9, 11), 1, 4), ((9, 11, 1), 2, 8), ((7, 2, 1), 1, 16),
+                                                 ((1, 1, 1), 1, 4), ((2, 2, 2), 4, 8), ((9, 1, 11), 3, 32)])
+def test_adjoint_on_degenerate_extents(torch_cuda, shape, n_freq, stride):
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = problem(shape, 740 + sum(shape) + n_freq, n_freq=n_freq)
+    G = np.random.default_rng(n_freq + stride).standard_normal(p.j.shape)
+    g = Grid(p.shape, 8, ckpt_stride=stride)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    gj, gk = g.backward(t(G), t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size,
+                        p.radiation_velocity, p.time_step)
+    torch.cuda.synchronize()
+    gj, gk = gj.cpu().numpy(), gk.cpu().numpy()
+    g.close()
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    rj, rk = oracle.backward(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G)
+    for b in range(n_freq):
+        for got, ref in ((gj[b], rj[b]), (gk[b], rk[b])):
+            e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert e <= GRAD_REL, (b, e)
+
+
+def test_batch_of_degenerate_instances(torch_cuda):
+    """The batched persistent kernel on slab, line and single-cell instances."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Batch
+    probs = [problem(s, 760 + i, n_freq=nf) for i, (s, nf) in
+             enumerate([((1, 9, 11), 1), ((7, 2, 1), 2), ((1, 1, 1), 4), ((2, 2, 2), 3), ((9, 11, 1), 5)])]
+    dev = []
+    for p in probs:
+        d = {k: torch.from_numpy(v).cuda() for k, v in (("j", p.j), ("kappa", p.kappa), ("sources", p.sources))}
+        d.update(num_rays=p.num_rays, step_size=p.step_size, radiation_velocity=1.0, time_step=p.time_step)
+        dev.append(d)
+    b = Batch(dev)
+    outs = [o.cpu().numpy() for o in b.run()]
+    torch.cuda.synchronize()
+    b.close()
+    for p, F in zip(probs, outs):
+        assert_parity(F, oracle_field(p))
