@@ -83,6 +83,20 @@ def test_bad_options_rejected_at_creation(lib, field, value, word):
     assert not h.value
 
 
+@pytest.mark.parametrize("dims,max_freq", [((1291, 1291, 1291), 1), ((1024, 1024, 512), 1), ((1024, 1024, 512), 4),
+                                           ((1024, 512, 512), 5), ((2, 1 << 30, 1), 1), ((0, 8, 8), 1),
+                                           ((8, -1, 8), 1), ((8, 8, 8), 0)])
+def test_grid_limits_rejected_at_creation(lib, dims, max_freq):
+    """The kernels index cells and packed bin groups with 32-bit integers: a grid whose
+    n0 n1 n2 times the bins rounded up to a group of four reaches 2^31 is refused on the host,
+    before any device call, as are empty extents and max_freq < 1."""
+    h = ctypes.c_void_p()
+    assert lib.rt_create_grid(ctypes.byref(h), *dims, max_freq, None) == 1
+    msg = lib.rt_last_error()
+    assert (b"too large" in msg) or (b">= 1" in msg)
+    assert not h.value
+
+
 @pytest.mark.parametrize("field,value", [("plan_lanes", 2), ("plan_tile", 2), ("plan_prefetch", 2),
                                          ("plan_prefetch", 4), ("plan_prefetch", 3)])
 def test_deterministic_rejects_plans_it_cannot_run(lib, field, value):
