@@ -123,3 +123,45 @@ def test_batch_of_degenerate_instances(torch_cuda):
     b.close()
     for p, F in zip(probs, outs):
         assert_parity(F, oracle_field(p))
+
+
+@pytest.mark.parametrize("num_rays,ns", [(1, 1), (1, 7), (2, 1), (2, 2), (33, 1), (5, 2)])
+def test_fewest_rays_and_substeps(torch_cuda, num_rays, ns):
+    """One ray (the lattice's single direction), two rays, and marches of one or two substeps
+    (a ray's only corner set is flushed at the end), for every plan family."""
+    p = inputs.random_small(780 + num_rays + ns, shape=(9, 7, 8), n_freq=4, n_src=3, num_rays=num_rays,
+                            step_size=0.6, horizon=ns * 0.6)
+    assert oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step) == ns
+    R = oracle_field(p)
+    for plan in PLANS:
+        F = advance(torch_cuda, p, plan=plan)
+        try:
+            assert_parity(F, R)
+        except AssertionError as e:
+            raise AssertionError(f"plan {plan}: {e}") from None
+
+
+@pytest.mark.parametrize("num_rays,ns,stride", [(1, 1, 4), (1, 7, 4), (2, 2, 8), (5, 3, 16)])
+def test_adjoint_fewest_rays_and_substeps(torch_cuda, num_rays, ns, stride):
+    """The reverse march when a ray has fewer substeps than one checkpoint segment."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    for n_freq in (1, 4):
+        p = inputs.random_small(800 + num_rays + ns, shape=(9, 7, 8), n_freq=n_freq, n_src=3,
+                                num_rays=num_rays, step_size=0.6, horizon=ns * 0.6)
+        G = np.random.default_rng(ns).standard_normal(p.j.shape)
+        g = Grid(p.shape, 8, ckpt_stride=stride)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+        gj, gk = g.backward(t(G), t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size,
+                            p.radiation_velocity, p.time_step)
+        torch.cuda.synchronize()
+        gj, gk = gj.cpu().numpy(), gk.cpu().numpy()
+        g.close()
+        rj, rk = oracle.backward(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G)
+        for b in range(n_freq):
+            for got, ref in ((gj[b], rj[b]), (gk[b], rk[b])):
+                if not np.any(ref):   # N_s = 1: I_0 = 0 and no later emission, so dL/dkappa = 0
+                    assert not np.any(got), (n_freq, b)
+                    continue
+                e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+                assert e <= GRAD_REL, (n_freq, b, e)
