@@ -237,20 +237,11 @@ __device__ __forceinline__ double widen_f32(float v) {
 __device__ __forceinline__ void red_add_f64(double* p, float v) {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(widen_f32(v)));
 }
-__device__ __forceinline__ void red_add_f64_if(bool q, double* p, float v) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f64 [%1], %2;\n\t}"
-                 ::"r"((int)q), "l"(p), "d"(widen_f32(v)));
-}
 
 // 64-bit integer reduction for the deterministic (fixed-point) accumulation mode, with the L2
 // policy of red_policy().
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long a, unsigned long long pol) {
     asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(a), "l"(pol));
-}
-__device__ __forceinline__ void red_add_u64_if(bool p, unsigned long long* a, unsigned long long v,
-                                               unsigned long long pol) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.L2::cache_hint.u64 [%1], %2, %3;\n\t}"
-                 ::"r"((int)p), "l"(a), "l"(v), "l"(pol));
 }
 
 }  // namespace rt

@@ -72,41 +72,35 @@ struct RayState {
 
 // Send one merged deposit (the sums for one corner) to memory. DET (the accumulation):
 //   0: one W-wide FP32 reduction;
-//   1: deterministic mode, one 64-bit fixed-point reduction per real bin (integer addition is
+//   1: deterministic mode, one 64-bit fixed-point reduction per bin (integer addition is
 //      associative, so the result does not depend on the order of the deposits);
-//   2: one FP64 reduction per real bin (the sums keep 53 bits however many small deposits a
+//   2: one FP64 reduction per bin (the sums keep 53 bits however many small deposits a
 //      large cell sum takes; same L2 rate per operation as the W-wide FP32 one).
-// Modes 1 and 2 use the 8-byte accumulator og64, packed like og ([cell][W]).
+// Modes 1 and 2 use the 8-byte accumulator og64, packed like og ([cell][W]); the padding bins of
+// a group (past nbins) have j = kappa = 0, so they deposit exact zeros into their own slots and
+// need no test.
 template <int W, int DET>
 __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
     if (DET == 2) {
         double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
 #pragma unroll
-        for (int b = 0; b < W; ++b)
-            if (W == 1 || b < L.nbins) red_add_f64(o + b, v[b]);
+        for (int b = 0; b < W; ++b) red_add_f64(o + b, v[b]);
     } else if (DET) {
         // v * 2^k is exact in FP32; its rounding to an integer is the fixed-point quantisation
+        unsigned long long* o = L.og64 + (size_t)cell * W;
 #pragma unroll
-        for (int b = 0; b < W; ++b)
-            if (W == 1 || b < L.nbins)
-                red_add_u64(L.og64 + (size_t)cell * W + b, (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
+        for (int b = 0; b < W; ++b) red_add_u64(o + b, (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
     } else {
         red_vec<W>(L.og, cell, v, L.pol);
     }
 }
 
-// flush() when p is true, without a branch (callers pass a valid cell either way).
+// flush() when p is true (callers pass a valid cell either way). FP32: one predicated vector
+// reduction. 8-byte sums: the W reductions of a corner under one branch, not one each.
 template <int W, int DET>
 __device__ __forceinline__ void flush_if(bool p, const Lane& L, int cell, const float* v) {
-    if (DET == 2) {
-        double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
-#pragma unroll
-        for (int b = 0; b < W; ++b) red_add_f64_if(p && (W == 1 || b < L.nbins), o + b, v[b]);
-    } else if (DET) {
-#pragma unroll
-        for (int b = 0; b < W; ++b)
-            red_add_u64_if(p && (W == 1 || b < L.nbins), L.og64 + (size_t)cell * W + b,
-                           (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
+    if (DET) {
+        if (p) flush<W, DET>(L, cell, v);
     } else {
         red_vec_if<W>(p, L.og, cell, v, L.pol);
     }
