@@ -165,3 +165,28 @@ def test_adjoint_fewest_rays_and_substeps(torch_cuda, num_rays, ns, stride):
                     continue
                 e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
                 assert e <= GRAD_REL, (n_freq, b, e)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 11), (7, 2, 1), (2, 2, 2)])
+def test_stateful_advance_on_degenerate_extents(torch_cuda, shape):
+    """rt_advance_continue (rays carried between calls, media changing between them) against the
+    oracle's stateful advance on slab, line and single-cell grids."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = inputs.random_small(820 + sum(shape), shape=shape, n_freq=3, n_src=3, num_rays=41, step_size=0.5,
+                            horizon=3.0)
+    g = Grid(p.shape, 8)
+    st = oracle.MarchState(p.n_freq, len(p.sources), p.num_rays)
+    s = torch.from_numpy(p.sources).cuda()
+    ns = oracle.num_substeps(p.step_size, 1.0, p.time_step)
+    for call, (aj, ak) in enumerate([(1.0, 1.0), (0.5, 1.7), (2.0, 0.3)]):
+        j = (p.j * aj).astype(np.float32)
+        k = (p.kappa * ak).astype(np.float32)
+        F = g.advance_continue(torch.from_numpy(j).cuda(), torch.from_numpy(k).cuda(), s, p.num_rays, p.step_size,
+                               1.0, p.time_step, restart=(call == 0)).cpu().numpy()
+        R = oracle.advance_state(j, k, p.sources, p.num_rays, p.step_size, ns, st, restart=(call == 0))
+        try:
+            assert_parity(F, R)
+        except AssertionError as e:
+            raise AssertionError(f"call {call}: {e}") from None
+    g.close()

@@ -125,3 +125,20 @@ def test_noalloc_matches_oracle_and_allocates_nothing(env):
     R = oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size,
                        oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step))
     close(out.cpu().numpy().astype(np.float64), R)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 11), (9, 11, 1), (7, 2, 1), (2, 2, 2)])
+def test_noalloc_on_degenerate_extents(env, shape):
+    """Slab, line and single-cell grids through the allocation-free entry point, against the
+    FP64 oracle."""
+    import oracle
+    torch, lib = env
+    p = inputs.random_small(90 + sum(shape), shape=shape, n_freq=3, n_src=3, num_rays=37, step_size=0.6,
+                            horizon=9.0)
+    out = torch.empty(p.j.shape, device="cuda")
+    st, _ = noalloc(torch, lib, p, out)
+    assert st == 0, lib.rt_last_error().decode()
+    torch.cuda.synchronize()
+    R = oracle.advance(p.j, p.kappa, p.sources, p.num_rays, p.step_size,
+                       oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step))
+    close(out.cpu().numpy().astype(np.float64), R)
