@@ -190,3 +190,29 @@ def test_stateful_advance_on_degenerate_extents(torch_cuda, shape):
         except AssertionError as e:
             raise AssertionError(f"call {call}: {e}") from None
     g.close()
+
+
+@pytest.mark.parametrize("shape,n_freq,stride", [((10, 1, 9), 1, 4), ((1, 9, 11), 2, 8), ((7, 2, 1), 4, 16),
+                                                 ((1, 1, 1), 1, 4)])
+def test_source_gradient_on_degenerate_extents(torch_cuda, shape, n_freq, stride):
+    """rt_backward_sources against the oracle; along a single-cell axis the component vanishes."""
+    torch = torch_cuda
+    from paper_2511_09389_gb300.api import Grid
+    p = problem(shape, 840 + sum(shape) + n_freq, n_freq=n_freq)
+    G = np.random.default_rng(n_freq + 3).standard_normal(p.j.shape)
+    g = Grid(p.shape, 8, ckpt_stride=stride)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    _, _, gs = g.backward(t(G), t(p.j), t(p.kappa), t(p.sources), p.num_rays, p.step_size,
+                          p.radiation_velocity, p.time_step, need_sources=True)
+    torch.cuda.synchronize()
+    gs = gs.cpu().numpy().astype(np.float64)
+    g.close()
+    ns = oracle.num_substeps(p.step_size, p.radiation_velocity, p.time_step)
+    rs = oracle.source_gradient(p.j, p.kappa, p.sources, p.num_rays, p.step_size, ns, G)
+    # the gradient's natural size: max |G| times max |F| per unit of length
+    scale = np.abs(G).max() * np.abs(oracle_field(p)).max()
+    if np.abs(rs).max() > 1e-9 * scale:          # a 1 x 1 x 1 grid has none: F does not move
+        assert np.linalg.norm(gs - rs) / np.linalg.norm(rs) <= GRAD_REL
+    for a, n in enumerate(shape):
+        if n == 1:
+            assert np.abs(gs[:, a]).max() <= 1e-6 * scale, (a, gs[:, a])

@@ -98,3 +98,31 @@ def test_single_cell_axis_adjoint_central_fd():
     e = rng.standard_normal(shape)
     lin = np.sum(G * oracle.advance(e, kap, src, nr, ds, ns))
     assert abs(lin - np.sum(gj * e)) <= 1e-12 * np.abs(lin) + 1e-14
+
+
+def test_source_gradient_on_a_slab():
+    """dL/d(source position) on a slab one cell thick along axis 1: the component along that axis
+    vanishes (both corners are the one cell, for the gather and the deposit alike: its terms
+    cancel to rounding), and the other two match FP64 central differences of the march."""
+    from paper_2511_09389_gb300 import inputs
+    rng = np.random.default_rng(31)
+    p = inputs.random_small(31, shape=(10, 1, 9), n_freq=2, n_src=2, num_rays=48, step_size=0.6, horizon=5.0,
+                            outside=False)
+    ns = oracle.num_substeps(p.step_size, 1.0, p.time_step)
+    G = rng.standard_normal(p.j.shape)
+    src = p.sources.astype(np.float64)
+    src[:, 1] = [0.3, -0.8]                      # inside the one cell and outside it
+
+    def loss(s):
+        return float((G * oracle.advance(p.j, p.kappa, s, p.num_rays, p.step_size, ns, geom_mode=1)).sum())
+
+    g = oracle.source_gradient(p.j, p.kappa, src, p.num_rays, p.step_size, ns, G, geom_mode=1)
+    assert np.abs(g[:, 1]).max() <= 1e-12 * np.abs(g).max()
+    h = 1e-6
+    fd = np.zeros_like(src)
+    for s in range(src.shape[0]):
+        for a in (0, 2):
+            e = np.zeros_like(src)
+            e[s, a] = h
+            fd[s, a] = (loss(src + e) - loss(src - e)) / (2 * h)
+    assert np.abs(g - fd).max() <= 1e-7 * np.abs(fd).max()
