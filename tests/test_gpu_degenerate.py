@@ -69,6 +69,8 @@ def test_every_plan_family_on_degenerate_extents(torch_cuda, shape):
             assert_parity(F, R)
         except AssertionError as e:
             raise AssertionError(f"plan {plan}: {e}") from None
+    # the autotuner times every candidate (tiled ones included, which such grids cannot take)
+    assert_parity(advance(torch_cuda, p, autotune=True), R)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 9, 11), (7, 2, 1), (2, 2, 2)])
