@@ -453,36 +453,31 @@ __global__ void k_fix_prepare(const float* __restrict__ j, long long nj, unsigne
     *fix = __uint_as_float((unsigned)(e + 127) << 23);
 }
 
-// out[b][c] (+)= acc[g][c][w] / fix for bin b = g * W + w (the packed fixed-point layout): the
-// integer is rounded once to FP32 and scaled by the power of two 1 / fix (exact)
-__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int n_freq, int W, long long ncell,
+// out[b][c] (+)= acc[b][c] / fix (the accumulator is bin-major, groups of W bins padded at the
+// end): the integer is rounded once to FP32 and scaled by the power of two 1 / fix (exact)
+__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int n_freq, long long ncell,
                                  const float* __restrict__ fix, float* __restrict__ out, int accumulate) {
     const float inv = 1.0f / *fix;
     const long long n = (long long)n_freq * ncell;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / ncell, c = i - b * ncell;
-        const long long g = b / W, w = b - g * W;
-        const float v = __ll2float_rn((long long)acc[(g * ncell + c) * W + w]) * inv;
+        const float v = __ll2float_rn((long long)acc[i]) * inv;
         out[i] = accumulate ? out[i] + v : v;
     }
 }
 
-// out[b][c] (+)= (float) (scale * acc[g][c][w]) for bin b = g * W + w (the packed FP64 layout)
-__global__ void k_f64_to_float(const double* __restrict__ acc, int n_freq, int W, long long ncell, double scale,
+// out[b][c] (+)= (float) (scale * acc[b][c]) (the FP64 accumulator, bin-major like the fixed-point one)
+__global__ void k_f64_to_float(const double* __restrict__ acc, int n_freq, long long ncell, double scale,
                                float* __restrict__ out, int accumulate) {
     const long long n = (long long)n_freq * ncell;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / ncell, c = i - b * ncell;
-        const long long g = b / W, w = b - g * W;
-        const float v = (float)(scale * __ldg(acc + (g * ncell + c) * W + w));
+        const float v = (float)(scale * __ldg(acc + i));
         out[i] = accumulate ? out[i] + v : v;
     }
 }
 
-cudaError_t launch_f64_to_float(const double* acc, int n_freq, int W, long long ncell, double scale, float* out,
+cudaError_t launch_f64_to_float(const double* acc, int n_freq, long long ncell, double scale, float* out,
                                 int accumulate, cudaStream_t st) {
-    k_f64_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, W, ncell, scale, out,
-                                                                            accumulate);
+    k_f64_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, ncell, scale, out, accumulate);
     return cudaGetLastError();
 }
 
@@ -492,10 +487,9 @@ cudaError_t launch_fix_prepare(const float* j, long long nj, unsigned long long*
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
+cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, long long ncell, const float* fix,
                                   float* out, int accumulate, cudaStream_t st) {
-    k_fixed_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, W, ncell, fix, out,
-                                                                               accumulate);
+    k_fixed_to_float<<<grid_for((long long)n_freq * ncell, 256), 256, 0, st>>>(acc, n_freq, ncell, fix, out, accumulate);
     return cudaGetLastError();
 }
 

@@ -38,8 +38,8 @@ struct Lane {
     const float* __restrict__ jg;
     const float* __restrict__ kg;
     float* __restrict__ og;
-    unsigned long long* __restrict__ og64;   // 8-byte accumulator of the group, packed like og
-                                              //   ([cell][W]): fixed point (deterministic mode) or
+    unsigned long long* __restrict__ og64;   // 8-byte accumulator of the group, bin-major
+                                              //   ([W][cell]): fixed point (deterministic mode) or
                                               //   FP64 (the wide accumulation), see flush()
     long long ncell;
     int nbins;                                //   real bins in this group (the rest are padding)
@@ -76,20 +76,22 @@ struct RayState {
 //      associative, so the result does not depend on the order of the deposits);
 //   2: one FP64 reduction per bin (the sums keep 53 bits however many small deposits a
 //      large cell sum takes; same L2 rate per operation as the W-wide FP32 one).
-// Modes 1 and 2 use the 8-byte accumulator og64, packed like og ([cell][W]); the padding bins of
-// a group (past nbins) have j = kappa = 0, so they deposit exact zeros into their own slots and
-// need no test.
+// Modes 1 and 2 use the 8-byte accumulator og64, bin-major ([W][cell]): the W reductions of one
+// corner go to W different sectors (L2 slices) instead of queueing on one, which matters on the
+// crowded cells next to the sources. The padding bins of a group (past nbins) have
+// j = kappa = 0, so they deposit exact zeros into their own rows and need no test.
 template <int W, int DET>
 __device__ __forceinline__ void flush(const Lane& L, int cell, const float* v) {
     if (DET == 2) {
-        double* o = reinterpret_cast<double*>(L.og64) + (size_t)cell * W;
+        double* o = reinterpret_cast<double*>(L.og64) + cell;
 #pragma unroll
-        for (int b = 0; b < W; ++b) red_add_f64(o + b, v[b]);
+        for (int b = 0; b < W; ++b) red_add_f64(o + b * L.ncell, v[b]);
     } else if (DET) {
         // v * 2^k is exact in FP32; its rounding to an integer is the fixed-point quantisation
-        unsigned long long* o = L.og64 + (size_t)cell * W;
+        unsigned long long* o = L.og64 + cell;
 #pragma unroll
-        for (int b = 0; b < W; ++b) red_add_u64(o + b, (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
+        for (int b = 0; b < W; ++b)
+            red_add_u64(o + b * L.ncell, (unsigned long long)__float2ll_rn(v[b] * L.fix), L.pol);
     } else {
         red_vec<W>(L.og, cell, v, L.pol);
     }

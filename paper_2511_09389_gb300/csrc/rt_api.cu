@@ -440,10 +440,10 @@ rt_status setup_accumulator(rt_grid* g, const Call& a, int ns, const Plan& plan,
 rt_status finish_accumulator(rt_grid* g, const Call& a, const Plan& plan, float scale, const rt::MarchArgs& m) {
     const long long ncell = g->ncell();
     if (m.acc_mode == 1)
-        RT_CUDA(rt::launch_fixed_to_float(m.acc64, a.n_freq, plan.W, ncell, m.fix, a.out, a.accumulate, a.st),
+        RT_CUDA(rt::launch_fixed_to_float(m.acc64, a.n_freq, ncell, m.fix, a.out, a.accumulate, a.st),
                 "fixed-point conversion");
     else if (m.acc_mode == 2)
-        RT_CUDA(rt::launch_f64_to_float((const double*)m.acc64, a.n_freq, plan.W, ncell, (double)scale, a.out,
+        RT_CUDA(rt::launch_f64_to_float((const double*)m.acc64, a.n_freq, ncell, (double)scale, a.out,
                                         a.accumulate, a.st),
                 "FP64 conversion launch");
     else if (plan.W > 1)

@@ -27,7 +27,7 @@ struct MarchArgs {
     float* acc;             // FP32 accumulator, same layout (W = 1: may be the output itself)
     int acc_mode;               // 0: FP32 reductions into acc; 1: 64-bit fixed point into acc64
                                 // (deterministic mode); 2: FP64 reductions into acc64 (as double)
-    unsigned long long* acc64;  // 8-byte accumulator [groups][ncell][W] (modes 1 and 2) or NULL
+    unsigned long long* acc64;  // 8-byte accumulator [groups][W][ncell] (modes 1 and 2) or NULL
     const float* fix;           // fixed-point units per unit deposit, a power of two (device scalar)
     const float4* dirs;     // ray directions (xyz, w unused), ray_count entries
     const float* src;       // device [nsrc][3]
@@ -101,9 +101,9 @@ cudaError_t launch_check_inputs(const float* j, const float* kappa, long long n,
 cudaError_t launch_input_hash(const float* j, const float* kappa, long long n, const float* src, int nsrc,
                               unsigned long long* out, cudaStream_t st);
 // FP64 accumulation: out[b][c] (+)= (float) (scale * acc[b / W][c][b % W]), the product in FP64.
-cudaError_t launch_f64_to_float(const double* acc, int n_freq, int W, long long ncell, double scale, float* out,
+cudaError_t launch_f64_to_float(const double* acc, int n_freq, long long ncell, double scale, float* out,
                                 int accumulate, cudaStream_t st);
-cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, int W, long long ncell, const float* fix,
+cudaError_t launch_fixed_to_float(const unsigned long long* acc, int n_freq, long long ncell, const float* fix,
                                   float* out, int accumulate, cudaStream_t st);
 
 // Geometry trace of one ray (test hook).
